@@ -1,0 +1,113 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module generates signals only: it holds none of the transform's
+arithmetic and imports nothing else from this package, so both the FP64 oracle
+checks and the CUDA path can be fed from it.  Every generator is a pure function
+of its seed (NumPy's PCG64, identical on x86 and Arm), returning complex64
+arrays in the library's layout (batch-major, transform elements contiguous;
+2D frames row-major).
+
+Workload recipes (the paper measures on no public dataset; these stand in for
+its radar workloads):
+
+* ``uniform``      -- iid U[-1, 1] real and imaginary parts.
+* ``tones``        -- per transform, unit-amplitude complex exponentials at
+                      seeded integer bins; the forward DFT of one tone at bin k0
+                      is N at k0 and 0 elsewhere.
+* ``buried_tone``  -- ``uniform`` plus a tone of amplitude 1e-3 at a seeded bin
+                      in every transform (mixed-precision accuracy workload).
+* ``sar_frame``    -- a [azimuth rows][range cols] frame of linear-FM chirp
+                      echoes (bandwidth-time product 500, sampled at 1.2x the
+                      bandwidth, so 600-sample chirps in both directions) from
+                      point scatterers with unit amplitude and uniform random
+                      phase, plus circular complex Gaussian noise at the given
+                      SNR relative to the mean signal power of the frame.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["uniform", "tones", "tone_bins", "buried_tone", "sar_frame", "chirp"]
+
+
+def uniform(seed: int, batch: int, n: int) -> np.ndarray:
+    """(batch, n) complex64 with iid U[-1, 1] real and imaginary parts."""
+    rng = np.random.default_rng(seed)
+    re = rng.uniform(-1.0, 1.0, size=(batch, n)).astype(np.float32)
+    im = rng.uniform(-1.0, 1.0, size=(batch, n)).astype(np.float32)
+    out = np.empty((batch, n), dtype=np.complex64)
+    out.real = re
+    out.imag = im
+    return out
+
+
+def tone_bins(seed: int, batch: int, n: int, ntones: int = 1) -> np.ndarray:
+    """(batch, ntones) int64 distinct bins in [0, n) used by ``tones``."""
+    rng = np.random.default_rng(seed)
+    k = min(ntones, n)
+    return np.stack([rng.choice(n, size=k, replace=False) for _ in range(batch)])
+
+
+def _exp_bins(bins: np.ndarray, n: int) -> np.ndarray:
+    """exp(+2 pi i k j / n) for j < n, one row per bin k; the phase index k*j is
+    reduced mod n as an integer before the angle is formed."""
+    j = np.arange(n, dtype=np.int64)
+    ph = (bins[:, None].astype(np.int64) * j[None, :]) % n
+    ang = 2.0 * np.pi * ph.astype(np.float64) / float(n)
+    return np.cos(ang) + 1j * np.sin(ang)
+
+
+def tones(seed: int, batch: int, n: int, ntones: int = 1) -> np.ndarray:
+    """(batch, n) complex64: sum of ``ntones`` unit tones per transform at the
+    bins returned by ``tone_bins(seed, batch, n, ntones)``."""
+    bins = tone_bins(seed, batch, n, ntones)
+    out = np.zeros((batch, n), dtype=np.complex128)
+    for b in range(batch):
+        out[b] = _exp_bins(bins[b], n).sum(axis=0)
+    return out.astype(np.complex64)
+
+
+def buried_tone(seed: int, batch: int, n: int, amplitude: float = 1e-3):
+    """``uniform`` plus one tone of the given amplitude at a seeded bin per
+    transform.  Returns (x complex64 (batch, n), bins int64 (batch,))."""
+    x = uniform(seed, batch, n).astype(np.complex128)
+    bins = np.random.default_rng(seed + 0x5EED).integers(0, n, size=batch)
+    for b in range(batch):
+        x[b] += amplitude * _exp_bins(bins[b:b + 1], n)[0]
+    return x.astype(np.complex64), bins
+
+
+def chirp(bt: float = 500.0, oversample: float = 1.2) -> np.ndarray:
+    """Baseband linear-FM chirp sampled at ``oversample`` x its bandwidth:
+    L = round(oversample * bt) samples, phase pi * (j - L/2)^2 / (oversample^2 bt)."""
+    length = int(round(oversample * bt))
+    t = np.arange(length, dtype=np.float64) - length / 2.0
+    return np.exp(1j * np.pi * t * t / (oversample * oversample * bt))
+
+
+def sar_frame(seed: int, rows: int = 4096, cols: int = 8192, scatterers: int = 50,
+              bt: float = 500.0, snr_db: float = 10.0, oversample: float = 1.2) -> np.ndarray:
+    """(rows, cols) complex64 SAR raw-data frame: azimuth along rows, range
+    along the contiguous columns."""
+    rng = np.random.default_rng(seed)
+    c = chirp(bt, oversample)
+    length = c.size
+    frame = np.zeros((rows, cols), dtype=np.complex128)
+    r0 = rng.integers(0, rows, size=scatterers)
+    c0 = rng.integers(0, cols, size=scatterers)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=scatterers)
+    half = length // 2
+    for s in range(scatterers):
+        ra, rb = r0[s] - half, r0[s] - half + length
+        ca, cb = c0[s] - half, c0[s] - half + length
+        ia, ib = max(ra, 0), min(rb, rows)
+        ja, jb = max(ca, 0), min(cb, cols)
+        if ia >= ib or ja >= jb:
+            continue
+        patch = np.exp(1j * phase[s]) * np.outer(c[ia - ra:ib - ra], c[ja - ca:jb - ca])
+        frame[ia:ib, ja:jb] += patch
+    power = np.mean(np.abs(frame) ** 2)
+    sigma2 = power / (10.0 ** (snr_db / 10.0))
+    noise = rng.standard_normal((rows, cols)) + 1j * rng.standard_normal((rows, cols))
+    frame += np.sqrt(sigma2 / 2.0) * noise
+    return frame.astype(np.complex64)
