@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the batched complex FFT on GB300.
+
+Workload: batched 1D complex64 FFTs, N = 2^8 .. 2^14 with N * batch = 2^27
+(1 GiB in, 1 GiB out per launch), forward and inverse, out-of-place, FP32.
+One step = the whole sweep: 7 sizes x 2 directions = 14 transforms of 2^27
+elements.  Metric: FFT GFLOP/s with the 5 N log2 N convention (Bergach et al.
+Eq. 1 convention), whole job; beside it the achieved HBM bandwidth of the
+Stockham pass kernel against the measured copy bandwidth (16 bytes per element
+per pass: one read and one write).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas, no collective on
+the data path; value = all ranks' work / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FFT GFLOP/s (5NlogN) + % HBM roofline, FP32 vs TC mixed; served p99 latency"
+LOGS = list(range(8, 15))
+TOTAL_LOG = 27
+DIRS = (-1, +1)
+WORKLOAD = ("batched 1D complex64 FFT sweep N=2^8..2^14, N*batch=2^27 (1 GiB in) per launch, "
+            "forward and inverse, out-of-place, FP32")
+KERNEL_SOURCES = ["paper_1505_08067_gb300/csrc/kernels.cu", "paper_1505_08067_gb300/csrc/fft_stage.h",
+                  "paper_1505_08067_gb300/csrc/fft_core.h"]
+
+
+def flops_of(logn: int, elements: int) -> float:
+    return 5.0 * elements * logn
+
+
+def step_flops(elements: int) -> float:
+    return sum(flops_of(l, elements) for l in LOGS) * len(DIRS)
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def load_traffic(sha: str):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_sha") != sha:
+        return None
+    return d.get("bytes_per_launch")
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[2], parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- oracle ----
+
+def oracle_gflops(seconds: float, steps: int = 1):
+    """Times the FP64 oracle (as it stands) on a bounded sample of the workload
+    sized for about `seconds` of CPU work in total over `steps` steps.
+    Returns (GFLOP/s, threads, sample description, per-step sample elems)."""
+    import numpy as np
+
+    from oracle import oracle
+    from paper_1505_08067_gb300 import synth
+    threads = oracle.num_threads(0)
+    probe = synth.uniform(2, 1, 2 ** 20).reshape(-1, 1024)
+    t0 = time.perf_counter()
+    oracle.fft(probe, -1)
+    rate = flops_of(10, 2 ** 20) / max(time.perf_counter() - t0, 1e-6)
+    per_step = seconds * rate / max(steps, 1)
+    elems = 2 ** int(max(14, min(TOTAL_LOG, math.floor(math.log2(per_step / step_flops(1))))))
+    x = synth.uniform(2, 1, elems)[0]
+    return rate, threads, elems, x
+
+
+def run_oracle_steps(x, elems, steps, warmup):
+    from oracle import oracle
+    for it in range(warmup + steps):
+        if it == warmup:
+            t0 = time.perf_counter()
+        for lg in LOGS:
+            for d in DIRS:
+                oracle.fft(x.reshape(-1, 2 ** lg), d)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args, rank: int) -> None:
+    if rank != 0:
+        return
+    _, threads, elems, x = oracle_gflops(60.0, args.steps + args.warmup)
+    secs = run_oracle_steps(x, elems, args.steps, args.warmup)
+    value = step_flops(elems) * args.steps / secs / 1e9
+    sample = (f"{elems} elements (of 2^27) per size and direction per step, iid U[-1,1] "
+              f"complex64 widened to FP64")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------ ours ----
+
+def ours(args, rank: int, world: int) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1505_08067_gb300 import gbfft, synth
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    E = 2 ** TOTAL_LOG
+    x_np = synth.uniform(2, 1, E)[0]
+    x = torch.from_numpy(x_np).to(dev)
+    y = torch.empty_like(x)
+    plans = {}
+    for lg in LOGS:
+        for d in DIRS:
+            plans[(lg, d)] = gbfft.Plan(2 ** lg, E >> lg, d, autotune=args.autotune)
+    launches_per_step = sum(p.launch_count for p in plans.values())
+    stream = torch.cuda.current_stream()
+    order = [(lg, d) for lg in LOGS for d in DIRS]
+
+    def one_step(evs=None):
+        for i, key in enumerate(order):
+            if evs is not None:
+                evs[i][0].record(stream)
+            plans[key].execute(x, y, stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    gpu_id = "0"
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        if getattr(props, "uuid", None) is not None:
+            u = str(props.uuid)
+            gpu_id = u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in order]
+          for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for s in range(args.steps):
+        one_step(ev[s])
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end)
+    per_launch = {key: [] for key in order}
+    for s in range(args.steps):
+        for i, key in enumerate(order):
+            per_launch[key].append(ev[s][i][0].elapsed_time(ev[s][i][1]))
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * step_flops(E) * args.steps / (ms_max * 1e-3) / 1e9
+
+    # roofline of the Stockham pass kernel (every launch here is one pass)
+    peaks = load_peaks()
+    alg_bytes = 16.0 * E
+    all_ms = [v for vs in per_launch.values() for v in vs]
+    avg_ms = sum(all_ms) / len(all_ms)
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    sha = kernel_source_sha()
+    traffic = load_traffic(sha)
+    per_size = {}
+    for lg in LOGS:
+        tms = statistics.median(per_launch[(lg, -1)] + per_launch[(lg, +1)])
+        per_size[f"2^{lg}"] = {"ms": round(tms, 4),
+                               "gflops": round(flops_of(lg, E) / (tms * 1e-3) / 1e9, 1),
+                               "gbs": round(alg_bytes / (tms * 1e-3) / 1e9, 1),
+                               "frac": round(alg_bytes / (tms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                               "radices": plans[(lg, -1)].describe()["passes"][0]["radices"]}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(x_np).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        def e2e_step():
+            for key in order:
+                plans[key].execute_host(h_in, h_out, x, y, stream)
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(1, min(args.steps, args.e2e_steps))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        a.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t2 = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * step_flops(E) * k2 / (float(t2.item()) * 1e-3) / 1e9,
+               "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * E * len(order),
+               "d2h_bytes_per_step": 8 * E * len(order), "steps": k2,
+               "api": "fft_execute_host (pinned host buffers, chunked H2D/kernel/D2H overlap)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, threads, elems, xs = oracle_gflops(15.0, 1)
+        secs = run_oracle_steps(xs, elems, 1, 0)
+        cpu = {"value": step_flops(elems) / secs / 1e9, "unit": "GFLOP/s", "cores": threads,
+               "kind": "oracle",
+               "sample": f"one sweep step on {elems} of the 2^27 elements per size and direction"}
+
+    if rank == 0:
+        frac = achieved / peaks["hbm_gbs"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: iid U[-1,1] complex64 (seed 2), generated on the host",
+            "config": {"workload": WORKLOAD, "sizes": [2 ** l for l in LOGS],
+                       "elements_per_launch": E, "precision": "FP32",
+                       "l2": "inputs larger than L2 (1 GiB per launch), no flush",
+                       "autotune": bool(args.autotune),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(frac, 4),
+                         "traffic": traffic, "kernel": "stockham_pass",
+                         "alg_bytes_per_launch": alg_bytes,
+                         "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "pct_hbm_roofline": round(100 * frac, 2),
+            "per_size": per_size,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        print(json.dumps(line))
+    for p in plans.values():
+        p.close()
+
+
+def main() -> None:
+    global LOGS, TOTAL_LOG
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--only", type=int, default=0, help="run only N = 2^ONLY (profiling)")
+    ap.add_argument("--total-log", type=int, default=TOTAL_LOG,
+                    help="log2 of elements per launch (profiling of smaller cases)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.only:
+        LOGS = [args.only]
+    TOTAL_LOG = args.total_log
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * gbfft -- batched complex FFT for one NVIDIA GB300 (sm_103a), C ABI.
+ *
+ * Method: Bergach, Kofman, de Simone, Tissot, Syska, "Efficient FFT mapping on
+ * GPU for radar processing application: modeling and implementation" (2015).
+ *   Sec. 2.1      the DFT X(k) = sum_n x(n) w_N^{nk}, w_N = exp(-2 pi i / N);
+ *                 the backward transform flips the exponent's sign; twiddle
+ *                 factors are precomputed and stored; mixed-radix stages.
+ *   Sec. 3.2      radix clustering bounded by on-chip storage; per-(radix,
+ *                 start stage) stage costs; shortest path over the schedule
+ *                 digraph picks the radix schedule; Eq. 1 bandwidth bound.
+ *   Sec. 3.3      transforms larger than one on-chip block are split and
+ *                 merged (four-step: column FFTs, twiddle, row FFTs).
+ *   Sec. 3.4      one transform per compute unit, global memory touched only at
+ *                 the first read and the last write; blocked transpose.
+ *   Sec. 3.1      the radar application: FFTs, a transpose, FFTs (2D frame).
+ *
+ * Conventions shared by every entry point:
+ *   - Data are complex64: interleaved (re, im) IEEE float32, 8 bytes per
+ *     element, natural order in and out.
+ *   - 1D: element i of transform b is at b*n[0] + i.
+ *     2D: n = {rows, cols}; frame b is row-major [rows][cols] (cols
+ *     contiguous) at b*rows*cols.
+ *   - direction FFT_FORWARD (-1) uses exp(-2 pi i nk/N); FFT_INVERSE (+1) uses
+ *     exp(+2 pi i nk/N) and is NOT normalised: inverse(forward(x)) = N x.
+ *   - Pointers named `in`/`out` are device pointers owned by the caller,
+ *     8-byte aligned.  `in` is never written.  in == out (in place) is allowed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Errors are returned as fft_status_t and never abort; fft_last_error()
+ *     gives a human-readable message for the calling thread.  No entry point
+ *     falls back to the CPU: without a usable CUDA device plan creation fails
+ *     with FFT_ERR_CUDA.
+ */
+#ifndef GBFFT_H
+#define GBFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GBFFT_API __attribute__((visibility("default")))
+#else
+#define GBFFT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft_plan_s* fft_plan_t; /* opaque; owned by the library */
+
+typedef enum {
+  FFT_OK = 0,
+  FFT_ERR_INVALID_ARG = 1,      /* null pointer, bad enum, misaligned pointer */
+  FFT_ERR_UNSUPPORTED_SIZE = 2, /* n not a power of two, or outside 2^0 .. 2^24 */
+  FFT_ERR_OUT_OF_MEMORY = 3,    /* device allocation for tables / workspace failed */
+  FFT_ERR_CUDA = 4,             /* a CUDA call failed (message in fft_last_error) */
+  FFT_ERR_TIMEOUT = 5,          /* a bounded wait gave up */
+  FFT_ERR_BAD_PLAN = 6,         /* null or destroyed plan, or plan/device mismatch */
+  FFT_ERR_NOT_IMPLEMENTED = 7   /* a valid request this build does not provide */
+} fft_status_t;
+
+enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
+
+enum {
+  FFT_PREC_FP32 = 0,     /* FP32 data, FP32 arithmetic, FP64-generated twiddles */
+  FFT_PREC_TC_FP16 = 1,  /* tensor-core class (reserved) */
+  FFT_PREC_TC_BF16 = 2,  /* tensor-core class (reserved) */
+  FFT_PREC_TC_BF16X3 = 3 /* tensor-core class (reserved) */
+};
+
+/*
+ * Create a plan for `batch` transforms of shape n[0..dims) (dims 1 or 2),
+ * direction FFT_FORWARD / FFT_INVERSE, precision FFT_PREC_*.
+ * Each length must be a power of two; 1D n[0] in [1, 2^24]; 2D rows and cols in
+ * [1, 2^14].  batch >= 0 (batch 0 gives a plan whose execute does nothing).
+ * The plan is bound to the CUDA device current at creation.  It allocates its
+ * twiddle tables and, for 1D n > 2^14, a workspace of batch*n complex64
+ * (query with fft_plan_workspace_bytes).  Nothing is allocated by fft_execute.
+ * Sec. 2.1 (DFT, direction), Sec. 3.2 (block size from on-chip limits,
+ * radix schedule), Sec. 3.3 (split into passes).
+ */
+GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
+                             int direction, int precision);
+
+/*
+ * Options for fft_plan_create_ex.  Zero-initialise and set what you need;
+ * a zero field means "library default".
+ *   autotune      1: time candidate radix schedules / tile shapes on this GPU at
+ *                 plan creation and keep the fastest (Sec. 3.2: stage costs are
+ *                 benchmarked, the shortest path over the schedule digraph is
+ *                 taken, then checked against whole-pass timings).
+ *   radix         elements per thread (2, 4, 8 or 16): the largest radix of the
+ *                 on-chip block (Sec. 3.2 "Insights").
+ *   schedule      log2 of the radix of each stage of the first pass, LSB-first
+ *                 nibbles, terminated by a zero nibble; e.g. 0x344 = radix
+ *                 16, 16, 8 (in that order).  Must sum to the pass length.
+ *   max_block_log2  largest on-chip block 2^k (default from shared memory);
+ *                 smaller values force multi-pass splits (testing).
+ *   tile          transforms per thread block for passes that allow a choice.
+ */
+typedef struct {
+  int autotune;
+  int radix;
+  uint32_t schedule;
+  int max_block_log2;
+  int tile;
+  int reserved[8];
+} fft_plan_options_t;
+
+GBFFT_API fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
+                                int direction, int precision,
+                                const fft_plan_options_t* options);
+
+/*
+ * Enqueue the transform of `in` into `out` on `stream` (device pointers, see
+ * the conventions above).  Asynchronous: returns after enqueueing; no host
+ * synchronisation and no allocation.  A plan may be used from several host
+ * threads only on distinct streams and only if no two executions overlap on
+ * the device when the plan has a workspace (multi-pass 1D).
+ * Sec. 3.4 (each pass reads and writes global memory once).
+ */
+GBFFT_API fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream);
+
+/*
+ * Host-memory variant: copy `host_in` (batch transforms, pinned or pageable)
+ * to the device buffer `dev_in`, transform into `dev_out`, copy `dev_out` back
+ * to `host_out`, all on `stream`, split into chunks of whole transforms so that
+ * copies in both directions overlap the kernels.  dev_in / dev_out are caller-
+ * owned device buffers of the full problem size (dev_in may equal dev_out).
+ * Asynchronous like fft_execute; host buffers must stay valid until the stream
+ * reaches this point.  Chunking applies to 1D plans; 2D plans run whole.
+ */
+GBFFT_API fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_out,
+                              void* dev_in, void* dev_out, void* stream);
+
+/* Release the plan, its tables and workspace.  Null is accepted. */
+GBFFT_API fft_status_t fft_plan_destroy(fft_plan_t plan);
+
+/* Bytes of device workspace owned by the plan (0 for single-pass plans). */
+GBFFT_API fft_status_t fft_plan_workspace_bytes(fft_plan_t plan, size_t* bytes);
+
+/* Kernel launches one fft_execute enqueues. */
+GBFFT_API fft_status_t fft_plan_launch_count(fft_plan_t plan, int* launches);
+
+/*
+ * JSON description of the plan (passes, radix schedules, tile shapes, grid,
+ * shared memory) written to buf (NUL-terminated, truncated to len).  Returns
+ * FFT_ERR_INVALID_ARG if buf is too small for the whole text.
+ */
+GBFFT_API fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len);
+
+/*
+ * Same planning as fft_plan_create_ex but for a hypothetical device and with
+ * no CUDA call at all: sm_count and smem_optin_bytes describe the GPU.  Writes
+ * the plan's JSON description.  Lets the planner be checked on a host without
+ * a GPU.
+ */
+GBFFT_API fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batch, int direction,
+                              int precision, const fft_plan_options_t* options, int sm_count,
+                              int smem_optin_bytes, char* buf, size_t len);
+
+/* Wait for the stream-ordered work of the plan's last execute and report any
+ * asynchronous CUDA error it raised. */
+GBFFT_API fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream);
+
+/* Message of the last failure on the calling thread ("" if none). */
+GBFFT_API const char* fft_last_error(void);
+
+/* ------------------------------------------------ schedule model (host) --
+ * Sec. 3.2 "FFT performance model": a radix schedule for N = 2^L is a path in
+ * the digraph whose nodes are stage indices 0..L and whose edge s -> s+log2(r)
+ * means "radix r starting at stage s"; under the stage-independence hypothesis
+ * a schedule costs the sum of its edges' benchmarked costs, and the cheapest
+ * schedule is the shortest source-to-sink path (Dijkstra).
+ *
+ * `radix_logs`  allowed log2(radix) values, e.g. {1, 2, 3} for radices 2, 4, 8.
+ * `cost`        cost[j * log2n + s] = cost of radix 2^radix_logs[j] starting
+ *               at stage s (entries whose edge would overrun the sink are
+ *               ignored; a negative or NaN entry removes that edge).
+ * These functions touch no GPU.
+ */
+
+/* Number of distinct schedules (source-to-sink paths). */
+GBFFT_API fft_status_t fft_schedule_count(int log2n, const int* radix_logs, int n_radix, uint64_t* count);
+
+/* Cheapest schedule: writes its radix logs in stage order to path_logs
+ * (capacity path_cap) and their number to path_len, total to total_cost. */
+GBFFT_API fft_status_t fft_schedule_shortest_path(int log2n, const int* radix_logs, int n_radix,
+                                        const double* cost, int* path_logs, int path_cap,
+                                        int* path_len, double* total_cost);
+
+/* Cost of a given schedule (radix logs in stage order) under the same model. */
+GBFFT_API fft_status_t fft_schedule_path_cost(int log2n, const int* radix_logs, int n_radix,
+                                    const double* cost, const int* path_logs, int path_len,
+                                    double* total_cost);
+
+/* Sec. 3.2 Eq. 1: bandwidth-bound FFT throughput in GFLOP/s (5 N log2 N
+ * convention) for bandwidth `gbs` GB/s when every complex sample of
+ * `bytes_per_sample` bytes crosses the bandwidth-limited link `passes` times
+ * (the paper's form is bytes_per_sample = 8, passes = 1). */
+GBFFT_API double fft_bandwidth_bound_gflops(int64_t n, double gbs, double bytes_per_sample, double passes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFFT_H */

@@ -1,0 +1,416 @@
+// C ABI of the library (include/gbfft.h).  Plans own their device twiddle
+// tables and workspace; fft_execute only enqueues kernels.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gbfft.h"
+#include "autotune.h"
+#include "kernels.h"
+#include "planner.h"
+
+using namespace gbfft;
+
+namespace {
+
+thread_local std::string g_err;
+
+fft_status_t fail(fft_status_t st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+fft_status_t cuda_fail(cudaError_t e, const char* what) {
+  return fail(FFT_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+constexpr uint32_t kMagic = 0x47424646u;  // "GBFF"
+
+}  // namespace
+
+struct fft_plan_s {
+  uint32_t magic = kMagic;
+  int device = -1;
+  PlanSpec spec;
+  Caps caps;
+  void* tables = nullptr;  // cf[spec.table_elems]
+  void* work = nullptr;    // cf[spec.work_elems]
+  std::vector<PassLaunch> launches;  // whole-batch launches, device pointers filled
+  // lazily created resources of fft_execute_host
+  cudaStream_t s_h2d = nullptr, s_k = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_h2d = nullptr, ev_k = nullptr, ev_end = nullptr;
+  std::mutex host_mu;
+};
+
+namespace {
+
+bool plan_ok(fft_plan_t p) { return p && p->magic == kMagic; }
+
+fft_status_t query_caps(Caps& caps, int& device) {
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "no usable CUDA device");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  caps.sm_count = prop.multiProcessorCount;
+  caps.smem_optin = (int)prop.sharedMemPerBlockOptin;
+  caps.max_block = prop.maxThreadsPerBlock;
+  return FFT_OK;
+}
+
+void bind_pointers(fft_plan_t p) {
+  p->launches.clear();
+  const cf* tw = static_cast<const cf*>(p->tables);
+  for (const PassSpec& s : p->spec.passes) {
+    PassLaunch l{};
+    if (s.kind == PASS_FFT) {
+      l.d = pass_desc(s, 0, p->spec.batch, p->spec.batch);
+      l.d.tw = tw;
+      l.d.epi_hi = s.epi ? tw + s.epi_hi_off : nullptr;
+      l.d.epi_lo = s.epi ? tw + s.epi_lo_off : nullptr;
+      l.R = s.R;
+      l.lmap = s.lmap;
+      l.smap = s.smap;
+      l.grid = s.grid;
+      l.block = s.block;
+      l.smem = s.smem;
+    }
+    p->launches.push_back(l);
+  }
+}
+
+void* buf_ptr(fft_plan_t p, int which, const void* in, void* out) {
+  if (which == BUF_IN) return const_cast<void*>(in);
+  if (which == BUF_OUT) return out;
+  return p->work;
+}
+
+int64_t elems_per_batch(const PlanSpec& s) { return s.dims == 1 ? s.n[0] : s.n[0] * s.n[1]; }
+
+// Enqueue all passes for batch entries [b0, b0 + nb) (pointers already offset).
+fft_status_t enqueue(fft_plan_t p, const void* in, void* out, void* work, int64_t b0, int64_t nb,
+                     cudaStream_t st) {
+  if (nb <= 0) return FFT_OK;
+  const int64_t E = elems_per_batch(p->spec);
+  for (size_t i = 0; i < p->spec.passes.size(); ++i) {
+    const PassSpec& s = p->spec.passes[i];
+    const void* src = s.src == BUF_IN ? in : (s.src == BUF_OUT ? (const void*)out : work);
+    void* dst = s.dst == BUF_OUT ? out : work;
+    cudaError_t e;
+    if (s.kind == PASS_COPY) {
+      e = launch_copy(src, dst, nb * E, 1, 1, st);
+    } else {
+      PassLaunch l = p->launches[i];
+      if (b0 != 0 || nb != p->spec.batch) {
+        PassDesc d = pass_desc(s, b0, nb, p->spec.batch);
+        d.tw = l.d.tw;
+        d.epi_hi = l.d.epi_hi;
+        d.epi_lo = l.d.epi_lo;
+        l.d = d;
+        int64_t g = d.tiles;
+        l.grid = (int)std::min<int64_t>(g, 0x7fffffff);
+      }
+      if (l.d.tiles == 0) continue;
+      e = launch_pass(l, src, dst, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  }
+  return FFT_OK;
+}
+
+fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t batch, int direction,
+                        int precision, const fft_plan_options_t* opt) {
+  if (!out) return fail(FFT_ERR_INVALID_ARG, "plan output pointer is null");
+  *out = nullptr;
+  Caps caps;
+  int dev = -1;
+  fft_status_t st = query_caps(caps, dev);
+  if (st != FFT_OK) return st;
+  PlanSpec spec = make_plan(n, dims, batch, direction, precision, opt, caps);
+  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error.c_str());
+  fft_plan_t p = new (std::nothrow) fft_plan_s();
+  if (!p) return fail(FFT_ERR_OUT_OF_MEMORY, "host allocation of the plan failed");
+  p->device = dev;
+  p->caps = caps;
+  p->spec = spec;
+  cudaError_t e;
+  if (spec.table_elems > 0) {
+    e = cudaMalloc(&p->tables, (size_t)spec.table_elems * 8);
+    if (e != cudaSuccess) {
+      delete p;
+      cudaGetLastError();
+      return fail(FFT_ERR_OUT_OF_MEMORY, "twiddle tables: %s", cudaGetErrorString(e));
+    }
+  }
+  if (spec.work_elems > 0) {
+    e = cudaMalloc(&p->work, (size_t)spec.work_elems * 8);
+    if (e != cudaSuccess) {
+      cudaFree(p->tables);
+      delete p;
+      cudaGetLastError();
+      return fail(FFT_ERR_OUT_OF_MEMORY, "workspace of %lld bytes: %s",
+                  (long long)spec.work_elems * 8, cudaGetErrorString(e));
+    }
+  }
+  for (const TwSegment& t : spec.tables) {
+    e = launch_twiddle_gen(static_cast<cf*>(p->tables) + t.off, t.count, t.den, t.mode, t.r,
+                           t.mult, 0);
+    if (e != cudaSuccess) {
+      fft_plan_destroy(p);
+      return cuda_fail(e, "twiddle generation");
+    }
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    fft_plan_destroy(p);
+    return cuda_fail(e, "twiddle generation");
+  }
+  bind_pointers(p);
+  if (opt && opt->autotune) {
+    st = autotune_plan(p->spec, p->caps, p->tables, p->work);
+    if (st != FFT_OK) {
+      std::string msg = g_err;
+      fft_plan_destroy(p);
+      g_err = msg;
+      return st;
+    }
+    bind_pointers(p);
+  }
+  *out = p;
+  return FFT_OK;
+}
+
+}  // namespace
+
+// Used by autotune.cpp to report failures through fft_last_error.
+namespace gbfft {
+fft_status_t set_error(fft_status_t st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace gbfft
+
+extern "C" {
+
+fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
+                             int direction, int precision) {
+  return build_plan(plan, n, dims, batch, direction, precision, nullptr);
+}
+
+fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
+                                int direction, int precision, const fft_plan_options_t* options) {
+  return build_plan(plan, n, dims, batch, direction, precision, options);
+}
+
+fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  if (plan->spec.batch == 0) return FFT_OK;
+  if (!in || !out) return fail(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7))
+    return fail(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned (complex64)");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != plan->device)
+    return fail(FFT_ERR_BAD_PLAN, "plan was created on device %d, current device is %d",
+                plan->device, dev);
+  return enqueue(plan, in, out, plan->work, 0, plan->spec.batch,
+                 static_cast<cudaStream_t>(stream));
+}
+
+fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_out, void* dev_in,
+                              void* dev_out, void* stream) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  const PlanSpec& s = plan->spec;
+  if (s.batch == 0) return FFT_OK;
+  if (!host_in || !host_out || !dev_in || !dev_out)
+    return fail(FFT_ERR_INVALID_ARG, "null buffer");
+  if (((uintptr_t)dev_in & 7) || ((uintptr_t)dev_out & 7))
+    return fail(FFT_ERR_INVALID_ARG, "device buffers must be 8-byte aligned");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != plan->device) return fail(FFT_ERR_BAD_PLAN, "plan/device mismatch");
+  std::lock_guard<std::mutex> lock(plan->host_mu);
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  if (!plan->s_h2d) {
+    const unsigned fl = cudaStreamNonBlocking;
+    if ((e = cudaStreamCreateWithFlags(&plan->s_h2d, fl)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&plan->s_k, fl)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&plan->s_d2h, fl)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&plan->ev_h2d, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&plan->ev_k, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&plan->ev_end, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "stream/event creation for host execution");
+  }
+  const int64_t E = elems_per_batch(s);
+  const size_t per = (size_t)E * 8;
+  // chunks of whole batch entries, about 32 MiB each (1D only; 2D runs whole)
+  int64_t chunk = s.batch;
+  if (s.dims == 1) chunk = std::max<int64_t>(1, (int64_t)((32u << 20) / per));
+  chunk = std::min(chunk, s.batch);
+  if ((e = cudaEventRecord(plan->ev_start, user)) != cudaSuccess) return cuda_fail(e, "record");
+  cudaStreamWaitEvent(plan->s_h2d, plan->ev_start, 0);
+  cudaStreamWaitEvent(plan->s_k, plan->ev_start, 0);
+  cudaStreamWaitEvent(plan->s_d2h, plan->ev_start, 0);
+  const char* hi = static_cast<const char*>(host_in);
+  char* ho = static_cast<char*>(host_out);
+  char* di = static_cast<char*>(dev_in);
+  char* dout = static_cast<char*>(dev_out);
+  char* wk = static_cast<char*>(plan->work);
+  for (int64_t b0 = 0; b0 < s.batch; b0 += chunk) {
+    const int64_t nb = std::min(chunk, s.batch - b0);
+    const size_t off = (size_t)b0 * per, bytes = (size_t)nb * per;
+    if ((e = cudaMemcpyAsync(di + off, hi + off, bytes, cudaMemcpyHostToDevice, plan->s_h2d)) !=
+        cudaSuccess)
+      return cuda_fail(e, "host-to-device copy");
+    cudaEventRecord(plan->ev_h2d, plan->s_h2d);
+    cudaStreamWaitEvent(plan->s_k, plan->ev_h2d, 0);
+    fft_status_t st = enqueue(plan, di + off, dout + off, wk ? wk + off : nullptr, b0, nb, plan->s_k);
+    if (st != FFT_OK) return st;
+    cudaEventRecord(plan->ev_k, plan->s_k);
+    cudaStreamWaitEvent(plan->s_d2h, plan->ev_k, 0);
+    if ((e = cudaMemcpyAsync(ho + off, dout + off, bytes, cudaMemcpyDeviceToHost, plan->s_d2h)) !=
+        cudaSuccess)
+      return cuda_fail(e, "device-to-host copy");
+  }
+  cudaEventRecord(plan->ev_end, plan->s_d2h);
+  if ((e = cudaStreamWaitEvent(user, plan->ev_end, 0)) != cudaSuccess)
+    return cuda_fail(e, "join");
+  return FFT_OK;
+}
+
+fft_status_t fft_plan_destroy(fft_plan_t plan) {
+  if (!plan) return FFT_OK;
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "destroyed or foreign plan");
+  plan->magic = 0;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != plan->device && plan->device >= 0) cudaSetDevice(plan->device);
+  if (plan->s_h2d) {
+    cudaStreamSynchronize(plan->s_h2d);
+    cudaStreamSynchronize(plan->s_k);
+    cudaStreamSynchronize(plan->s_d2h);
+    cudaStreamDestroy(plan->s_h2d);
+    cudaStreamDestroy(plan->s_k);
+    cudaStreamDestroy(plan->s_d2h);
+    cudaEventDestroy(plan->ev_start);
+    cudaEventDestroy(plan->ev_h2d);
+    cudaEventDestroy(plan->ev_k);
+    cudaEventDestroy(plan->ev_end);
+  }
+  if (plan->tables) cudaFree(plan->tables);
+  if (plan->work) cudaFree(plan->work);
+  if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+  delete plan;
+  return FFT_OK;
+}
+
+fft_status_t fft_plan_workspace_bytes(fft_plan_t plan, size_t* bytes) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  if (!bytes) return fail(FFT_ERR_INVALID_ARG, "bytes is null");
+  *bytes = (size_t)plan->spec.work_elems * 8;
+  return FFT_OK;
+}
+
+fft_status_t fft_plan_launch_count(fft_plan_t plan, int* launches) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  if (!launches) return fail(FFT_ERR_INVALID_ARG, "launches is null");
+  *launches = plan->spec.batch == 0 ? 0 : (int)plan->spec.passes.size();
+  return FFT_OK;
+}
+
+static fft_status_t copy_text(const std::string& t, char* buf, size_t len) {
+  if (!buf || len == 0) return fail(FFT_ERR_INVALID_ARG, "buffer is null or empty");
+  size_t n = std::min(len - 1, t.size());
+  memcpy(buf, t.data(), n);
+  buf[n] = 0;
+  if (t.size() >= len) return fail(FFT_ERR_INVALID_ARG, "buffer too small (%zu bytes needed)",
+                                   t.size() + 1);
+  return FFT_OK;
+}
+
+fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  return copy_text(describe(plan->spec), buf, len);
+}
+
+fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batch, int direction,
+                              int precision, const fft_plan_options_t* options, int sm_count,
+                              int smem_optin_bytes, char* buf, size_t len) {
+  if (sm_count <= 0 || smem_optin_bytes <= 0)
+    return fail(FFT_ERR_INVALID_ARG, "device description must be positive");
+  Caps caps;
+  caps.sm_count = sm_count;
+  caps.smem_optin = smem_optin_bytes;
+  PlanSpec spec = make_plan(n, dims, batch, direction, precision, options, caps);
+  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error.c_str());
+  return copy_text(describe(spec), buf, len);
+}
+
+fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronisation");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "asynchronous error");
+  return FFT_OK;
+}
+
+const char* fft_last_error(void) { return g_err.c_str(); }
+
+fft_status_t fft_schedule_count(int log2n, const int* radix_logs, int n_radix, uint64_t* count) {
+  if (log2n < 0 || log2n > 60 || !radix_logs || n_radix <= 0 || !count)
+    return fail(FFT_ERR_INVALID_ARG, "bad schedule-count arguments");
+  *count = count_schedules(log2n, radix_logs, n_radix);
+  return FFT_OK;
+}
+
+fft_status_t fft_schedule_shortest_path(int log2n, const int* radix_logs, int n_radix,
+                                        const double* cost, int* path_logs, int path_cap,
+                                        int* path_len, double* total_cost) {
+  if (log2n < 1 || !radix_logs || n_radix <= 0 || !cost || !path_logs || !path_len ||
+      !total_cost)
+    return fail(FFT_ERR_INVALID_ARG, "bad shortest-path arguments");
+  std::vector<int> path;
+  double total = 0;
+  if (!shortest_schedule(log2n, radix_logs, n_radix, cost, path, total))
+    return fail(FFT_ERR_INVALID_ARG, "no schedule reaches the sink");
+  if ((int)path.size() > path_cap) return fail(FFT_ERR_INVALID_ARG, "path capacity too small");
+  for (size_t i = 0; i < path.size(); ++i) path_logs[i] = path[i];
+  *path_len = (int)path.size();
+  *total_cost = total;
+  return FFT_OK;
+}
+
+fft_status_t fft_schedule_path_cost(int log2n, const int* radix_logs, int n_radix,
+                                    const double* cost, const int* path_logs, int path_len,
+                                    double* total_cost) {
+  if (log2n < 1 || !radix_logs || n_radix <= 0 || !cost || !path_logs || path_len <= 0 ||
+      !total_cost)
+    return fail(FFT_ERR_INVALID_ARG, "bad path-cost arguments");
+  double t = 0;
+  if (!schedule_cost(log2n, radix_logs, n_radix, cost, path_logs, path_len, t))
+    return fail(FFT_ERR_INVALID_ARG, "path is not a source-to-sink schedule");
+  *total_cost = t;
+  return FFT_OK;
+}
+
+double fft_bandwidth_bound_gflops(int64_t n, double gbs, double bytes_per_sample, double passes) {
+  if (n < 2 || gbs <= 0 || bytes_per_sample <= 0 || passes <= 0) return 0.0;
+  double lg = 0;
+  for (int64_t v = n; v > 1; v >>= 1) lg += 1;
+  // samples per second the link sustains times the flops each sample carries
+  return 5.0 * (double)n * lg * gbs / (bytes_per_sample * passes * (double)n);
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Per-thread building blocks of the Stockham pass kernel.
+//
+// The method (Bergach et al.): each transform -- or each column/row of a
+// multi-pass split -- is computed by one on-chip block that holds the whole
+// sequence (Sec. 3.4: one FFT per compute unit, global memory touched only at
+// the first read and the last write); inside the block the transform runs as a
+// sequence of radix stages (Sec. 2.1, mixed radix; Sec. 3.2, radix clustering)
+// separated by a barrier (Sec. 3.2 "FFT performance model").  Sizes that do
+// not fit one block are split into passes joined by twiddle multiplies and a
+// transpose (Sec. 3.3, Sec. 3.4).
+//
+// Stage formulation (Stockham autosort, natural order in and out): for a stage
+// of radix r after stages whose radices multiply to Ns, butterfly jb
+// (0 <= jb < L/r) reads elements jb + i*L/r (i < r), multiplies element i by
+// w_{Ns*r}^{i*k} with k = jb mod Ns, takes a length-r DFT and writes element i
+// to (jb - k)*r + k + i*Ns.
+//
+// Everything here compiles both for the GPU (nvcc) and for a host compiler,
+// so the test harness can replay a pass's exact index arithmetic on the CPU
+// and check every access against its buffer before a kernel runs.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define GB_HD __host__ __device__ __forceinline__
+#define GB_UNROLL _Pragma("unroll")
+#else
+#define GB_HD inline
+#define GB_UNROLL
+#endif
+
+namespace gbfft {
+
+struct alignas(8) cf {
+  float x, y;
+};
+
+GB_HD cf mk(float x, float y) { cf r; r.x = x; r.y = y; return r; }
+GB_HD cf cadd(cf a, cf b) { return mk(a.x + b.x, a.y + b.y); }
+GB_HD cf csub(cf a, cf b) { return mk(a.x - b.x, a.y - b.y); }
+GB_HD cf cmul(cf a, cf b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+GB_HD cf cconj(cf a) { return mk(a.x, -a.y); }
+
+// cos(pi/8), sin(pi/8), sqrt(2)/2 rounded to FP32.
+#define GB_C8 0.92387953251128674f
+#define GB_S8 0.38268343236508977f
+#define GB_H2 0.70710678118654752f
+
+// a * w16^m, w16 = exp(-2 pi i / 16).  Quarter turns are exact swaps and
+// sign flips; odd multiples of an eighth turn cost two multiplies.
+GB_HD cf mul_w16(cf a, int m) {
+  switch (m & 15) {
+    case 0: return a;
+    case 4: return mk(a.y, -a.x);
+    case 8: return mk(-a.x, -a.y);
+    case 12: return mk(-a.y, a.x);
+    case 2: return mk(GB_H2 * (a.x + a.y), GB_H2 * (a.y - a.x));
+    case 6: return mk(GB_H2 * (a.y - a.x), -GB_H2 * (a.x + a.y));
+    case 10: return mk(-GB_H2 * (a.x + a.y), GB_H2 * (a.x - a.y));
+    case 14: return mk(GB_H2 * (a.x - a.y), GB_H2 * (a.x + a.y));
+    case 1: return cmul(a, mk(GB_C8, -GB_S8));
+    case 3: return cmul(a, mk(GB_S8, -GB_C8));
+    case 5: return cmul(a, mk(-GB_S8, -GB_C8));
+    case 7: return cmul(a, mk(-GB_C8, -GB_S8));
+    case 9: return cmul(a, mk(-GB_C8, GB_S8));
+    case 11: return cmul(a, mk(-GB_S8, GB_C8));
+    case 13: return cmul(a, mk(GB_S8, GB_C8));
+    default: return cmul(a, mk(GB_C8, GB_S8));  // 15
+  }
+}
+
+// Forward DFT of length P in {1, 2, 4} on v[0], v[S], ..., natural order.
+template <int P, int S>
+GB_HD void dft_small(cf* v) {
+  if (P == 2) {
+    cf a = v[0], b = v[S];
+    v[0] = cadd(a, b);
+    v[S] = csub(a, b);
+  } else if (P == 4) {
+    cf a0 = v[0], a1 = v[S], a2 = v[2 * S], a3 = v[3 * S];
+    cf t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    cf t2 = cadd(a1, a3), t3 = csub(a1, a3);
+    t3 = mk(t3.y, -t3.x);  // * (-i)
+    v[0] = cadd(t0, t2);
+    v[2 * S] = csub(t0, t2);
+    v[S] = cadd(t1, t3);
+    v[3 * S] = csub(t1, t3);
+  }
+}
+
+// Forward DFT of length N = P*Q in registers, natural order in and out.
+// Index split n = Q*n1 + n2, k = k1 + P*k2: length-P DFTs over n1, twiddle
+// w_N^{n2*k1}, length-Q DFTs over n2 (Cooley-Tukey), then the output
+// permutation, which after unrolling is only a renaming of registers.
+template <int P, int Q>
+GB_HD void dft_pq(cf* v) {
+  constexpr int N = P * Q;
+GB_UNROLL
+  for (int n2 = 0; n2 < Q; ++n2) dft_small<P, Q>(v + n2);
+GB_UNROLL
+  for (int k1 = 1; k1 < P; ++k1)
+GB_UNROLL
+    for (int n2 = 1; n2 < Q; ++n2)
+      v[Q * k1 + n2] = mul_w16(v[Q * k1 + n2], (n2 * k1 * (16 / N)) & 15);
+GB_UNROLL
+  for (int k1 = 0; k1 < P; ++k1) dft_small<Q, 1>(v + Q * k1);
+  cf t[N];
+GB_UNROLL
+  for (int k1 = 0; k1 < P; ++k1)
+GB_UNROLL
+    for (int k2 = 0; k2 < Q; ++k2) t[k1 + P * k2] = v[Q * k1 + k2];
+GB_UNROLL
+  for (int i = 0; i < N; ++i) v[i] = t[i];
+}
+
+template <int RR>
+GB_HD void dft_radix(cf* v) {
+  if (RR == 2) dft_small<2, 1>(v);
+  else if (RR == 4) dft_small<4, 1>(v);
+  else if (RR == 8) dft_pq<2, 4>(v);
+  else if (RR == 16) dft_pq<4, 4>(v);
+}
+
+// ---------------------------------------------------------------- layout --
+
+enum { MAP_ROWS = 0, MAP_COLS = 1 };
+
+// One pass = a batch of length-L transforms grouped G to a thread block
+// ("tile").  Element a of transform g of tile (outer, inner) lives at
+//   outer*o + inner*t + g*gs + a*e        (separately for input and output).
+struct Strides {
+  int64_t o, t, g, e;
+};
+
+struct PassDesc {
+  int32_t logL;        // L = 2^logL, 1 <= L <= 2^14
+  int32_t nst;         // number of radix stages
+  int32_t rlog[15];    // log2 of each stage's radix (1..4)
+  int32_t tw_off[15];  // stage s twiddles start at tw + tw_off[s]: [k][i], Ns*r entries
+  int32_t G;           // transforms per tile
+  int32_t T;           // threads per transform = L / R
+  int32_t pitch;       // shared-memory pitch per transform (row layout)
+  int32_t smem_elems;  // shared-memory complex elements used
+  int64_t tiles;       // tiles in the whole pass
+  int64_t tiles_inner; // tiles per outer index
+  int64_t count_inner; // valid transforms per outer index (ragged last tile)
+  Strides in, out;
+  int32_t conj_in, conj_out;  // backward transform = conj(forward(conj(x)))
+  int32_t epi;                // 1: multiply output (n2, k1) by w_N^{n2*k1}
+  int32_t epi_lo_bits;        // w_N^m = hi[m >> lo_bits] * lo[m & (2^lo_bits - 1)]
+  const cf* tw;
+  const cf* epi_hi;
+  const cf* epi_lo;
+};
+
+GB_HD void thread_coords(int map, int tid, int T, int G, int& g, int& t) {
+  if (map == MAP_ROWS) { g = tid / T; t = tid - g * T; }
+  else { t = tid / G; g = tid - t * G; }
+}
+
+// Shared-memory slot of element a of transform g.  Row layout: a padding
+// slot every 16 elements plus a per-transform offset (pitch); column layout:
+// transforms interleaved, a padding slot every 16.  Both keep the Stockham
+// reads and writes free of bank conflicts for the tile shapes the planner
+// emits.
+GB_HD int smem_slot(int layout, int g, int a, int G, int pitch) {
+  if (layout == MAP_ROWS) return g * pitch + a + (a >> 4);
+  int s = a * G + g;
+  return s + (s >> 4);
+}
+
+GB_HD int64_t elem_offset(const Strides& s, int64_t outer, int64_t inner, int g, int64_t a) {
+  return outer * s.o + inner * s.t + (int64_t)g * s.g + a * s.e;
+}
+
+}  // namespace gbfft

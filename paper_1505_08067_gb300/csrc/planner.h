@@ -1,0 +1,99 @@
+// Host-side planning: turns (n, dims, batch, direction) and the GPU's limits
+// into a list of passes.  No CUDA calls here, so the planner runs on any host.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gbfft.h"
+#include "fft_core.h"
+
+namespace gbfft {
+
+enum { BUF_IN = 0, BUF_OUT = 1, BUF_WORK = 2 };
+enum { PASS_FFT = 0, PASS_COPY = 1 };
+
+struct Caps {
+  int sm_count = 152;
+  int smem_optin = 232448;  // bytes of dynamic shared memory a block may opt into
+  int max_block = 1024;
+};
+
+struct PassSpec {
+  int kind = PASS_FFT;
+  int logL = 0;
+  int R = 1;
+  int G = 1;
+  int lmap = MAP_ROWS, smap = MAP_ROWS;
+  std::vector<int> rlogs;      // radix schedule, stage order
+  int64_t tiles = 0, tiles_inner = 1, count_inner = 0;
+  int64_t outer = 1;           // number of outer indices (batch of a multi-pass plan)
+  Strides in{}, out{};
+  int src = BUF_IN, dst = BUF_OUT;
+  int conj_in = 0, conj_out = 0;
+  int epi = 0, epi_logN = 0, epi_lo_bits = 0;
+  int block = 0;
+  int pitch = 0;
+  int smem_elems = 0;
+  size_t smem = 0;
+  int grid = 0;
+  bool batch_is_tiles = false;  // contiguous pass: batch maps to tiles of G transforms
+  int64_t units_per_batch = 1;  // contiguous pass: transforms per batch entry
+  // PASS_COPY
+  int64_t copy_count = 0, copy_in_stride = 1, copy_out_stride = 1;
+  // twiddle-table offsets (complex entries) inside the plan's table allocation
+  std::vector<int32_t> tw_off;  // per stage (stage 0 unused)
+  int64_t epi_hi_off = 0, epi_lo_off = 0;
+};
+
+struct TwSegment {  // one twiddle_gen launch
+  int64_t off, count, den, mult;
+  int mode, r;
+};
+
+struct PlanSpec {
+  int dims = 1;
+  int64_t n[2] = {1, 1};
+  int64_t batch = 0;
+  int direction = FFT_FORWARD;
+  int precision = FFT_PREC_FP32;
+  int max_block_log2 = 14;
+  std::vector<PassSpec> passes;
+  std::vector<TwSegment> tables;
+  int64_t table_elems = 0;
+  int64_t work_elems = 0;
+  fft_status_t status = FFT_OK;
+  std::string error;
+};
+
+// Largest on-chip block 2^k for these limits: the shared-memory exchange
+// buffer (with its padding) must fit one block, and at most 1024 threads of
+// 16 elements each hold it.
+int block_log2_limit(const Caps& caps);
+
+// Default radix schedule of a length-2^logL pass with 2^logR elements per
+// thread: as many full-radix stages as fit, the remainder radix last.
+std::vector<int> default_schedule(int logL, int logR);
+
+PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int precision,
+                   const fft_plan_options_t* opt, const Caps& caps);
+
+// Rebuild one pass for a different radix / schedule / tile (autotuner); keeps
+// geometry.  Returns false if the combination is invalid.
+bool reshape_pass(PassSpec& p, int R, const std::vector<int>& rlogs, int G, const Caps& caps);
+
+// Fill PassDesc (without device pointers) for a pass restricted to
+// batch entries [b0, b0 + nb).
+PassDesc pass_desc(const PassSpec& p, int64_t b0, int64_t nb, int64_t n_total);
+
+std::string describe(const PlanSpec& s);
+
+// Schedule digraph (Sec. 3.2).
+uint64_t count_schedules(int log2n, const int* radix_logs, int n_radix);
+bool shortest_schedule(int log2n, const int* radix_logs, int n_radix, const double* cost,
+                       std::vector<int>& path, double& total);
+bool schedule_cost(int log2n, const int* radix_logs, int n_radix, const double* cost,
+                   const int* path, int len, double& total);
+
+}  // namespace gbfft

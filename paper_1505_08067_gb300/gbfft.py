@@ -1,0 +1,306 @@
+"""Thin ctypes binding of ``libgbfft.so`` (C ABI in ``include/gbfft.h``).
+
+Argument marshalling only: every transform runs in the library's CUDA kernels.
+The functions keep the C names (``fft_plan_create``, ``fft_execute``, ...);
+``Plan`` wraps them for torch tensors (torch is used for device memory and
+streams only).  If the shared library has not been built the first call raises
+``RuntimeError``; there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgbfft.so")
+
+FFT_OK = 0
+FFT_ERR_INVALID_ARG = 1
+FFT_ERR_UNSUPPORTED_SIZE = 2
+FFT_ERR_OUT_OF_MEMORY = 3
+FFT_ERR_CUDA = 4
+FFT_ERR_TIMEOUT = 5
+FFT_ERR_BAD_PLAN = 6
+FFT_ERR_NOT_IMPLEMENTED = 7
+STATUS_NAMES = {0: "FFT_OK", 1: "FFT_ERR_INVALID_ARG", 2: "FFT_ERR_UNSUPPORTED_SIZE",
+                3: "FFT_ERR_OUT_OF_MEMORY", 4: "FFT_ERR_CUDA", 5: "FFT_ERR_TIMEOUT",
+                6: "FFT_ERR_BAD_PLAN", 7: "FFT_ERR_NOT_IMPLEMENTED"}
+FFT_FORWARD = -1
+FFT_INVERSE = +1
+FFT_PREC_FP32 = 0
+FFT_PREC_TC_FP16 = 1
+FFT_PREC_TC_BF16 = 2
+FFT_PREC_TC_BF16X3 = 3
+
+
+class GbfftError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class fft_plan_options_t(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int), ("radix", ctypes.c_int),
+                ("schedule", ctypes.c_uint32), ("max_block_log2", ctypes.c_int),
+                ("tile", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_SIGS = {
+    "fft_plan_create": [ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.c_int, _i64, ctypes.c_int,
+                        ctypes.c_int],
+    "fft_plan_create_ex": [ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.c_int, _i64,
+                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(fft_plan_options_t)],
+    "fft_execute": [_vp, _vp, _vp, _vp],
+    "fft_execute_host": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "fft_plan_destroy": [_vp],
+    "fft_plan_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "fft_plan_launch_count": [_vp, ctypes.POINTER(ctypes.c_int)],
+    "fft_plan_describe": [_vp, ctypes.c_char_p, ctypes.c_size_t],
+    "fft_plan_dry_run": [ctypes.POINTER(_i64), ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int,
+                         ctypes.POINTER(fft_plan_options_t), ctypes.c_int, ctypes.c_int,
+                         ctypes.c_char_p, ctypes.c_size_t],
+    "fft_plan_sync_status": [_vp, _vp],
+    "fft_schedule_count": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_uint64)],
+    "fft_schedule_shortest_path": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_double)],
+    "fft_schedule_path_cost": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                               ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
+}
+
+
+def load():
+    """Open libgbfft.so (built by ``paper_1505_08067_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.fft_last_error.argtypes = []
+    lib.fft_last_error.restype = ctypes.c_char_p
+    lib.fft_bandwidth_bound_gflops.argtypes = [_i64, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double]
+    lib.fft_bandwidth_bound_gflops.restype = ctypes.c_double
+    _lib = lib
+    return lib
+
+
+def fft_last_error() -> str:
+    return load().fft_last_error().decode()
+
+
+def _check(status: int) -> None:
+    if status != FFT_OK:
+        raise GbfftError(status, fft_last_error())
+
+
+def _shape(n) -> tuple:
+    return tuple(int(v) for v in (n if isinstance(n, (tuple, list)) else (n,)))
+
+
+def _options(opts: dict) -> fft_plan_options_t:
+    o = fft_plan_options_t()
+    for k, v in opts.items():
+        if k not in ("autotune", "radix", "schedule", "max_block_log2", "tile"):
+            raise TypeError(f"unknown plan option {k!r}")
+        setattr(o, k, int(v))
+    return o
+
+
+# ------------------------------------------------------------ C-named API --
+
+def fft_plan_create(n, batch: int, direction: int = FFT_FORWARD,
+                    precision: int = FFT_PREC_FP32, **options) -> int:
+    """Returns the opaque plan handle (an integer)."""
+    shape = _shape(n)
+    arr = (_i64 * len(shape))(*shape)
+    h = _vp()
+    if options:
+        o = _options(options)
+        _check(load().fft_plan_create_ex(ctypes.byref(h), arr, len(shape), int(batch), direction,
+                                         precision, ctypes.byref(o)))
+    else:
+        _check(load().fft_plan_create(ctypes.byref(h), arr, len(shape), int(batch), direction,
+                                      precision))
+    return h.value
+
+
+def fft_execute(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().fft_execute(plan, in_ptr, out_ptr, stream))
+
+
+def fft_execute_host(plan: int, host_in: int, host_out: int, dev_in: int, dev_out: int,
+                     stream: int = 0) -> None:
+    _check(load().fft_execute_host(plan, host_in, host_out, dev_in, dev_out, stream))
+
+
+def fft_plan_destroy(plan: int) -> None:
+    _check(load().fft_plan_destroy(plan))
+
+
+def fft_plan_workspace_bytes(plan: int) -> int:
+    v = ctypes.c_size_t()
+    _check(load().fft_plan_workspace_bytes(plan, ctypes.byref(v)))
+    return v.value
+
+
+def fft_plan_launch_count(plan: int) -> int:
+    v = ctypes.c_int()
+    _check(load().fft_plan_launch_count(plan, ctypes.byref(v)))
+    return v.value
+
+
+def fft_plan_describe(plan: int) -> dict:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().fft_plan_describe(plan, buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+def fft_plan_dry_run(n, batch: int, direction: int = FFT_FORWARD, precision: int = FFT_PREC_FP32,
+                     sm_count: int = 152, smem_optin_bytes: int = 232448, **options) -> dict:
+    shape = _shape(n)
+    arr = (_i64 * len(shape))(*shape)
+    o = _options(options)
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().fft_plan_dry_run(arr, len(shape), int(batch), direction, precision,
+                                   ctypes.byref(o), sm_count, smem_optin_bytes, buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+def fft_plan_sync_status(plan: int, stream: int = 0) -> None:
+    _check(load().fft_plan_sync_status(plan, stream))
+
+
+def _cost_arrays(log2n, radix_logs, cost):
+    rl = (ctypes.c_int * len(radix_logs))(*radix_logs)
+    flat = [float(cost[j][s]) if s < len(cost[j]) else -1.0
+            for j in range(len(radix_logs)) for s in range(log2n)]
+    return rl, (ctypes.c_double * len(flat))(*flat)
+
+
+def fft_schedule_count(log2n: int, radix_logs: Sequence[int]) -> int:
+    rl = (ctypes.c_int * len(radix_logs))(*radix_logs)
+    v = ctypes.c_uint64()
+    _check(load().fft_schedule_count(log2n, rl, len(radix_logs), ctypes.byref(v)))
+    return v.value
+
+
+def fft_schedule_shortest_path(log2n: int, radix_logs: Sequence[int], cost):
+    """cost[j][s]: cost of radix 2**radix_logs[j] starting at stage s (None/-1 = no edge).
+    Returns (list of radices in stage order, total cost)."""
+    rl, c = _cost_arrays(log2n, radix_logs, [[-1.0 if v is None else v for v in row] for row in cost])
+    path = (ctypes.c_int * 64)()
+    ln = ctypes.c_int()
+    tot = ctypes.c_double()
+    _check(load().fft_schedule_shortest_path(log2n, rl, len(radix_logs), c, path, 64,
+                                             ctypes.byref(ln), ctypes.byref(tot)))
+    return [1 << path[i] for i in range(ln.value)], tot.value
+
+
+def fft_schedule_path_cost(log2n: int, radix_logs: Sequence[int], cost, radices: Sequence[int]):
+    rl, c = _cost_arrays(log2n, radix_logs, [[-1.0 if v is None else v for v in row] for row in cost])
+    logs = [int(r).bit_length() - 1 for r in radices]
+    p = (ctypes.c_int * len(logs))(*logs)
+    tot = ctypes.c_double()
+    _check(load().fft_schedule_path_cost(log2n, rl, len(radix_logs), c, p, len(logs),
+                                         ctypes.byref(tot)))
+    return tot.value
+
+
+def fft_bandwidth_bound_gflops(n: int, gbs: float, bytes_per_sample: float = 8.0,
+                               passes: float = 1.0) -> float:
+    return load().fft_bandwidth_bound_gflops(int(n), gbs, bytes_per_sample, passes)
+
+
+# ------------------------------------------------------- torch convenience --
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A plan for ``batch`` transforms of shape ``n`` (int for 1D, (rows, cols) for 2D)."""
+
+    def __init__(self, n, batch: int, direction: int = FFT_FORWARD,
+                 precision: int = FFT_PREC_FP32, **options):
+        self.shape = _shape(n)
+        self.batch = int(batch)
+        self.direction = direction
+        self.handle: Optional[int] = fft_plan_create(self.shape, self.batch, direction, precision,
+                                                     **options)
+
+    @property
+    def elements(self) -> int:
+        e = self.batch
+        for v in self.shape:
+            e *= v
+        return e
+
+    def _check_tensor(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64:
+            raise TypeError(f"{name} must be a CUDA complex64 tensor")
+        if not t.is_contiguous() or t.numel() != self.elements:
+            raise ValueError(f"{name} must be contiguous with {self.elements} elements")
+
+    def execute(self, x, out=None, stream=None):
+        """Enqueue the transform of tensor ``x`` into ``out`` (allocated if None)."""
+        import torch
+        self._check_tensor(x, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "output")
+        fft_execute(self.handle, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def execute_host(self, host_in, host_out, dev_in, dev_out, stream=None):
+        """Host -> device -> transform -> host, pipelined in chunks (torch tensors)."""
+        fft_execute_host(self.handle, host_in.data_ptr(), host_out.data_ptr(), dev_in.data_ptr(),
+                         dev_out.data_ptr(), _stream_handle(stream))
+
+    def describe(self) -> dict:
+        return fft_plan_describe(self.handle)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return fft_plan_workspace_bytes(self.handle)
+
+    @property
+    def launch_count(self) -> int:
+        return fft_plan_launch_count(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            fft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

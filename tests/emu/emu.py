@@ -1,0 +1,59 @@
+"""Loader for the CPU replay harness (test infrastructure, see emu_harness.cpp)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+CSRC = os.path.join(ROOT, "paper_1505_08067_gb300", "csrc")
+LIB = os.path.join(HERE, "_emu.so")
+SRCS = [os.path.join(HERE, "emu_harness.cpp"), os.path.join(CSRC, "planner.cpp")]
+DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "planner.h")] + \
+    [os.path.join(ROOT, "include", "gbfft.h")]
+_lib = None
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int), ("radix", ctypes.c_int), ("schedule", ctypes.c_uint32),
+                ("max_block_log2", ctypes.c_int), ("tile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(p) for p in DEPS):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-shared", "-fPIC",
+                        "-Wno-unknown-pragmas", "-I" + CSRC, "-I" + os.path.join(ROOT, "include"),
+                        "-o", tmp] + SRCS, check=True)
+        os.replace(tmp, LIB)
+    lib = ctypes.CDLL(LIB)
+    lib.emu_run.restype = ctypes.c_int64
+    lib.emu_run.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int64,
+                            ctypes.c_int, ctypes.POINTER(Options), ctypes.c_int,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]
+    _lib = lib
+    return lib
+
+
+def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, **opts):
+    """Replay the planned passes for complex64 input x of shape (batch, *shape)."""
+    lib = load()
+    x = np.ascontiguousarray(x, dtype=np.complex64)
+    dims = len(shape)
+    n = (ctypes.c_int64 * 2)(*shape, *([1] * (2 - dims)))
+    batch = x.size // int(np.prod(shape)) if np.prod(shape) else 0
+    out = np.zeros_like(x)
+    o = Options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    msg = ctypes.create_string_buffer(512)
+    nerr = lib.emu_run(n, dims, batch, direction, ctypes.byref(o), smem_optin,
+                       x.ctypes.data, out.ctypes.data, msg, 512)
+    return out, int(nerr), msg.value.decode()

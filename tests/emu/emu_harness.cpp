@@ -1,0 +1,204 @@
+// Test infrastructure: replays the GPU pass kernel's per-thread phases on the
+// CPU, thread by thread, exactly as planned by the library's planner, with a
+// memory policy that checks every access:
+//   - global loads/stores and twiddle loads stay inside their buffers;
+//   - shared-memory slots stay inside the tile's allocation;
+//   - every shared read hits a slot written in the immediately preceding
+//     write phase (no stale read), no slot is written twice in one phase
+//     (no write collision);
+//   - every output element of a pass is written exactly once.
+// It never stands in for the GPU: the library has no CPU path, and the GPU
+// parity tests compare the CUDA kernels with the FP64 oracle.  This harness
+// only lets the index arithmetic be checked before a kernel runs.
+
+#include <array>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "fft_stage.h"
+#include "planner.h"
+
+using namespace gbfft;
+
+namespace {
+
+struct Ctx {
+  const cf* in = nullptr;
+  int64_t in_len = 0;
+  cf* out = nullptr;
+  int64_t out_len = 0;
+  std::vector<uint8_t>* out_hits = nullptr;
+  const cf* tw = nullptr;
+  int64_t tw_len = 0;
+  int smem_len = 0;
+  std::vector<int64_t>* slot_epoch = nullptr;
+  std::vector<int64_t>* slot_write = nullptr;
+  int64_t epoch = 0;
+  int64_t errors = 0;
+  std::string first_error;
+};
+Ctx g;
+
+void err(const char* what, int64_t idx) {
+  if (g.errors++ == 0) {
+    char b[256];
+    snprintf(b, sizeof b, "%s (index %lld)", what, (long long)idx);
+    g.first_error = b;
+  }
+}
+
+struct CheckMem {
+  static cf ldg(const cf* p, int64_t off) {
+    if (p != g.in || off < 0 || off >= g.in_len) { err("global load out of bounds", off); return mk(0, 0); }
+    return p[off];
+  }
+  static void stg(cf* p, int64_t off, cf v) {
+    if (p != g.out || off < 0 || off >= g.out_len) { err("global store out of bounds", off); return; }
+    if ((*g.out_hits)[off]++) err("output element written twice", off);
+    p[off] = v;
+  }
+  static cf ldtw(const cf* p) {
+    int64_t off = p - g.tw;
+    if (off < 0 || off >= g.tw_len) { err("twiddle load out of bounds", off); return mk(1, 0); }
+    return *p;
+  }
+  static cf lds(const cf* s, int i) {
+    if (i < 0 || i >= g.smem_len) { err("shared load out of bounds", i); return mk(0, 0); }
+    if ((*g.slot_epoch)[i] != g.epoch) err("shared load of a slot not written in the last phase", i);
+    return s[i];
+  }
+  static void sts(cf* s, int i, cf v) {
+    if (i < 0 || i >= g.smem_len) { err("shared store out of bounds", i); return; }
+    if ((*g.slot_write)[i] == g.epoch) err("two writes to one shared slot in one phase", i);
+    (*g.slot_write)[i] = g.epoch;
+    (*g.slot_epoch)[i] = g.epoch;
+    s[i] = v;
+  }
+};
+
+// Host twiddles for the harness only (FP64, rounded to FP32).
+cf root(int64_t e, int64_t den) {
+  e %= den;
+  double a = -2.0 * M_PI * (double)e / (double)den;
+  return mk((float)cos(a), (float)sin(a));
+}
+
+template <int R, int LM, int SM>
+void run_pass_t(const PassDesc& d, const cf* in, cf* out) {
+  using B = PassBody<R, LM, SM, CheckMem>;
+  const int nthr = d.G * d.T;
+  std::vector<cf> smem(std::max(1, d.smem_elems));
+  std::vector<int64_t> ep(smem.size(), -1), wr(smem.size(), -1);
+  g.slot_epoch = &ep;
+  g.slot_write = &wr;
+  g.smem_len = d.smem_elems;
+  std::vector<std::array<cf, R>> V(nthr);
+  for (int64_t tile = 0; tile < d.tiles; ++tile) {
+    typename B::Tile tl = B::tile_of(d, tile);
+    ++g.epoch;
+    for (int tid = 0; tid < nthr; ++tid) {
+      cf (&v)[R] = *reinterpret_cast<cf(*)[R]>(V[tid].data());
+      B::first(v, d, in, out, smem.data(), tl, tid);
+    }
+    int Ns = 1 << d.rlog[0];
+    for (int s = 1; s < d.nst; ++s) {
+      for (int tid = 0; tid < nthr; ++tid) {
+        cf (&v)[R] = *reinterpret_cast<cf(*)[R]>(V[tid].data());
+        B::read(v, d, s, Ns, out, smem.data(), tl, tid);
+      }
+      if (s < d.nst - 1) {
+        ++g.epoch;
+        for (int tid = 0; tid < nthr; ++tid) {
+          cf (&v)[R] = *reinterpret_cast<cf(*)[R]>(V[tid].data());
+          B::write(v, d, s, Ns, smem.data(), tid);
+        }
+      }
+      Ns <<= d.rlog[s];
+    }
+  }
+}
+
+template <int LM, int SM>
+void run_maps(int R, const PassDesc& d, const cf* in, cf* out) {
+  switch (R) {
+    case 2: run_pass_t<2, LM, SM>(d, in, out); break;
+    case 4: run_pass_t<4, LM, SM>(d, in, out); break;
+    case 8: run_pass_t<8, LM, SM>(d, in, out); break;
+    case 16: run_pass_t<16, LM, SM>(d, in, out); break;
+    default: err("bad R", R);
+  }
+}
+
+}  // namespace
+
+
+
+extern "C" {
+
+// Plans (n, dims, batch, direction, options) for a device with the given
+// limits, replays every pass on the CPU and writes the result to `out`
+// (complex64, same size as `in`).  Returns the number of access violations;
+// the first one is described in msg.
+int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
+                const fft_plan_options_t* opt, int smem_optin, const float* in_f, float* out_f,
+                char* msg, size_t msg_len) {
+  Caps caps;
+  caps.smem_optin = smem_optin;
+  PlanSpec s = make_plan(n, dims, batch, direction, FFT_PREC_FP32, opt, caps);
+  g = Ctx{};
+  if (s.status != FFT_OK) {
+    snprintf(msg, msg_len, "plan failed: %s", s.error.c_str());
+    return -1;
+  }
+  const int64_t E = (dims == 1 ? n[0] : n[0] * n[1]) * batch;
+  std::vector<cf> tables(std::max<int64_t>(1, s.table_elems));
+  for (const TwSegment& t : s.tables)
+    for (int64_t j = 0; j < t.count; ++j) {
+      int64_t e = t.mode == 0 ? (j / t.r) * (j % t.r) : j * t.mult;
+      tables[t.off + j] = root(e, t.den);
+    }
+  std::vector<cf> work(std::max<int64_t>(1, s.work_elems));
+  const cf* in = reinterpret_cast<const cf*>(in_f);
+  cf* out = reinterpret_cast<cf*>(out_f);
+  for (const PassSpec& p : s.passes) {
+    const cf* src = p.src == BUF_IN ? in : (p.src == BUF_OUT ? out : work.data());
+    cf* dst = p.dst == BUF_OUT ? out : work.data();
+    if (p.kind == PASS_COPY) {
+      for (int64_t i = 0; i < E; ++i) dst[i] = src[i];
+      continue;
+    }
+    PassDesc d = pass_desc(p, 0, batch, batch);
+    d.tw = tables.data();
+    d.epi_hi = tables.data() + p.epi_hi_off;
+    d.epi_lo = tables.data() + p.epi_lo_off;
+    // In-place passes read and write the same buffer: copy the source so the
+    // checker can tell loads from stores.
+    std::vector<cf> src_copy;
+    if (src == dst) {
+      src_copy.assign(src, src + E);
+      src = src_copy.data();
+    }
+    g.in = src;
+    g.in_len = p.src == BUF_WORK ? s.work_elems : E;
+    g.out = dst;
+    g.out_len = p.dst == BUF_WORK ? s.work_elems : E;
+    std::vector<uint8_t> hits(g.out_len, 0);
+    g.out_hits = &hits;
+    g.tw = tables.data();
+    g.tw_len = s.table_elems;
+    if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
+    else if (p.lmap == MAP_COLS && p.smap == MAP_COLS) run_maps<1, 1>(p.R, d, src, dst);
+    else run_maps<0, 1>(p.R, d, src, dst);
+    for (int64_t i = 0; i < g.out_len; ++i)
+      if (hits[i] != 1) { err("output element not written exactly once", i); break; }
+  }
+  snprintf(msg, msg_len, "%s", g.first_error.c_str());
+  return g.errors;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+"""The C ABI without a GPU: the library loads, exports every symbol the header
+declares, plans on a described device, and fails cleanly where a GPU is
+needed.  CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1505_08067_gb300 import gbfft as g
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"GBFFT_API[^;(]*?\b(fft_\w+)\s*\(", txt, re.S))
+    return names
+
+
+def test_header_symbols_exported():
+    lib = ctypes.CDLL(g.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 15
+    for name in sorted(names):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_no_gpu_means_error_not_fallback():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except Exception:
+        pass
+    with pytest.raises(g.GbfftError) as e:
+        g.fft_plan_create(1024, 4)
+    assert e.value.status == g.FFT_ERR_CUDA
+
+
+@pytest.mark.parametrize("n,batch,status", [
+    (12, 1, g.FFT_ERR_UNSUPPORTED_SIZE), (2 ** 25, 1, g.FFT_ERR_UNSUPPORTED_SIZE),
+    (0, 1, g.FFT_ERR_UNSUPPORTED_SIZE), (1024, -1, g.FFT_ERR_INVALID_ARG),
+    ((2 ** 15, 8), 1, g.FFT_ERR_UNSUPPORTED_SIZE), ((3, 8), 1, g.FFT_ERR_UNSUPPORTED_SIZE)])
+def test_dry_run_rejects(n, batch, status):
+    with pytest.raises(g.GbfftError) as e:
+        g.fft_plan_dry_run(n, batch)
+    assert e.value.status == status
+
+
+def test_dry_run_rejects_options():
+    with pytest.raises(g.GbfftError):
+        g.fft_plan_dry_run(1024, 1, radix=3)
+    with pytest.raises(g.GbfftError):
+        g.fft_plan_dry_run(1024, 1, schedule=0x333)     # 8*8*8 != 1024
+    with pytest.raises(g.GbfftError):
+        g.fft_plan_dry_run(1024, 1, precision=9)
+    with pytest.raises(g.GbfftError) as e:
+        g.fft_plan_dry_run(1024, 1, precision=g.FFT_PREC_TC_BF16)
+    assert e.value.status == g.FFT_ERR_NOT_IMPLEMENTED
+
+
+@pytest.mark.parametrize("logn", range(0, 25))
+@pytest.mark.parametrize("batch", [1, 3, 64])
+def test_planner_limits(logn, batch):
+    """Every planned pass respects the device limits and covers its transforms."""
+    smem = 232448
+    d = g.fft_plan_dry_run(2 ** logn, batch, smem_optin_bytes=smem)
+    assert d["max_block_log2"] == 14
+    passes = d["passes"]
+    assert len(passes) == (1 if logn <= 14 else 2)
+    for p in passes:
+        if p["kind"] != "fft":
+            continue
+        assert p["block"] <= 1024 and p["smem"] <= smem
+        assert 1 << sum(r.bit_length() - 1 for r in p["radices"]) == p["L"]
+        assert max(p["radices"]) <= p["R"]
+        assert p["tiles_inner"] * p["G"] >= p["count_inner"]
+    if logn > 14:
+        assert d["workspace_bytes"] == 8 * batch * 2 ** logn
+        p1, p2 = passes
+        assert p1["L"] * p2["L"] == 2 ** logn and p1["epi"] == 1 and p2["smap"] == "cols"
+
+
+def test_sar_frame_plan():
+    d = g.fft_plan_dry_run((4096, 8192), 1)
+    rows, cols = d["passes"]
+    assert rows["L"] == 8192 and rows["count_inner"] == 4096
+    assert cols["L"] == 4096 and cols["lmap"] == "cols" and cols["src"] == cols["dst"] == 1
+    assert d["workspace_bytes"] == 0
+
+
+def test_smaller_device_forces_more_passes():
+    d = g.fft_plan_dry_run(2 ** 14, 1, smem_optin_bytes=48 * 1024)
+    assert d["max_block_log2"] == 12 and len(d["passes"]) == 2

@@ -1,0 +1,67 @@
+"""CPU replay of the planned GPU passes (tests/emu): every access in bounds, no
+stale or colliding shared-memory slot, every output written once, and the
+replayed arithmetic within the FP32 tolerance of the FP64 oracle.  This checks
+the kernels' index logic before they run; the GPU parity tests are separate."""
+import numpy as np
+import pytest
+
+from emu import emu
+from paper_1505_08067_gb300 import synth
+
+
+def _check(oracle, shape, batch, direction=-1, seed=5, **opts):
+    n = int(np.prod(shape))
+    x = synth.uniform(seed, batch, n).reshape((batch,) + tuple(shape))
+    y, nerr, msg = emu.run(x, shape, direction=direction, **opts)
+    assert nerr == 0, msg
+    if batch == 0:
+        return
+    ref = oracle.fft(x, direction) if len(shape) == 1 else oracle.fft2d(x, direction)
+    err = oracle.rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1))
+    tol = 1e-6 * max(1.0, np.log2(n))
+    assert np.max(err) <= tol, (shape, batch, opts, np.max(err))
+
+
+@pytest.mark.parametrize("logn", range(0, 15))
+@pytest.mark.parametrize("batch", [1, 3])
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_single_pass(oracle, logn, batch, direction):
+    _check(oracle, (2 ** logn,), batch, direction)
+
+
+@pytest.mark.parametrize("logn,batch", [(15, 2), (16, 1), (17, 1), (18, 1)])
+def test_four_step(oracle, logn, batch):
+    _check(oracle, (2 ** logn,), batch)
+    _check(oracle, (2 ** logn,), batch, +1)
+
+
+@pytest.mark.parametrize("logn,bmax", [(6, 3), (7, 4), (9, 5), (12, 6), (16, 8), (14, 7)])
+def test_forced_splits(oracle, logn, bmax):
+    _check(oracle, (2 ** logn,), 3, max_block_log2=bmax)
+
+
+@pytest.mark.parametrize("radix,schedule", [(8, 0), (4, 0), (2, 0), (16, 0x2422), (16, 0x4222),
+                                            (16, 0x1144), (16, 0x4411), (8, 0x1333)])
+def test_forced_schedules_n1024(oracle, radix, schedule):
+    _check(oracle, (1024,), 5, radix=radix, schedule=schedule)
+
+
+@pytest.mark.parametrize("tile", [1, 2, 8, 32])
+def test_tiles_with_ragged_batch(oracle, tile):
+    _check(oracle, (256,), 37, tile=tile)
+
+
+@pytest.mark.parametrize("shape", [(8, 16), (16, 8), (1, 64), (64, 1), (1, 1), (32, 32),
+                                   (256, 512), (2 ** 14, 2)])
+def test_2d(oracle, shape):
+    _check(oracle, shape, 2)
+    _check(oracle, shape, 1, +1)
+
+
+def test_empty_batch(oracle):
+    _check(oracle, (64,), 0)
+
+
+def test_largest_four_step_slice(oracle):
+    """The widest tile shapes of the 2^24 plan on a cheaper 2^20 replay."""
+    _check(oracle, (2 ** 20,), 1)

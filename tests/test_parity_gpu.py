@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA kernels, called through the C ABI, against the FP64
+oracle on the same seeded inputs.  Tolerance (relative L2 per transform):
+1e-6 * log2(N) for the FP32 path (log2(rows*cols) for 2D).  Full-size
+workloads are checked on sampled transforms the oracle computes one by one,
+plus whole-array invariants."""
+import numpy as np
+import pytest
+
+from paper_1505_08067_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _tol(n):
+    return 1e-6 * max(1.0, np.log2(n))
+
+
+def _run(gb, x_np, shape, direction=-1, out_in_place=False, **opts):
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
+    batch = x_np.shape[0]
+    with gb.Plan(shape if len(shape) > 1 else shape[0], batch, direction, **opts) as p:
+        if out_in_place:
+            y = x.clone()
+            p.execute(y, y)
+        else:
+            y = p.execute(x)
+        torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def _compare(oracle, y, x, shape, direction=-1):
+    batch = x.shape[0]
+    ref = oracle.fft(x, direction) if len(shape) == 1 else oracle.fft2d(x, direction)
+    err = oracle.rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1))
+    n = int(np.prod(shape))
+    assert np.max(err) <= _tol(n), (shape, float(np.max(err)))
+    return float(np.max(err))
+
+
+@pytest.mark.parametrize("logn", range(0, 15))
+@pytest.mark.parametrize("batch", [1, 3, 64])
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_single_pass_sweep(gb, oracle, logn, batch, direction):
+    n = 2 ** logn
+    x = synth.uniform(1000 + logn, batch, n)
+    y = _run(gb, x, (n,), direction)
+    _compare(oracle, y, x, (n,), direction)
+
+
+@pytest.mark.parametrize("logn", range(15, 21))
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_four_step_sweep(gb, oracle, logn, direction):
+    n = 2 ** logn
+    batch = max(1, 2 ** 20 // n)
+    x = synth.uniform(2000 + logn, batch, n)
+    y = _run(gb, x, (n,), direction)
+    _compare(oracle, y, x, (n,), direction)
+
+
+@pytest.mark.parametrize("logn,bmax", [(6, 3), (10, 5), (12, 6), (14, 7), (16, 8), (13, 12)])
+def test_forced_splits(gb, oracle, logn, bmax):
+    x = synth.uniform(3000 + logn, 5, 2 ** logn)
+    y = _run(gb, x, (2 ** logn,), max_block_log2=bmax)
+    _compare(oracle, y, x, (2 ** logn,))
+
+
+def _schedules(total, parts=(1, 2, 3, 4)):
+    if total == 0:
+        yield []
+        return
+    for p in parts:
+        if p <= total:
+            for rest in _schedules(total - p, parts):
+                yield [p] + rest
+
+
+def test_every_radix_schedule_n1024(gb, oracle):
+    """All radix-{2,4,8,16} schedules of a 1024-point transform agree."""
+    x = synth.uniform(4000, 7, 1024)
+    ref = oracle.fft(x)
+    worst = 0.0
+    scheds = [s for s in _schedules(10) if len(s) <= 8]
+    for s in scheds:
+        code = 0
+        for i, lg in enumerate(s):
+            code |= lg << (4 * i)
+        y = _run(gb, x, (1024,), schedule=code, radix=1 << max(s))
+        worst = max(worst, float(np.max(oracle.rel_l2(y, ref))))
+    assert len(scheds) > 100 and worst <= _tol(1024)
+
+
+@pytest.mark.parametrize("radix", [2, 4, 8, 16])
+@pytest.mark.parametrize("logn", [5, 9, 13])
+def test_register_radix(gb, oracle, radix, logn):
+    x = synth.uniform(4100 + logn, 9, 2 ** logn)
+    y = _run(gb, x, (2 ** logn,), radix=radix)
+    _compare(oracle, y, x, (2 ** logn,))
+
+
+@pytest.mark.parametrize("tile", [1, 2, 4, 16, 64])
+def test_tiles_ragged_batch(gb, oracle, tile):
+    x = synth.uniform(4200, 37, 256)
+    _compare(oracle, _run(gb, x, (256,), tile=tile), x, (256,))
+
+
+@pytest.mark.parametrize("shape", [(2 ** 12,), (2 ** 18,), (64, 32)])
+def test_in_place(gb, oracle, shape):
+    n = int(np.prod(shape))
+    x = synth.uniform(4300, 3, n).reshape((3,) + shape)
+    y = _run(gb, x, shape, out_in_place=True)
+    _compare(oracle, y, x, shape)
+
+
+@pytest.mark.parametrize("shape", [(8, 16), (16, 8), (1, 64), (64, 1), (1, 1), (256, 512),
+                                   (2 ** 14, 4), (4, 2 ** 14)])
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_2d(gb, oracle, shape, direction):
+    n = int(np.prod(shape))
+    x = synth.uniform(4400 + n, 2, n).reshape((2,) + shape)
+    _compare(oracle, _run(gb, x, shape, direction), x, shape, direction)
+
+
+def test_tones_closed_form(gb, oracle):
+    """A unit tone at bin k0 maps to N at k0: the peak lands exactly there."""
+    for n in (256, 4096, 2 ** 14, 2 ** 20):
+        batch = 4
+        x = synth.tones(4500 + n, batch, n, 1)
+        bins = synth.tone_bins(4500 + n, batch, n, 1)[:, 0]
+        y = _run(gb, x, (n,))
+        assert np.array_equal(np.argmax(np.abs(y), axis=1), bins)
+        peak = y[np.arange(batch), bins]
+        assert np.max(np.abs(peak - n)) <= 1e-5 * n
+        _compare(oracle, y, x, (n,))
+
+
+def test_impulse_and_roundtrip(gb, oracle):
+    n = 4096
+    x = np.zeros((2, n), np.complex64)
+    x[0, 0] = 1
+    x[1, 17] = 1
+    y = _run(gb, x, (n,))
+    assert np.max(np.abs(y[0] - 1)) <= 1e-6
+    _compare(oracle, y, x, (n,))
+    z = synth.uniform(4600, 3, n)
+    back = _run(gb, _run(gb, z, (n,)), (n,), +1)
+    assert np.max(oracle.rel_l2(back, n * z.astype(np.complex128))) <= 2 * _tol(n)
+
+
+def test_empty_batch_and_errors(gb):
+    x = torch.zeros(8, dtype=torch.complex64, device="cuda")
+    with gb.Plan(8, 0) as p:
+        assert p.launch_count == 0
+        gb.fft_execute(p.handle, 0, 0)          # batch 0: nothing to do
+    with gb.Plan(8, 1) as p:
+        with pytest.raises(gb.GbfftError) as e:
+            gb.fft_execute(p.handle, x.data_ptr() + 4, x.data_ptr())
+        assert e.value.status == gb.FFT_ERR_INVALID_ARG
+        h = p.handle
+    with pytest.raises(gb.GbfftError) as e:
+        gb.fft_plan_create(12, 1)
+    assert e.value.status == gb.FFT_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(gb.GbfftError) as e:
+        gb.fft_plan_create(2 ** 25, 1)
+    assert e.value.status == gb.FFT_ERR_UNSUPPORTED_SIZE
+    del h
+
+
+def test_execute_host_matches_device(gb, oracle):
+    for shape, batch in (((4096,), 300), ((2 ** 18,), 6), ((64, 128), 3)):
+        n = int(np.prod(shape))
+        x = synth.uniform(4700 + n, batch, n).reshape((batch,) + shape)
+        host_in = torch.from_numpy(x).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        dev_in = torch.empty(host_in.shape, dtype=torch.complex64, device="cuda")
+        dev_out = torch.empty_like(dev_in)
+        with gb.Plan(shape if len(shape) > 1 else shape[0], batch) as p:
+            p.execute_host(host_in, host_out, dev_in, dev_out)
+            torch.cuda.synchronize()
+            ref = p.execute(dev_in).cpu().numpy()
+        assert np.array_equal(host_out.numpy(), ref)
+        _compare(oracle, host_out.numpy(), x, shape)
+
+
+# ------------------------------------------------ full-size workloads ------
+
+def _full(gb, oracle, n, batch, seed, direction=-1, samples=6):
+    x_np = synth.uniform(seed, batch, n)
+    x = torch.from_numpy(x_np).cuda()
+    with gb.Plan(n, batch, direction) as p:
+        y = p.execute(x)
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([[0, batch - 1], rng.integers(0, batch, samples)]))
+    ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.fft_select(x_np, idx, direction)
+    err = oracle.rel_l2(ys, ref)
+    assert np.max(err) <= _tol(n), (n, batch, float(np.max(err)))
+    # whole-array invariant (Parseval): sum |X|^2 = N sum |x|^2
+    ex = torch.sum(torch.abs(x.to(torch.complex128)) ** 2).item()
+    ey = torch.sum(torch.abs(y.to(torch.complex128)) ** 2).item()
+    assert abs(ey / (n * ex) - 1) <= 1e-5
+
+
+@pytest.mark.parametrize("logn", range(8, 15))
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_full_size_batched_sweep(gb, oracle, logn, direction):
+    """N = 2^8..2^14, N * batch = 2^27 (1 GiB in), as timed by the benchmark."""
+    _full(gb, oracle, 2 ** logn, 2 ** (27 - logn), 5000 + logn, direction)
+
+
+@pytest.mark.parametrize("logn,batch", [(20, 64), (22, 16), (24, 4)])
+def test_full_size_multipass(gb, oracle, logn, batch):
+    _full(gb, oracle, 2 ** logn, batch, 6000 + logn, samples=1)
+
+
+def test_sar_frame(gb, oracle):
+    """The 4096 azimuth x 8192 range chirp frame, whole, against the oracle."""
+    frame = synth.sar_frame(7000)[None]
+    y = _run(gb, frame, (4096, 8192))
+    err = _compare(oracle, y, frame, (4096, 8192))
+    assert err <= _tol(2 ** 25)
+
+
+def test_buried_tone_n4096(gb, oracle):
+    """N = 4096, batch 32768: uniform noise plus a 1e-3 tone; FP32 path."""
+    x, bins = synth.buried_tone(8000, 32768, 4096)
+    xt = torch.from_numpy(x).cuda()
+    with gb.Plan(4096, 32768) as p:
+        y = p.execute(xt)
+        torch.cuda.synchronize()
+    idx = np.arange(0, 32768, 997)
+    ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.fft_select(x, idx)
+    assert np.max(oracle.rel_l2(ys, ref)) <= _tol(4096)
+    tone_err = np.abs(ys[np.arange(idx.size), bins[idx]] - ref[np.arange(idx.size), bins[idx]])
+    assert np.max(tone_err) / (4096 * 1e-3) <= 1e-3
