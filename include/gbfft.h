@@ -98,6 +98,8 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *   max_block_log2  largest on-chip block 2^k (default from shared memory);
  *                 smaller values force multi-pass splits (testing).
  *   tile          transforms per thread block for passes that allow a choice.
+ *   generic       1: run every pass with the run-time-parameter kernel even
+ *                 where a compile-time specialisation of the shape exists.
  */
 typedef struct {
   int autotune;
@@ -105,7 +107,8 @@ typedef struct {
   uint32_t schedule;
   int max_block_log2;
   int tile;
-  int reserved[8];
+  int generic;      /* 1: never use the compile-time specialised kernels (testing) */
+  int reserved[7];
 } fft_plan_options_t;
 
 GBFFT_API fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,

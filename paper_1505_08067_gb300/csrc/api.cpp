@@ -85,15 +85,11 @@ void bind_pointers(fft_plan_t p) {
       l.grid = s.grid;
       l.block = s.block;
       l.smem = s.smem;
+      l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, p->spec.generic_only, &l.specialised);
+      prepare_launch(l);
     }
     p->launches.push_back(l);
   }
-}
-
-void* buf_ptr(fft_plan_t p, int which, const void* in, void* out) {
-  if (which == BUF_IN) return const_cast<void*>(in);
-  if (which == BUF_OUT) return out;
-  return p->work;
 }
 
 int64_t elems_per_batch(const PlanSpec& s) { return s.dims == 1 ? s.n[0] : s.n[0] * s.n[1]; }
@@ -118,6 +114,9 @@ fft_status_t enqueue(fft_plan_t p, const void* in, void* out, void* work, int64_
         d.epi_hi = l.d.epi_hi;
         d.epi_lo = l.d.epi_lo;
         l.d = d;
+        l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, p->spec.generic_only, &l.specialised);
+        cudaError_t pe = prepare_launch(l);
+        if (pe != cudaSuccess) return cuda_fail(pe, "kernel attributes");
         int64_t g = d.tiles;
         l.grid = (int)std::min<int64_t>(g, 0x7fffffff);
       }

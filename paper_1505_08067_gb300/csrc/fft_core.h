@@ -163,6 +163,18 @@ GB_HD void thread_coords(int map, int tid, int T, int G, int& g, int& t) {
 // transforms interleaved, a padding slot every 16.  Both keep the Stockham
 // reads and writes free of bank conflicts for the tile shapes the planner
 // emits.
+//
+// In the row layout slot(x) = x + (x >> 4) inside a transform, and a
+// butterfly touches x = base + i*D with D = L/r (reads) or D = Ns (writes).
+// Then slot(base + i*D) = slot(base) + i*D + ((i*D) >> 4) exactly:
+//   - if D is a multiple of 16 the low four bits of base are untouched;
+//   - reads: base = jb < L/r = D, so when D < 16 (D divides 16) base + i*D
+//     never carries into the next 16-block beyond what i*D itself does;
+//   - writes: base = (jb - k)*r + k with k = jb mod Ns < Ns, and (jb - k)*r
+//     is a multiple of Ns*r; if Ns*r <= 16 everything stays inside one
+//     16-block, otherwise (jb - k)*r is a multiple of 16 and base mod 16 = k,
+//     which again adds no carry to i*D.
+// So the offsets of a butterfly's elements are constants whenever D is.
 GB_HD int smem_slot(int layout, int g, int a, int G, int pitch) {
   if (layout == MAP_ROWS) return g * pitch + a + (a >> 4);
   int s = a * G + g;

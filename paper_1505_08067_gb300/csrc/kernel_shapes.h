@@ -1,0 +1,35 @@
+// Pass shapes compiled with every parameter fixed at compile time (see
+// CtTraits in fft_stage.h).  Each entry:
+//   GB_SHAPE(log2 L, schedule, stages, R, G, load map, store map, contiguous, epilogue)
+// schedule = log2 radices, stage 0 in the low nibble.  A pass whose shape
+// matches an entry runs that instantiation; every other pass runs the generic
+// kernel, which computes the same transform with run-time parameters.
+#pragma once
+
+#define GB_SHAPES(GB_SHAPE)                                   \
+  /* batched contiguous transforms, radix-16 stages, remainder last */ \
+  GB_SHAPE(8, 0x44, 2, 16, 16, 0, 0, true, 0)                 \
+  GB_SHAPE(9, 0x144, 3, 16, 8, 0, 0, true, 0)                 \
+  GB_SHAPE(10, 0x244, 3, 16, 4, 0, 0, true, 0)                \
+  GB_SHAPE(11, 0x344, 3, 16, 2, 0, 0, true, 0)                \
+  GB_SHAPE(12, 0x444, 3, 16, 1, 0, 0, true, 0)                \
+  GB_SHAPE(13, 0x1444, 4, 16, 1, 0, 0, true, 0)               \
+  GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)
+
+namespace gbfft {
+
+// Does pass descriptor `d` (run with R elements per thread and these maps)
+// have exactly this compile-time shape?
+GB_HD bool shape_matches(const PassDesc& d, int R, int lmap, int smap, int logL, uint32_t sched,
+                         int nst, int sR, int G, int slmap, int ssmap, bool contig, int epi) {
+  uint32_t s = 0;
+  for (int i = 0; i < d.nst && i < 8; ++i) s |= (uint32_t)d.rlog[i] << (4 * i);
+  if (d.nst > 8) return false;
+  const int64_t L = int64_t(1) << d.logL;
+  const bool is_contig = d.in.e == 1 && d.out.e == 1 && d.in.g == L && d.out.g == L &&
+                         d.in.t == d.G * L && d.out.t == d.G * L;
+  return d.logL == logL && s == sched && d.nst == nst && R == sR && d.G == G && lmap == slmap &&
+         smap == ssmap && d.epi == epi && (!contig || is_contig);
+}
+
+}  // namespace gbfft

@@ -1,25 +1,28 @@
 // Device kernels of the batched complex FFT (sm_103a).
 //
-//  stockham_pass<R, LMAP, SMAP>  one pass of a batched transform: every
+//  stockham_pass<R, LMAP, SMAP, TR>  one pass of a batched transform: every
 //      transform of length L <= 2^14 (or a tile of G of them) lives on one SM,
 //      each thread holds R elements in registers, radix stages exchange through
 //      shared memory, global memory is read once and written once
 //      (Bergach et al. Sec. 3.4 "one FFT per EU": only the first read and the
 //      last write touch the memory hierarchy).  The output can be written
 //      transposed and multiplied by the four-step twiddle w_N^{n2 k1}, which is
-//      how passes of a split transform are joined (Sec. 3.3).
+//      how passes of a split transform are joined (Sec. 3.3).  TR = RtTraits
+//      is the generic kernel; CtTraits instantiations fix the hot shapes at
+//      compile time.
 //  twiddle_gen                   FP64 roots of unity rounded once to FP32
 //      (the precomputed twiddle table of Sec. 2.1).
 //  copy_kernel                   length-1 transforms (the DFT is the identity).
 #include <cuda_runtime.h>
 
 #include "fft_stage.h"
+#include "kernel_shapes.h"
 #include "kernels.h"
 
 namespace gbfft {
 
 struct DevMem {
-  // Input is read exactly once: stream it past L1 with an evict-first hint.
+  // Input is read exactly once: stream it with an evict-first hint.
   GB_HD static cf ldg(const cf* p, int64_t off) {
 #ifdef __CUDA_ARCH__
     float2 r = __ldcs(reinterpret_cast<const float2*>(p) + off);
@@ -47,26 +50,41 @@ struct DevMem {
   GB_HD static void sts(cf* s, int i, cf v) { s[i] = v; }
 };
 
-template <int R, int LMAP, int SMAP>
+template <int R, int LMAP, int SMAP, class TR>
 __global__ void __launch_bounds__(1024)
 stockham_pass(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* sm = reinterpret_cast<cf*>(smem_raw);
-  using B = PassBody<R, LMAP, SMAP, DevMem>;
+  using B = PassBody<R, LMAP, SMAP, DevMem, TR>;
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
     const typename B::Tile tl = B::tile_of(d, tile);
     cf v[R];
     B::first(v, d, in, out, sm, tl, tid);
-    int Ns = 1 << d.rlog[0];
-    for (int s = 1; s < d.nst; ++s) {
-      __syncthreads();
-      B::read(v, d, s, Ns, out, sm, tl, tid);
-      if (s < d.nst - 1) {
+    int Ns = 1 << TR::rlog(d, 0);
+    if constexpr (TR::kMaxStages < 15) {
+      // compile-time schedule: unrolled, every radix and offset a constant
+#pragma unroll
+      for (int s = 1; s < TR::kMaxStages; ++s) {
         __syncthreads();
-        B::write(v, d, s, Ns, sm, tid);
+        B::read(v, d, s, Ns, out, sm, tl, tid);
+        if (s < TR::kMaxStages - 1) {
+          __syncthreads();
+          B::write(v, d, s, Ns, sm, tid);
+        }
+        Ns <<= TR::rlog(d, s);
       }
-      Ns <<= d.rlog[s];
+    } else {
+#pragma unroll 1
+      for (int s = 1; s < d.nst; ++s) {
+        __syncthreads();
+        B::read(v, d, s, Ns, out, sm, tl, tid);
+        if (s < d.nst - 1) {
+          __syncthreads();
+          B::write(v, d, s, Ns, sm, tid);
+        }
+        Ns <<= d.rlog[s];
+      }
     }
     __syncthreads();  // shared memory is reused by the next tile
   }
@@ -80,9 +98,9 @@ __global__ void copy_kernel(const cf* __restrict__ in, cf* out, int64_t count, i
     out[i * out_stride] = in[i * in_stride];
 }
 
-// Twiddle tables in FP64, rounded once to FP32.  Segment j of `count`:
-//   mode 0 (stage table, radix r):  exponent = (j / r) * (j % r)
-//   mode 1 (power table):           exponent = j * mult
+// Twiddle tables in FP64, rounded once to FP32.  Entry j of `count`:
+//   mode 0 (stage table):  exponent = (j / r) * (j % r)
+//   mode 1 (power table):  exponent = j * mult
 // value = exp(-2 pi i * (exponent mod den) / den).  The exponent is reduced as
 // an integer, so sincospi receives an exact argument in [0, 2).
 __global__ void twiddle_gen(float2* out, int64_t count, int64_t den, int mode, int r,
@@ -99,69 +117,61 @@ __global__ void twiddle_gen(float2* out, int64_t count, int64_t den, int mode, i
 
 // ------------------------------------------------------------------ host --
 
-template <int R, int LMAP, int SMAP>
-static cudaError_t launch_t(const PassDesc& d, const cf* in, cf* out, int grid, int block,
-                            size_t smem, cudaStream_t st) {
-  auto k = stockham_pass<R, LMAP, SMAP>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k<<<grid, block, smem, st>>>(in, out, d);
-  return cudaGetLastError();
+using KernelFn = void (*)(const cf*, cf*, PassDesc);
+
+template <int R, int LMAP, int SMAP, class TR>
+static KernelFn kfn() {
+  return stockham_pass<R, LMAP, SMAP, TR>;
 }
 
-template <int LMAP, int SMAP>
-static cudaError_t launch_maps(int R, const PassDesc& d, const cf* in, cf* out, int grid,
-                               int block, size_t smem, cudaStream_t st) {
-  switch (R) {
-    case 2: return launch_t<2, LMAP, SMAP>(d, in, out, grid, block, smem, st);
-    case 4: return launch_t<4, LMAP, SMAP>(d, in, out, grid, block, smem, st);
-    case 8: return launch_t<8, LMAP, SMAP>(d, in, out, grid, block, smem, st);
-    case 16: return launch_t<16, LMAP, SMAP>(d, in, out, grid, block, smem, st);
-    default: return cudaErrorInvalidValue;
+static KernelFn generic_kernel(int R, int lmap, int smap) {
+#define GB_GEN(RR, A, B_) \
+  if (R == RR && lmap == A && smap == B_) return kfn<RR, A, B_, RtTraits>();
+  GB_GEN(2, 0, 0) GB_GEN(4, 0, 0) GB_GEN(8, 0, 0) GB_GEN(16, 0, 0)
+  GB_GEN(2, 1, 1) GB_GEN(4, 1, 1) GB_GEN(8, 1, 1) GB_GEN(16, 1, 1)
+  GB_GEN(2, 0, 1) GB_GEN(4, 0, 1) GB_GEN(8, 0, 1) GB_GEN(16, 0, 1)
+#undef GB_GEN
+  return nullptr;
+}
+
+const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool generic_only,
+                           bool* specialised) {
+  if (specialised) *specialised = !generic_only;
+  if (!generic_only) {
+#define GB_TRY(LOGL, SCHED, NST, RR, G, LM, SM, CONTIG, EPI)                                 \
+  if (shape_matches(d, R, lmap, smap, LOGL, SCHED, NST, RR, G, LM, SM, CONTIG, EPI))         \
+    return (const void*)kfn<RR, LM, SM, CtTraits<LOGL, SCHED, NST, RR, G, CONTIG, EPI>>();
+  GB_SHAPES(GB_TRY)
+#undef GB_TRY
   }
+  if (specialised) *specialised = false;
+  return (const void*)generic_kernel(R, lmap, smap);
+}
+
+cudaError_t prepare_launch(PassLaunch& p) {
+  if (!p.fn) return cudaErrorInvalidValue;
+  if (p.smem > 48 * 1024)
+    return cudaFuncSetAttribute(p.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  return cudaSuccess;
 }
 
 cudaError_t launch_pass(const PassLaunch& p, const void* in, void* out, cudaStream_t st) {
-  const cf* i = static_cast<const cf*>(in);
-  cf* o = static_cast<cf*>(out);
-  if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS)
-    return launch_maps<MAP_ROWS, MAP_ROWS>(p.R, p.d, i, o, p.grid, p.block, p.smem, st);
-  if (p.lmap == MAP_COLS && p.smap == MAP_COLS)
-    return launch_maps<MAP_COLS, MAP_COLS>(p.R, p.d, i, o, p.grid, p.block, p.smem, st);
-  if (p.lmap == MAP_ROWS && p.smap == MAP_COLS)
-    return launch_maps<MAP_ROWS, MAP_COLS>(p.R, p.d, i, o, p.grid, p.block, p.smem, st);
-  return cudaErrorInvalidValue;
+  KernelFn k = reinterpret_cast<KernelFn>(const_cast<void*>(p.fn));
+  if (!k) return cudaErrorInvalidValue;
+  k<<<p.grid, p.block, p.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), p.d);
+  return cudaGetLastError();
 }
 
-cudaError_t kernel_attributes(int R, int lmap, int smap, cudaFuncAttributes* attr) {
-#define GB_ATTR(RR, A, B_) \
-  if (R == RR && lmap == A && smap == B_) return cudaFuncGetAttributes(attr, stockham_pass<RR, A, B_>);
-  GB_ATTR(2, 0, 0) GB_ATTR(4, 0, 0) GB_ATTR(8, 0, 0) GB_ATTR(16, 0, 0)
-  GB_ATTR(2, 1, 1) GB_ATTR(4, 1, 1) GB_ATTR(8, 1, 1) GB_ATTR(16, 1, 1)
-  GB_ATTR(2, 0, 1) GB_ATTR(4, 0, 1) GB_ATTR(8, 0, 1) GB_ATTR(16, 0, 1)
-#undef GB_ATTR
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t occupancy(int R, int lmap, int smap, int block, size_t smem, int* ctas_per_sm) {
-#define GB_OCC(RR, A, B_)                                                                   \
-  if (R == RR && lmap == A && smap == B_) {                                                 \
-    auto k = stockham_pass<RR, A, B_>;                                                      \
-    if (smem > 48 * 1024) {                                                                 \
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                           (int)smem);                                      \
-      if (e != cudaSuccess) return e;                                                       \
-    }                                                                                       \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k, block, smem);      \
+cudaError_t occupancy(const PassLaunch& p, int* ctas_per_sm) {
+  KernelFn k = reinterpret_cast<KernelFn>(const_cast<void*>(p.fn));
+  if (!k) return cudaErrorInvalidValue;
+  if (p.smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p.smem);
+    if (e != cudaSuccess) return e;
   }
-  GB_OCC(2, 0, 0) GB_OCC(4, 0, 0) GB_OCC(8, 0, 0) GB_OCC(16, 0, 0)
-  GB_OCC(2, 1, 1) GB_OCC(4, 1, 1) GB_OCC(8, 1, 1) GB_OCC(16, 1, 1)
-  GB_OCC(2, 0, 1) GB_OCC(4, 0, 1) GB_OCC(8, 0, 1) GB_OCC(16, 0, 1)
-#undef GB_OCC
-  return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, (const void*)k, p.block,
+                                                       p.smem);
 }
 
 cudaError_t launch_copy(const void* in, void* out, int64_t count, int64_t in_stride,

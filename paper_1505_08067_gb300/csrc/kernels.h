@@ -14,11 +14,21 @@ struct PassLaunch {
   int lmap, smap;   // thread maps of the load (and middle) stages and of the store
   int grid, block;  // grid size (tiles are grid-strided) and threads per block
   size_t smem;      // dynamic shared memory in bytes
+  const void* fn = nullptr;  // resolved kernel (specialised or generic)
+  bool specialised = false;
 };
 
+// Kernel for this pass shape: a compile-time specialisation when one matches,
+// else the generic kernel for (R, maps).
+const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool generic_only,
+                           bool* specialised);
+
+// Per-kernel attributes a launch needs (opt-in shared memory); call once after
+// resolving, before the first launch_pass.
+cudaError_t prepare_launch(PassLaunch& p);
+
 cudaError_t launch_pass(const PassLaunch& p, const void* in, void* out, cudaStream_t st);
-cudaError_t kernel_attributes(int R, int lmap, int smap, cudaFuncAttributes* attr);
-cudaError_t occupancy(int R, int lmap, int smap, int block, size_t smem, int* ctas_per_sm);
+cudaError_t occupancy(const PassLaunch& p, int* ctas_per_sm);
 cudaError_t launch_copy(const void* in, void* out, int64_t count, int64_t in_stride,
                         int64_t out_stride, cudaStream_t st);
 cudaError_t launch_twiddle_gen(void* out, int64_t count, int64_t den, int mode, int r,

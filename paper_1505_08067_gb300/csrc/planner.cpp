@@ -204,6 +204,7 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
     bmax = std::min(bmax, o.max_block_log2);
   }
   s.max_block_log2 = bmax;
+  s.generic_only = o.generic != 0;
   const int inv = direction == FFT_INVERSE;
 
   if (dims == 1) {
@@ -317,7 +318,8 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
     for (size_t st = 1; st < p.rlogs.size(); ++st) {
       const int r = 1 << p.rlogs[st];
       p.tw_off[st] = (int32_t)off;
-      s.tables.push_back(TwSegment{off, Ns * r, Ns * r, 1, 0, r});
+      // i-major: entry i*Ns + k = w_{Ns*r}^{i*k}
+      s.tables.push_back(TwSegment{off, Ns * r, Ns * r, 1, 0, (int)Ns});
       off += Ns * r;
       off = (off + 1) & ~int64_t(1);  // keep 16-byte alignment of segments
       Ns *= r;
@@ -384,6 +386,7 @@ std::string describe(const PlanSpec& s) {
   if (s.dims == 2) o << "," << s.n[1];
   o << "],\"batch\":" << s.batch << ",\"direction\":" << s.direction
     << ",\"precision\":" << s.precision << ",\"max_block_log2\":" << s.max_block_log2
+    << ",\"generic\":" << (s.generic_only ? 1 : 0)
     << ",\"workspace_bytes\":" << s.work_elems * 8 << ",\"table_elems\":" << s.table_elems
     << ",\"passes\":[";
   for (size_t i = 0; i < s.passes.size(); ++i) {

@@ -47,7 +47,7 @@ struct PassSpec {
   int64_t epi_hi_off = 0, epi_lo_off = 0;
 };
 
-struct TwSegment {  // one twiddle_gen launch
+struct TwSegment {  // one twiddle_gen launch (mode 0: exponent (j / r) * (j % r))
   int64_t off, count, den, mult;
   int mode, r;
 };
@@ -59,6 +59,7 @@ struct PlanSpec {
   int direction = FFT_FORWARD;
   int precision = FFT_PREC_FP32;
   int max_block_log2 = 14;
+  bool generic_only = false;  // never pick compile-time specialisations
   std::vector<PassSpec> passes;
   std::vector<TwSegment> tables;
   int64_t table_elems = 0;

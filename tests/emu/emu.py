@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_1505_08067_gb300", "csrc")
 LIB = os.path.join(HERE, "_emu.so")
 SRCS = [os.path.join(HERE, "emu_harness.cpp"), os.path.join(CSRC, "planner.cpp")]
-DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "planner.h")] + \
+DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "planner.h", "kernel_shapes.h")] + \
     [os.path.join(ROOT, "include", "gbfft.h")]
 _lib = None
 
@@ -20,7 +20,7 @@ _lib = None
 class Options(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int), ("radix", ctypes.c_int), ("schedule", ctypes.c_uint32),
                 ("max_block_log2", ctypes.c_int), ("tile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("generic", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 def load():
@@ -36,14 +36,18 @@ def load():
     lib = ctypes.CDLL(LIB)
     lib.emu_run.restype = ctypes.c_int64
     lib.emu_run.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int64,
-                            ctypes.c_int, ctypes.POINTER(Options), ctypes.c_int,
-                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]
+                            ctypes.c_int, ctypes.POINTER(Options), ctypes.c_int, ctypes.c_int,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
+                            ctypes.POINTER(ctypes.c_int64)]
     _lib = lib
     return lib
 
 
-def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, **opts):
-    """Replay the planned passes for complex64 input x of shape (batch, *shape)."""
+def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, specialised=True, stats=None,
+        **opts):
+    """Replay the planned passes for complex64 input x of shape (batch, *shape).
+    With specialised=True a pass whose shape the library compiles with fixed
+    parameters replays that instantiation (as the GPU would run it)."""
     lib = load()
     x = np.ascontiguousarray(x, dtype=np.complex64)
     dims = len(shape)
@@ -54,6 +58,10 @@ def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, **opts):
     for k, v in opts.items():
         setattr(o, k, v)
     msg = ctypes.create_string_buffer(512)
+    sp = ctypes.c_int64(0)
     nerr = lib.emu_run(n, dims, batch, direction, ctypes.byref(o), smem_optin,
-                       x.ctypes.data, out.ctypes.data, msg, 512)
+                       1 if specialised else 0, x.ctypes.data, out.ctypes.data, msg, 512,
+                       ctypes.byref(sp))
+    if stats is not None:
+        stats["special_passes"] = sp.value
     return out, int(nerr), msg.value.decode()

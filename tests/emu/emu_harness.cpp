@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "fft_stage.h"
+#include "kernel_shapes.h"
 #include "planner.h"
 
 using namespace gbfft;
@@ -40,6 +41,7 @@ struct Ctx {
   std::vector<int64_t>* slot_write = nullptr;
   int64_t epoch = 0;
   int64_t errors = 0;
+  int64_t special_passes = 0;
   std::string first_error;
 };
 Ctx g;
@@ -54,13 +56,15 @@ void err(const char* what, int64_t idx) {
 
 struct CheckMem {
   static cf ldg(const cf* p, int64_t off) {
-    if (p != g.in || off < 0 || off >= g.in_len) { err("global load out of bounds", off); return mk(0, 0); }
-    return p[off];
+    const int64_t idx = (p - g.in) + off;
+    if (idx < 0 || idx >= g.in_len) { err("global load out of bounds", idx); return mk(0, 0); }
+    return g.in[idx];
   }
   static void stg(cf* p, int64_t off, cf v) {
-    if (p != g.out || off < 0 || off >= g.out_len) { err("global store out of bounds", off); return; }
-    if ((*g.out_hits)[off]++) err("output element written twice", off);
-    p[off] = v;
+    const int64_t idx = (p - g.out) + off;
+    if (idx < 0 || idx >= g.out_len) { err("global store out of bounds", idx); return; }
+    if ((*g.out_hits)[idx]++) err("output element written twice", idx);
+    g.out[idx] = v;
   }
   static cf ldtw(const cf* p) {
     int64_t off = p - g.tw;
@@ -88,9 +92,9 @@ cf root(int64_t e, int64_t den) {
   return mk((float)cos(a), (float)sin(a));
 }
 
-template <int R, int LM, int SM>
+template <int R, int LM, int SM, class TR = RtTraits>
 void run_pass_t(const PassDesc& d, const cf* in, cf* out) {
-  using B = PassBody<R, LM, SM, CheckMem>;
+  using B = PassBody<R, LM, SM, CheckMem, TR>;
   const int nthr = d.G * d.T;
   std::vector<cf> smem(std::max(1, d.smem_elems));
   std::vector<int64_t> ep(smem.size(), -1), wr(smem.size(), -1);
@@ -123,6 +127,21 @@ void run_pass_t(const PassDesc& d, const cf* in, cf* out) {
   }
 }
 
+// The same compile-time shapes the GPU library instantiates.
+template <int R, int LM, int SM, class TR>
+void run_ct(const PassDesc& d, const cf* in, cf* out);
+
+bool run_special(int R, int lmap, int smap, const PassDesc& d, const cf* in, cf* out) {
+#define GB_TRY(LOGL, SCHED, NST, RR, G, LMAP_, SMAP_, CONTIG, EPI)                          \
+  if (shape_matches(d, R, lmap, smap, LOGL, SCHED, NST, RR, G, LMAP_, SMAP_, CONTIG, EPI)) { \
+    run_ct<RR, LMAP_, SMAP_, CtTraits<LOGL, SCHED, NST, RR, G, CONTIG, EPI>>(d, in, out);   \
+    return true;                                                                         \
+  }
+  GB_SHAPES(GB_TRY)
+#undef GB_TRY
+  return false;
+}
+
 template <int LM, int SM>
 void run_maps(int R, const PassDesc& d, const cf* in, cf* out) {
   switch (R) {
@@ -132,6 +151,11 @@ void run_maps(int R, const PassDesc& d, const cf* in, cf* out) {
     case 16: run_pass_t<16, LM, SM>(d, in, out); break;
     default: err("bad R", R);
   }
+}
+
+template <int R, int LM, int SM, class TR>
+void run_ct(const PassDesc& d, const cf* in, cf* out) {
+  run_pass_t<R, LM, SM, TR>(d, in, out);
 }
 
 }  // namespace
@@ -145,8 +169,9 @@ extern "C" {
 // (complex64, same size as `in`).  Returns the number of access violations;
 // the first one is described in msg.
 int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
-                const fft_plan_options_t* opt, int smem_optin, const float* in_f, float* out_f,
-                char* msg, size_t msg_len) {
+                const fft_plan_options_t* opt, int smem_optin, int specialised,
+                const float* in_f, float* out_f, char* msg, size_t msg_len,
+                int64_t* special_passes) {
   Caps caps;
   caps.smem_optin = smem_optin;
   PlanSpec s = make_plan(n, dims, batch, direction, FFT_PREC_FP32, opt, caps);
@@ -191,13 +216,15 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
     g.out_hits = &hits;
     g.tw = tables.data();
     g.tw_len = s.table_elems;
-    if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
+    if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
+    else if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
     else if (p.lmap == MAP_COLS && p.smap == MAP_COLS) run_maps<1, 1>(p.R, d, src, dst);
     else run_maps<0, 1>(p.R, d, src, dst);
     for (int64_t i = 0; i < g.out_len; ++i)
       if (hits[i] != 1) { err("output element not written exactly once", i); break; }
   }
   snprintf(msg, msg_len, "%s", g.first_error.c_str());
+  if (special_passes) *special_passes = g.special_passes;
   return g.errors;
 }
 

@@ -9,10 +9,10 @@ from emu import emu
 from paper_1505_08067_gb300 import synth
 
 
-def _check(oracle, shape, batch, direction=-1, seed=5, **opts):
+def _check(oracle, shape, batch, direction=-1, seed=5, specialised=True, **opts):
     n = int(np.prod(shape))
     x = synth.uniform(seed, batch, n).reshape((batch,) + tuple(shape))
-    y, nerr, msg = emu.run(x, shape, direction=direction, **opts)
+    y, nerr, msg = emu.run(x, shape, direction=direction, specialised=specialised, **opts)
     assert nerr == 0, msg
     if batch == 0:
         return
@@ -27,6 +27,22 @@ def _check(oracle, shape, batch, direction=-1, seed=5, **opts):
 @pytest.mark.parametrize("direction", [-1, 1])
 def test_single_pass(oracle, logn, batch, direction):
     _check(oracle, (2 ** logn,), batch, direction)
+
+
+@pytest.mark.parametrize("logn", range(8, 15))
+@pytest.mark.parametrize("direction", [-1, 1])
+@pytest.mark.parametrize("specialised", [True, False])
+def test_compile_time_shapes(oracle, logn, direction, specialised):
+    """The batch sizes the benchmark uses select the compile-time kernels; the
+    generic kernel must agree on the same plan."""
+    n = 2 ** logn
+    batch = 2 ** 16 // n
+    st = {}
+    x = synth.uniform(9, batch, n)
+    y, nerr, msg = emu.run(x, (n,), direction=direction, specialised=specialised, stats=st)
+    assert nerr == 0, msg
+    assert st["special_passes"] == (1 if specialised else 0)
+    assert np.max(oracle.rel_l2(y, oracle.fft(x, direction))) <= 1e-6 * logn
 
 
 @pytest.mark.parametrize("logn,batch", [(15, 2), (16, 1), (17, 1), (18, 1)])

@@ -235,3 +235,19 @@ def test_buried_tone_n4096(gb, oracle):
     assert np.max(oracle.rel_l2(ys, ref)) <= _tol(4096)
     tone_err = np.abs(ys[np.arange(idx.size), bins[idx]] - ref[np.arange(idx.size), bins[idx]])
     assert np.max(tone_err) / (4096 * 1e-3) <= 1e-3
+
+
+@pytest.mark.parametrize("logn", range(8, 15))
+def test_generic_and_specialised_kernels_agree(gb, oracle, logn):
+    """The benchmark's batch shapes select compile-time kernels; forcing the
+    run-time-parameter kernel on the same plan gives the same transform."""
+    n = 2 ** logn
+    batch = 2 ** 18 // n
+    x = synth.uniform(9000 + logn, batch, n)
+    for d in (-1, 1):
+        ys = _run(gb, x, (n,), d)
+        yg = _run(gb, x, (n,), d, generic=1)
+        ref = oracle.fft_select(x, np.arange(0, batch, 7), d)
+        for y in (ys, yg):
+            assert np.max(oracle.rel_l2(y[::7], ref)) <= _tol(n)
+        assert np.max(np.abs(ys - yg)) <= 1e-5 * np.sqrt(n)
