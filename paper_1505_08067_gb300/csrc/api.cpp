@@ -12,6 +12,7 @@
 
 #include "../../include/gbfft.h"
 #include "autotune.h"
+#include "exec.h"
 #include "kernels.h"
 #include "planner.h"
 
@@ -19,15 +20,15 @@ using namespace gbfft;
 
 namespace {
 
-thread_local std::string g_err;
+// Message of the last failure on this thread (fixed storage: reporting an
+// error never allocates).
+thread_local char g_err[512];
 
 fft_status_t fail(fft_status_t st, const char* fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
   va_end(ap);
-  g_err = buf;
   return st;
 }
 
@@ -46,7 +47,7 @@ struct fft_plan_s {
   Caps caps;
   void* tables = nullptr;  // cf[spec.table_elems]
   void* work = nullptr;    // cf[spec.work_elems]
-  std::vector<PassLaunch> launches;  // whole-batch launches, device pointers filled
+  PassLaunch launches[4];  // whole-batch launches, device pointers filled
   // lazily created resources of fft_execute_host
   cudaStream_t s_h2d = nullptr, s_k = nullptr, s_d2h = nullptr;
   cudaEvent_t ev_start = nullptr, ev_h2d = nullptr, ev_k = nullptr, ev_end = nullptr;
@@ -69,64 +70,7 @@ fft_status_t query_caps(Caps& caps, int& device) {
   return FFT_OK;
 }
 
-void bind_pointers(fft_plan_t p) {
-  p->launches.clear();
-  const cf* tw = static_cast<const cf*>(p->tables);
-  for (const PassSpec& s : p->spec.passes) {
-    PassLaunch l{};
-    if (s.kind == PASS_FFT) {
-      l.d = pass_desc(s, 0, p->spec.batch, p->spec.batch);
-      l.d.tw = tw;
-      l.d.epi_hi = s.epi ? tw + s.epi_hi_off : nullptr;
-      l.d.epi_lo = s.epi ? tw + s.epi_lo_off : nullptr;
-      l.R = s.R;
-      l.lmap = s.lmap;
-      l.smap = s.smap;
-      l.grid = s.grid;
-      l.block = s.block;
-      l.smem = s.smem;
-      l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, p->spec.generic_only, &l.specialised);
-      prepare_launch(l);
-    }
-    p->launches.push_back(l);
-  }
-}
-
 int64_t elems_per_batch(const PlanSpec& s) { return s.dims == 1 ? s.n[0] : s.n[0] * s.n[1]; }
-
-// Enqueue all passes for batch entries [b0, b0 + nb) (pointers already offset).
-fft_status_t enqueue(fft_plan_t p, const void* in, void* out, void* work, int64_t b0, int64_t nb,
-                     cudaStream_t st) {
-  if (nb <= 0) return FFT_OK;
-  const int64_t E = elems_per_batch(p->spec);
-  for (size_t i = 0; i < p->spec.passes.size(); ++i) {
-    const PassSpec& s = p->spec.passes[i];
-    const void* src = s.src == BUF_IN ? in : (s.src == BUF_OUT ? (const void*)out : work);
-    void* dst = s.dst == BUF_OUT ? out : work;
-    cudaError_t e;
-    if (s.kind == PASS_COPY) {
-      e = launch_copy(src, dst, nb * E, 1, 1, st);
-    } else {
-      PassLaunch l = p->launches[i];
-      if (b0 != 0 || nb != p->spec.batch) {
-        PassDesc d = pass_desc(s, b0, nb, p->spec.batch);
-        d.tw = l.d.tw;
-        d.epi_hi = l.d.epi_hi;
-        d.epi_lo = l.d.epi_lo;
-        l.d = d;
-        l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, p->spec.generic_only, &l.specialised);
-        cudaError_t pe = prepare_launch(l);
-        if (pe != cudaSuccess) return cuda_fail(pe, "kernel attributes");
-        int64_t g = d.tiles;
-        l.grid = (int)std::min<int64_t>(g, 0x7fffffff);
-      }
-      if (l.d.tiles == 0) continue;
-      e = launch_pass(l, src, dst, st);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  }
-  return FFT_OK;
-}
 
 fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t batch, int direction,
                         int precision, const fft_plan_options_t* opt) {
@@ -136,8 +80,9 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
   int dev = -1;
   fft_status_t st = query_caps(caps, dev);
   if (st != FFT_OK) return st;
-  PlanSpec spec = make_plan(n, dims, batch, direction, precision, opt, caps);
-  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error.c_str());
+  PlanSpec spec;
+  make_plan(spec, n, dims, batch, direction, precision, opt, caps);
+  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
   fft_plan_t p = new (std::nothrow) fft_plan_s();
   if (!p) return fail(FFT_ERR_OUT_OF_MEMORY, "host allocation of the plan failed");
   p->device = dev;
@@ -162,29 +107,27 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
                   (long long)spec.work_elems * 8, cudaGetErrorString(e));
     }
   }
-  for (const TwSegment& t : spec.tables) {
-    e = launch_twiddle_gen(static_cast<cf*>(p->tables) + t.off, t.count, t.den, t.mode, t.r,
-                           t.mult, 0);
-    if (e != cudaSuccess) {
-      fft_plan_destroy(p);
-      return cuda_fail(e, "twiddle generation");
-    }
-  }
-  e = cudaDeviceSynchronize();
+  e = enqueue_tables(spec, static_cast<cf*>(p->tables), 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = bind_launches(p->spec, static_cast<const cf*>(p->tables), p->launches);
   if (e != cudaSuccess) {
     fft_plan_destroy(p);
     return cuda_fail(e, "twiddle generation");
   }
-  bind_pointers(p);
   if (opt && opt->autotune) {
     st = autotune_plan(p->spec, p->caps, p->tables, p->work);
     if (st != FFT_OK) {
-      std::string msg = g_err;
+      char msg[sizeof g_err];
+      memcpy(msg, g_err, sizeof msg);
       fft_plan_destroy(p);
-      g_err = msg;
+      memcpy(g_err, msg, sizeof msg);
       return st;
     }
-    bind_pointers(p);
+    e = bind_launches(p->spec, static_cast<const cf*>(p->tables), p->launches);
+    if (e != cudaSuccess) {
+      fft_plan_destroy(p);
+      return cuda_fail(e, "kernel attributes");
+    }
   }
   *out = p;
   return FFT_OK;
@@ -221,8 +164,10 @@ fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* strea
   if (dev != plan->device)
     return fail(FFT_ERR_BAD_PLAN, "plan was created on device %d, current device is %d",
                 plan->device, dev);
-  return enqueue(plan, in, out, plan->work, 0, plan->spec.batch,
-                 static_cast<cudaStream_t>(stream));
+  e = enqueue_passes(plan->spec, plan->launches, in, out, plan->work, 0, plan->spec.batch,
+                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return FFT_OK;
 }
 
 fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_out, void* dev_in,
@@ -274,8 +219,9 @@ fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_o
       return cuda_fail(e, "host-to-device copy");
     cudaEventRecord(plan->ev_h2d, plan->s_h2d);
     cudaStreamWaitEvent(plan->s_k, plan->ev_h2d, 0);
-    fft_status_t st = enqueue(plan, di + off, dout + off, wk ? wk + off : nullptr, b0, nb, plan->s_k);
-    if (st != FFT_OK) return st;
+    e = enqueue_passes(s, plan->launches, di + off, dout + off, wk ? wk + off : nullptr, b0, nb,
+                       plan->s_k);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     cudaEventRecord(plan->ev_k, plan->s_k);
     cudaStreamWaitEvent(plan->s_d2h, plan->ev_k, 0);
     if ((e = cudaMemcpyAsync(ho + off, dout + off, bytes, cudaMemcpyDeviceToHost, plan->s_d2h)) !=
@@ -351,8 +297,9 @@ fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batch, int dir
   Caps caps;
   caps.sm_count = sm_count;
   caps.smem_optin = smem_optin_bytes;
-  PlanSpec spec = make_plan(n, dims, batch, direction, precision, options, caps);
-  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error.c_str());
+  PlanSpec spec;
+  make_plan(spec, n, dims, batch, direction, precision, options, caps);
+  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
   return copy_text(describe(spec), buf, len);
 }
 
@@ -365,7 +312,7 @@ fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream) {
   return FFT_OK;
 }
 
-const char* fft_last_error(void) { return g_err.c_str(); }
+const char* fft_last_error(void) { return g_err; }
 
 fft_status_t fft_schedule_count(int log2n, const int* radix_logs, int n_radix, uint64_t* count) {
   if (log2n < 0 || log2n > 60 || !radix_logs || n_radix <= 0 || !count)

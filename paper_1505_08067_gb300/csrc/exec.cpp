@@ -1,0 +1,72 @@
+// See exec.h.
+#include "exec.h"
+
+#include <algorithm>
+
+namespace gbfft {
+
+cudaError_t bind_launches(const PlanSpec& s, const cf* tables, PassLaunch* launches) {
+  for (int i = 0; i < s.passes.size(); ++i) {
+    const PassSpec& p = s.passes[i];
+    PassLaunch l{};
+    if (p.kind == PASS_FFT) {
+      l.d = pass_desc(p, 0, s.batch, s.batch);
+      l.d.tw = tables;
+      l.d.epi_hi = p.epi ? tables + p.epi_hi_off : nullptr;
+      l.d.epi_lo = p.epi ? tables + p.epi_lo_off : nullptr;
+      l.R = p.R;
+      l.lmap = p.lmap;
+      l.smap = p.smap;
+      l.grid = p.grid;
+      l.block = p.block;
+      l.smem = p.smem;
+      l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
+      cudaError_t e = prepare_launch(l);
+      if (e != cudaSuccess) return e;
+    }
+    launches[i] = l;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st) {
+  for (const TwSegment& t : s.tables) {
+    cudaError_t e = launch_twiddle_gen(tables + t.off, t.count, t.den, t.mode, t.r, t.mult, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const void* in,
+                           void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  const int64_t E = s.dims == 1 ? s.n[0] : s.n[0] * s.n[1];
+  for (int i = 0; i < s.passes.size(); ++i) {
+    const PassSpec& p = s.passes[i];
+    const void* src = p.src == BUF_IN ? in : (p.src == BUF_OUT ? (const void*)out : work);
+    void* dst = p.dst == BUF_OUT ? out : work;
+    cudaError_t e;
+    if (p.kind == PASS_COPY) {
+      e = launch_copy(src, dst, nb * E, 1, 1, st);
+    } else {
+      PassLaunch l = launches[i];
+      if (b0 != 0 || nb != s.batch) {
+        PassDesc d = pass_desc(p, b0, nb, s.batch);
+        d.tw = l.d.tw;
+        d.epi_hi = l.d.epi_hi;
+        d.epi_lo = l.d.epi_lo;
+        l.d = d;
+        l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
+        e = prepare_launch(l);
+        if (e != cudaSuccess) return e;
+        l.grid = (int)std::min<int64_t>(d.tiles, 0x7fffffff);
+      }
+      if (l.d.tiles == 0) continue;
+      e = launch_pass(l, src, dst, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace gbfft

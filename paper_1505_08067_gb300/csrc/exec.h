@@ -1,0 +1,24 @@
+// Binding a plan's passes to device pointers and enqueueing them; shared by the
+// plan objects of the C ABI and by entry points that keep their tables and
+// workspace elsewhere.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "planner.h"
+
+namespace gbfft {
+
+// Fills launches[i] for every pass of `s` (tables = device twiddle tables of
+// s.table_elems entries).  Resolves and prepares each kernel.
+cudaError_t bind_launches(const PlanSpec& s, const cf* tables, PassLaunch* launches);
+
+// Enqueues the twiddle-table generation of `s` into `tables` on `st`.
+cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st);
+
+// Enqueues every pass for batch entries [b0, b0 + nb); `in`, `out` and `work`
+// already point at entry b0.
+cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const void* in,
+                           void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st);
+
+}  // namespace gbfft

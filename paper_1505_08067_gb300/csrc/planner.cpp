@@ -38,8 +38,8 @@ int block_log2_limit(const Caps& caps) {
   return best;
 }
 
-std::vector<int> default_schedule(int logL, int logR) {
-  std::vector<int> s;
+Sched default_schedule(int logL, int logR) {
+  Sched s;
   if (logL <= 0) return s;
   if (logR > logL) logR = logL;
   int full = logL / logR, rem = logL % logR;
@@ -48,7 +48,7 @@ std::vector<int> default_schedule(int logL, int logR) {
   return s;
 }
 
-static bool fill_launch(PassSpec& p, const Caps& caps, std::string& err) {
+static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
   const int L = 1 << p.logL;
   if (p.kind == PASS_COPY) {
     p.block = 256;
@@ -93,7 +93,7 @@ static bool fill_launch(PassSpec& p, const Caps& caps, std::string& err) {
   return true;
 }
 
-bool reshape_pass(PassSpec& p, int R, const std::vector<int>& rlogs, int G, const Caps& caps) {
+bool reshape_pass(PassSpec& p, int R, const Sched& rlogs, int G, const Caps& caps) {
   PassSpec q = p;
   q.R = R;
   q.rlogs = rlogs;
@@ -109,13 +109,13 @@ bool reshape_pass(PassSpec& p, int R, const std::vector<int>& rlogs, int G, cons
     if (q.smap == MAP_COLS) q.out.t = G;
     else q.out.t = q.out.g * G;
   }
-  std::string err;
+  const char* err = nullptr;
   if (!fill_launch(q, caps, err)) return false;
   p = q;
   return true;
 }
 
-static PassSpec fft_pass(int logL, int R, const std::vector<int>& sched) {
+static PassSpec fft_pass(int logL, int R, const Sched& sched) {
   PassSpec p;
   p.kind = PASS_FFT;
   p.logL = logL;
@@ -132,9 +132,9 @@ static int choose_R(int logL, int req) {
   return R;
 }
 
-static std::vector<int> sched_for(int logL, int R, uint32_t forced) {
+static Sched sched_for(int logL, int R, uint32_t forced) {
   if (forced) {
-    std::vector<int> s;
+    Sched s;
     for (int i = 0; i < 8 && ((forced >> (4 * i)) & 15); ++i) s.push_back((forced >> (4 * i)) & 15);
     return s;
   }
@@ -166,41 +166,40 @@ static PassSpec contiguous_pass(int logL, int64_t batch, int64_t units_per_batch
   return p;
 }
 
-PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int precision,
-                   const fft_plan_options_t* opt, const Caps& caps) {
-  PlanSpec s;
+void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direction,
+               int precision, const fft_plan_options_t* opt, const Caps& caps) {
+  s = PlanSpec();
   fft_plan_options_t o{};
   if (opt) o = *opt;
   auto fail = [&](fft_status_t st, const char* msg) {
     s.status = st;
-    s.error = msg;
+    snprintf(s.error, sizeof s.error, "%s", msg);
     s.passes.clear();
-    return s;
   };
-  if (!n) return fail(FFT_ERR_INVALID_ARG, "n is null");
-  if (dims != 1 && dims != 2) return fail(FFT_ERR_INVALID_ARG, "dims must be 1 or 2");
-  if (batch < 0) return fail(FFT_ERR_INVALID_ARG, "batch must be >= 0");
+  if (!n) { fail(FFT_ERR_INVALID_ARG, "n is null"); return; }
+  if (dims != 1 && dims != 2) { fail(FFT_ERR_INVALID_ARG, "dims must be 1 or 2"); return; }
+  if (batch < 0) { fail(FFT_ERR_INVALID_ARG, "batch must be >= 0"); return; }
   if (direction != FFT_FORWARD && direction != FFT_INVERSE)
-    return fail(FFT_ERR_INVALID_ARG, "direction must be FFT_FORWARD (-1) or FFT_INVERSE (+1)");
+    { fail(FFT_ERR_INVALID_ARG, "direction must be FFT_FORWARD (-1) or FFT_INVERSE (+1)"); return; }
   if (precision < FFT_PREC_FP32 || precision > FFT_PREC_TC_BF16X3)
-    return fail(FFT_ERR_INVALID_ARG, "unknown precision");
+    { fail(FFT_ERR_INVALID_ARG, "unknown precision"); return; }
   if (precision != FFT_PREC_FP32)
-    return fail(FFT_ERR_NOT_IMPLEMENTED, "tensor-core precision classes are not built yet");
+    { fail(FFT_ERR_NOT_IMPLEMENTED, "tensor-core precision classes are not built yet"); return; }
   if (o.radix && (o.radix < 2 || o.radix > 16 || !is_pow2(o.radix)))
-    return fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16");
+    { fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16"); return; }
   if (o.tile < 0 || o.tile > 1024 || (o.tile && !is_pow2(o.tile)))
-    return fail(FFT_ERR_INVALID_ARG, "tile option must be a power of two <= 1024");
+    { fail(FFT_ERR_INVALID_ARG, "tile option must be a power of two <= 1024"); return; }
   s.dims = dims;
   s.batch = batch;
   s.direction = direction;
   s.precision = precision;
   for (int d = 0; d < dims; ++d) {
-    if (!is_pow2(n[d])) return fail(FFT_ERR_UNSUPPORTED_SIZE, "each length must be a power of two >= 1");
+    if (!is_pow2(n[d])) { fail(FFT_ERR_UNSUPPORTED_SIZE, "each length must be a power of two >= 1"); return; }
     s.n[d] = n[d];
   }
   int bmax = block_log2_limit(caps);
   if (o.max_block_log2 > 0) {
-    if (o.max_block_log2 < 2) return fail(FFT_ERR_INVALID_ARG, "max_block_log2 must be >= 2");
+    if (o.max_block_log2 < 2) { fail(FFT_ERR_INVALID_ARG, "max_block_log2 must be >= 2"); return; }
     bmax = std::min(bmax, o.max_block_log2);
   }
   s.max_block_log2 = bmax;
@@ -210,7 +209,7 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
   if (dims == 1) {
     const int64_t N = n[0];
     const int logN = ilog2(N);
-    if (logN > 24) return fail(FFT_ERR_UNSUPPORTED_SIZE, "1D length must be <= 2^24");
+    if (logN > 24) { fail(FFT_ERR_UNSUPPORTED_SIZE, "1D length must be <= 2^24"); return; }
     if (N == 1) {
       PassSpec p;
       p.kind = PASS_COPY;
@@ -226,7 +225,7 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
       // rows of length N2 written transposed.  N1 <= N2 keeps the strided
       // column tiles wide.
       const int l1 = logN / 2, l2 = logN - l1;
-      if (l2 > bmax) return fail(FFT_ERR_UNSUPPORTED_SIZE, "length needs more than two passes");
+      if (l2 > bmax) { fail(FFT_ERR_UNSUPPORTED_SIZE, "length needs more than two passes"); return; }
       const int64_t N1 = int64_t(1) << l1, N2 = int64_t(1) << l2;
       const int64_t B = int64_t(1) << bmax;
       // pass 1: column FFTs of length N1 over N2 columns, twiddle on store
@@ -272,7 +271,7 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
     const int64_t rows = n[0], cols = n[1];
     const int lr = ilog2(rows), lc = ilog2(cols);
     if (lr > bmax || lc > bmax)
-      return fail(FFT_ERR_UNSUPPORTED_SIZE, "2D lengths must each fit one on-chip block (<= 2^14)");
+      { fail(FFT_ERR_UNSUPPORTED_SIZE, "2D lengths must each fit one on-chip block (<= 2^14)"); return; }
     if (rows == 1 && cols == 1) {
       PassSpec p;
       p.kind = PASS_COPY;
@@ -310,8 +309,8 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
   // launch shapes and twiddle tables
   int64_t off = 0;
   for (auto& p : s.passes) {
-    std::string err;
-    if (!fill_launch(p, caps, err)) return fail(FFT_ERR_INVALID_ARG, err.c_str());
+    const char* err = nullptr;
+    if (!fill_launch(p, caps, err)) { fail(FFT_ERR_INVALID_ARG, err); return; }
     if (p.kind != PASS_FFT) continue;
     p.tw_off.assign(p.rlogs.size(), 0);
     int64_t Ns = int64_t(1) << p.rlogs[0];
@@ -344,7 +343,6 @@ PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int
       p.grid = (int)g;
     }
   }
-  return s;
 }
 
 PassDesc pass_desc(const PassSpec& p, int64_t b0, int64_t nb, int64_t n_total) {

@@ -11,6 +11,32 @@
 
 namespace gbfft {
 
+// Fixed-capacity array: planning needs no heap allocation (a plan never has
+// more than 15 stages per pass, 4 passes or 40 twiddle segments).
+template <class T, int N>
+struct SmallVec {
+  T v[N];
+  int n = 0;
+  void push_back(const T& x) {
+    if (n < N) v[n++] = x;
+  }
+  void clear() { n = 0; }
+  void assign(int count, const T& x) {
+    n = count < N ? count : N;
+    for (int i = 0; i < n; ++i) v[i] = x;
+  }
+  int size() const { return n; }
+  bool empty() const { return n == 0; }
+  T& operator[](int i) { return v[i]; }
+  const T& operator[](int i) const { return v[i]; }
+  T* begin() { return v; }
+  T* end() { return v + n; }
+  const T* begin() const { return v; }
+  const T* end() const { return v + n; }
+  static constexpr int capacity() { return N; }
+};
+using Sched = SmallVec<int, 15>;
+
 enum { BUF_IN = 0, BUF_OUT = 1, BUF_WORK = 2 };
 enum { PASS_FFT = 0, PASS_COPY = 1 };
 
@@ -26,7 +52,7 @@ struct PassSpec {
   int R = 1;
   int G = 1;
   int lmap = MAP_ROWS, smap = MAP_ROWS;
-  std::vector<int> rlogs;      // radix schedule, stage order
+  Sched rlogs;                 // radix schedule, stage order
   int64_t tiles = 0, tiles_inner = 1, count_inner = 0;
   int64_t outer = 1;           // number of outer indices (batch of a multi-pass plan)
   Strides in{}, out{};
@@ -43,7 +69,7 @@ struct PassSpec {
   // PASS_COPY
   int64_t copy_count = 0, copy_in_stride = 1, copy_out_stride = 1;
   // twiddle-table offsets (complex entries) inside the plan's table allocation
-  std::vector<int32_t> tw_off;  // per stage (stage 0 unused)
+  SmallVec<int32_t, 15> tw_off;  // per stage (stage 0 unused)
   int64_t epi_hi_off = 0, epi_lo_off = 0;
 };
 
@@ -60,12 +86,12 @@ struct PlanSpec {
   int precision = FFT_PREC_FP32;
   int max_block_log2 = 14;
   bool generic_only = false;  // never pick compile-time specialisations
-  std::vector<PassSpec> passes;
-  std::vector<TwSegment> tables;
+  SmallVec<PassSpec, 4> passes;
+  SmallVec<TwSegment, 40> tables;
   int64_t table_elems = 0;
   int64_t work_elems = 0;
   fft_status_t status = FFT_OK;
-  std::string error;
+  char error[256] = {0};
 };
 
 // Largest on-chip block 2^k for these limits: the shared-memory exchange
@@ -75,14 +101,15 @@ int block_log2_limit(const Caps& caps);
 
 // Default radix schedule of a length-2^logL pass with 2^logR elements per
 // thread: as many full-radix stages as fit, the remainder radix last.
-std::vector<int> default_schedule(int logL, int logR);
+Sched default_schedule(int logL, int logR);
 
-PlanSpec make_plan(const int64_t* n, int dims, int64_t batch, int direction, int precision,
-                   const fft_plan_options_t* opt, const Caps& caps);
+// Heap-free: fills `s` in place.
+void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direction,
+               int precision, const fft_plan_options_t* opt, const Caps& caps);
 
 // Rebuild one pass for a different radix / schedule / tile (autotuner); keeps
 // geometry.  Returns false if the combination is invalid.
-bool reshape_pass(PassSpec& p, int R, const std::vector<int>& rlogs, int G, const Caps& caps);
+bool reshape_pass(PassSpec& p, int R, const Sched& rlogs, int G, const Caps& caps);
 
 // Fill PassDesc (without device pointers) for a pass restricted to
 // batch entries [b0, b0 + nb).

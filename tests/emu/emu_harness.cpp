@@ -174,10 +174,11 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
                 int64_t* special_passes) {
   Caps caps;
   caps.smem_optin = smem_optin;
-  PlanSpec s = make_plan(n, dims, batch, direction, FFT_PREC_FP32, opt, caps);
+  static PlanSpec s;
+  make_plan(s, n, dims, batch, direction, FFT_PREC_FP32, opt, caps);
   g = Ctx{};
   if (s.status != FFT_OK) {
-    snprintf(msg, msg_len, "plan failed: %s", s.error.c_str());
+    snprintf(msg, msg_len, "plan failed: %s", s.error);
     return -1;
   }
   const int64_t E = (dims == 1 ? n[0] : n[0] * n[1]) * batch;
