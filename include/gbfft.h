@@ -167,6 +167,30 @@ GBFFT_API fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batc
  * asynchronous CUDA error it raised. */
 GBFFT_API fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream);
 
+/*
+ * Allocation-free execution.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate GPU memory while they run -- a
+ * real-time radar loop that reserves all of its memory at start-up and cannot
+ * afford cudaMalloc's blocking and device synchronisation later, or code
+ * embedded in a framework that owns the device-memory budget.  It transforms
+ * `batch` contiguous 1D sequences of length n from `in` to `out` on `stream`
+ * (same data conventions as fft_execute) without a plan, and allocates
+ * nothing: the twiddle tables and the between-pass workspace live in one array
+ * the library reserves statically on every GPU that loads it (64 MiB of
+ * workspace plus 512 KiB of tables, held until the process exits).
+ *   - n is a power of two in [1, 2^23].  For n > 2^14 (two passes) n*batch
+ *     must be at most 2^23 complex elements; larger problems return
+ *     FFT_ERR_UNSUPPORTED_SIZE (create a plan instead).
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture begins.
+ *   - Every call uses the same array and leaves its contents behind.  Calls
+ *     whose GPU work overlaps (different streams, several host threads) race
+ *     and corrupt each other's results: serialise them.  Each call rewrites
+ *     everything it reads from the array, so nothing needs clearing.
+ */
+GBFFT_API fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction,
+                                           const void* in, void* out, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 GBFFT_API const char* fft_last_error(void);
 

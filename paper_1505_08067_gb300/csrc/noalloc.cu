@@ -1,0 +1,111 @@
+// fft_execute_noalloc: the batched 1D transform without a plan and without any
+// device allocation.
+//
+// Who needs it: callers that are not allowed to allocate GPU memory once they
+// are running -- for example a radar processing loop that reserves all of its
+// memory at start-up and must not stall later (cudaMalloc can block and
+// synchronise the device), or code that runs inside a host framework that owns
+// the whole device-memory budget and forbids allocations behind its back.
+// Such callers still own their input and output buffers; everything else the
+// transform needs (twiddle tables and, for lengths above 2^14, the workspace
+// between the two passes) lives in one array reserved statically below.
+//
+// The array is a file-scope __device__ variable, so every GPU that loads this
+// library holds it until the process exits.  Host code must not use its name
+// as an address (on the host it is only a stand-in): the device address is
+// looked up with cudaGetSymbolAddress once per device, the first time this
+// entry point runs on that device, and cached.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/gbfft.h"
+#include "exec.h"
+
+namespace gbfft {
+fft_status_t set_error(fft_status_t st, const char* msg);
+}
+
+using namespace gbfft;
+
+namespace {
+
+constexpr int64_t kWorkElems = int64_t(1) << 23;   // 64 MiB of complex64 workspace
+constexpr int64_t kTableElems = int64_t(1) << 16;  // 512 KiB of twiddle factors
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) float2 g_noalloc_scratch[kWorkElems + kTableElems];
+
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (which must be current).
+fft_status_t scratch_address(int dev, void** ptr) {
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(FFT_ERR_INVALID_ARG, "fft_execute_noalloc supports device ids 0..63");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return set_error(FFT_ERR_CUDA, "fft_execute_noalloc: cudaGetSymbolAddress of the static "
+                                     "scratch array failed");
+    }
+    g_addr[dev] = p;
+  }
+  *ptr = g_addr[dev];
+  return FFT_OK;
+}
+
+}  // namespace
+
+extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction,
+                                            const void* in, void* out, void* stream) {
+  if (n < 1 || (n & (n - 1)) || n > kWorkElems)
+    return set_error(FFT_ERR_UNSUPPORTED_SIZE,
+                     "fft_execute_noalloc: n must be a power of two between 1 and 2^23");
+  if (batch < 0) return set_error(FFT_ERR_INVALID_ARG, "batch must be >= 0");
+  if (batch == 0) return FFT_OK;
+  if (!in || !out) return set_error(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7))
+    return set_error(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned (complex64)");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(FFT_ERR_CUDA, "no usable CUDA device");
+  }
+  Caps caps;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+    caps.sm_count = v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+    caps.smem_optin = v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxThreadsPerBlock, dev) == cudaSuccess)
+    caps.max_block = v;
+  PlanSpec s;
+  make_plan(s, &n, 1, batch, direction, FFT_PREC_FP32, nullptr, caps);
+  if (s.status != FFT_OK) return set_error(s.status, s.error);
+  if (s.work_elems > kWorkElems)
+    return set_error(FFT_ERR_UNSUPPORTED_SIZE,
+                     "fft_execute_noalloc: n * batch needs more than the 64 MiB static workspace "
+                     "(at most 2^23 complex elements when n > 2^14); use fft_plan_create");
+  if (s.table_elems > kTableElems)
+    return set_error(FFT_ERR_UNSUPPORTED_SIZE,
+                     "fft_execute_noalloc: twiddle tables exceed the static area");
+  void* base = nullptr;
+  fft_status_t st = scratch_address(dev, &base);
+  if (st != FFT_OK) return st;
+  cf* work = static_cast<cf*>(base);
+  cf* tables = work + kWorkElems;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  PassLaunch launches[4];
+  cudaError_t e = enqueue_tables(s, tables, cs);
+  if (e == cudaSuccess) e = bind_launches(s, tables, launches);
+  if (e == cudaSuccess) e = enqueue_passes(s, launches, in, out, work, 0, batch, cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(FFT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return FFT_OK;
+}

@@ -58,6 +58,7 @@ _SIGS = {
                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(fft_plan_options_t)],
     "fft_execute": [_vp, _vp, _vp, _vp],
     "fft_execute_host": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "fft_execute_noalloc": [_i64, _i64, ctypes.c_int, _vp, _vp, _vp],
     "fft_plan_destroy": [_vp],
     "fft_plan_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "fft_plan_launch_count": [_vp, ctypes.POINTER(ctypes.c_int)],
@@ -147,6 +148,12 @@ def fft_execute(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
 def fft_execute_host(plan: int, host_in: int, host_out: int, dev_in: int, dev_out: int,
                      stream: int = 0) -> None:
     _check(load().fft_execute_host(plan, host_in, host_out, dev_in, dev_out, stream))
+
+
+def fft_execute_noalloc(n: int, batch: int, direction: int, in_ptr: int, out_ptr: int,
+                        stream: int = 0) -> None:
+    """Plan-free transform that allocates no device memory (see include/gbfft.h)."""
+    _check(load().fft_execute_noalloc(int(n), int(batch), direction, in_ptr, out_ptr, stream))
 
 
 def fft_plan_destroy(plan: int) -> None:
