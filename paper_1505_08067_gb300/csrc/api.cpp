@@ -45,7 +45,8 @@ struct fft_plan_s {
   int device = -1;
   PlanSpec spec;
   Caps caps;
-  void* tables = nullptr;  // cf[spec.table_elems]
+  void* tables = nullptr;  // cf[spec.table_elems], then the status word
+  int* status = nullptr;   // set by kernels whose bounded waits give up
   void* work = nullptr;    // cf[spec.work_elems]
   PassLaunch launches[4];  // whole-batch launches, device pointers filled
   // lazily created resources of fft_execute_host
@@ -89,13 +90,18 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
   p->caps = caps;
   p->spec = spec;
   cudaError_t e;
-  if (spec.table_elems > 0) {
-    e = cudaMalloc(&p->tables, (size_t)spec.table_elems * 8);
-    if (e != cudaSuccess) {
-      delete p;
-      cudaGetLastError();
-      return fail(FFT_ERR_OUT_OF_MEMORY, "twiddle tables: %s", cudaGetErrorString(e));
-    }
+  e = cudaMalloc(&p->tables, (size_t)spec.table_elems * 8 + 16);
+  if (e != cudaSuccess) {
+    delete p;
+    cudaGetLastError();
+    return fail(FFT_ERR_OUT_OF_MEMORY, "twiddle tables: %s", cudaGetErrorString(e));
+  }
+  p->status = reinterpret_cast<int*>(static_cast<char*>(p->tables) + (size_t)spec.table_elems * 8);
+  e = cudaMemset(p->status, 0, 16);
+  if (e != cudaSuccess) {
+    cudaFree(p->tables);
+    delete p;
+    return cuda_fail(e, "status word");
   }
   if (spec.work_elems > 0) {
     e = cudaMalloc(&p->work, (size_t)spec.work_elems * 8);
@@ -109,7 +115,8 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
   }
   e = enqueue_tables(spec, static_cast<cf*>(p->tables), 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = bind_launches(p->spec, static_cast<const cf*>(p->tables), p->launches);
+  if (e == cudaSuccess)
+    e = bind_launches(p->spec, p->caps, static_cast<const cf*>(p->tables), p->status, p->launches);
   if (e != cudaSuccess) {
     fft_plan_destroy(p);
     return cuda_fail(e, "twiddle generation");
@@ -123,7 +130,7 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
       memcpy(g_err, msg, sizeof msg);
       return st;
     }
-    e = bind_launches(p->spec, static_cast<const cf*>(p->tables), p->launches);
+    e = bind_launches(p->spec, p->caps, static_cast<const cf*>(p->tables), p->status, p->launches);
     if (e != cudaSuccess) {
       fft_plan_destroy(p);
       return cuda_fail(e, "kernel attributes");
@@ -309,6 +316,13 @@ fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronisation");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "asynchronous error");
+  int flag = 0;
+  e = cudaMemcpy(&flag, plan->status, sizeof flag, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status word");
+  if (flag) {
+    cudaMemset(plan->status, 0, sizeof flag);
+    return fail(FFT_ERR_TIMEOUT, "a kernel gave up waiting for its TMA copy (bounded wait)");
+  }
   return FFT_OK;
 }
 

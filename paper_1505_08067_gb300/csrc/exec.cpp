@@ -5,7 +5,8 @@
 
 namespace gbfft {
 
-cudaError_t bind_launches(const PlanSpec& s, const cf* tables, PassLaunch* launches) {
+cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables, int* status,
+                          PassLaunch* launches) {
   for (int i = 0; i < s.passes.size(); ++i) {
     const PassSpec& p = s.passes[i];
     PassLaunch l{};
@@ -14,6 +15,7 @@ cudaError_t bind_launches(const PlanSpec& s, const cf* tables, PassLaunch* launc
       l.d.tw = tables;
       l.d.epi_hi = p.epi ? tables + p.epi_hi_off : nullptr;
       l.d.epi_lo = p.epi ? tables + p.epi_lo_off : nullptr;
+      l.d.status = status;
       l.R = p.R;
       l.lmap = p.lmap;
       l.smap = p.smap;
@@ -23,6 +25,11 @@ cudaError_t bind_launches(const PlanSpec& s, const cf* tables, PassLaunch* launc
       l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
       cudaError_t e = prepare_launch(l);
       if (e != cudaSuccess) return e;
+      l.has_staged = resolve_staged(l.d, s.generic_only, &l.staged);
+      if (l.has_staged) {
+        e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
+        if (e != cudaSuccess) return e;
+      }
     }
     launches[i] = l;
   }
@@ -62,7 +69,13 @@ cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const 
         l.grid = (int)std::min<int64_t>(d.tiles, 0x7fffffff);
       }
       if (l.d.tiles == 0) continue;
-      e = launch_pass(l, src, dst, st);
+      if (l.has_staged && ((uintptr_t)src & 15) == 0) {
+        StagedLaunch sl = l.staged;
+        if (sl.grid > l.d.tiles) sl.grid = (int)l.d.tiles;
+        e = launch_staged(sl, l.d, src, dst, st);
+      } else {
+        e = launch_pass(l, src, dst, st);
+      }
     }
     if (e != cudaSuccess) return e;
   }

@@ -11,7 +11,9 @@ namespace gbfft {
 
 // Fills launches[i] for every pass of `s` (tables = device twiddle tables of
 // s.table_elems entries).  Resolves and prepares each kernel.
-cudaError_t bind_launches(const PlanSpec& s, const cf* tables, PassLaunch* launches);
+// `status` is a device int the staged kernels set if a bounded wait gives up.
+cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables, int* status,
+                          PassLaunch* launches);
 
 // Enqueues the twiddle-table generation of `s` into `tables` on `st`.
 cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st);

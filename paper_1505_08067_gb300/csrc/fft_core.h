@@ -23,9 +23,11 @@
 
 #if defined(__CUDACC__)
 #define GB_HD __host__ __device__ __forceinline__
+#define GB_HDC __host__ __device__
 #define GB_UNROLL _Pragma("unroll")
 #else
 #define GB_HD inline
+#define GB_HDC
 #define GB_UNROLL
 #endif
 
@@ -151,6 +153,7 @@ struct PassDesc {
   const cf* tw;
   const cf* epi_hi;
   const cf* epi_lo;
+  int* status;  // device word set to nonzero if a bounded wait gives up
 };
 
 GB_HD void thread_coords(int map, int tid, int T, int G, int& g, int& t) {

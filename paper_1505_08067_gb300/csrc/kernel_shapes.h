@@ -16,6 +16,14 @@
   GB_SHAPE(13, 0x1444, 4, 16, 1, 0, 0, true, 0)               \
   GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)
 
+// Contiguous transforms that run the staged kernel (fft_split.h): whole
+// transform per block, TMA prefetch of the next one, half-size exchanges.
+//   GB_STAGED(log2 L, schedule, stages, blocks per SM)
+#define GB_STAGED_SHAPES(GB_STAGED) \
+  GB_STAGED(12, 0x444, 3, 4)        \
+  GB_STAGED(13, 0x1444, 4, 2)       \
+  GB_STAGED(14, 0x2444, 4, 1)
+
 namespace gbfft {
 
 // Does pass descriptor `d` (run with R elements per thread and these maps)
@@ -30,6 +38,17 @@ GB_HD bool shape_matches(const PassDesc& d, int R, int lmap, int smap, int logL,
                          d.in.t == d.G * L && d.out.t == d.G * L;
   return d.logL == logL && s == sched && d.nst == nst && R == sR && d.G == G && lmap == slmap &&
          smap == ssmap && d.epi == epi && (!contig || is_contig);
+}
+
+// Is `d` a pass the staged kernel of this (log2 L, schedule, stages) runs?
+// One whole contiguous transform per tile, no four-step epilogue.
+GB_HD bool staged_shape_matches(const PassDesc& d, int logL, uint32_t sched, int nst) {
+  uint32_t s = 0;
+  for (int i = 0; i < d.nst && i < 8; ++i) s |= (uint32_t)d.rlog[i] << (4 * i);
+  if (d.nst > 8) return false;
+  const int64_t L = int64_t(1) << d.logL;
+  return d.G == 1 && d.epi == 0 && d.in.e == 1 && d.out.e == 1 && d.in.t == L && d.out.t == L &&
+         d.logL == logL && s == sched && d.nst == nst;
 }
 
 }  // namespace gbfft

@@ -16,7 +16,24 @@ struct PassLaunch {
   size_t smem;      // dynamic shared memory in bytes
   const void* fn = nullptr;  // resolved kernel (specialised or generic)
   bool specialised = false;
+  bool has_staged = false;   // a staged kernel exists for this shape (see below)
+  struct StagedLaunchData {
+    const void* fn = nullptr;
+    int grid = 0, block = 0;
+    size_t smem = 0;
+  } staged;
 };
+
+// The staged kernel for a contiguous pass (one transform per block, TMA
+// prefetch of the next); used when the source is 16-byte aligned.
+using StagedLaunch = PassLaunch::StagedLaunchData;
+
+// Fills `s` if a staged kernel exists for this pass shape.
+bool resolve_staged(const PassDesc& d, bool generic_only, StagedLaunch* s);
+// Opt-in shared memory and a persistent grid of (blocks per SM) x SMs.
+cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count);
+cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* in, void* out,
+                          cudaStream_t st);
 
 // Kernel for this pass shape: a compile-time specialisation when one matches,
 // else the generic kernel for (R, maps).

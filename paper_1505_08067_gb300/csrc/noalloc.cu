@@ -90,7 +90,7 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
     return set_error(FFT_ERR_UNSUPPORTED_SIZE,
                      "fft_execute_noalloc: n * batch needs more than the 64 MiB static workspace "
                      "(at most 2^23 complex elements when n > 2^14); use fft_plan_create");
-  if (s.table_elems > kTableElems)
+  if (s.table_elems + 2 > kTableElems)
     return set_error(FFT_ERR_UNSUPPORTED_SIZE,
                      "fft_execute_noalloc: twiddle tables exceed the static area");
   void* base = nullptr;
@@ -98,10 +98,11 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
   if (st != FFT_OK) return st;
   cf* work = static_cast<cf*>(base);
   cf* tables = work + kWorkElems;
+  int* status = reinterpret_cast<int*>(tables + (kTableElems - 2));
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   PassLaunch launches[4];
   cudaError_t e = enqueue_tables(s, tables, cs);
-  if (e == cudaSuccess) e = bind_launches(s, tables, launches);
+  if (e == cudaSuccess) e = bind_launches(s, caps, tables, status, launches);
   if (e == cudaSuccess) e = enqueue_passes(s, launches, in, out, work, 0, batch, cs);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_1505_08067_gb300", "csrc")
 LIB = os.path.join(HERE, "_emu.so")
 SRCS = [os.path.join(HERE, "emu_harness.cpp"), os.path.join(CSRC, "planner.cpp")]
-DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "planner.h", "kernel_shapes.h")] + \
+DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "fft_split.h", "planner.h", "kernel_shapes.h")] + \
     [os.path.join(ROOT, "include", "gbfft.h")]
 _lib = None
 
@@ -63,5 +63,6 @@ def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, specialised=True,
                        1 if specialised else 0, x.ctypes.data, out.ctypes.data, msg, 512,
                        ctypes.byref(sp))
     if stats is not None:
-        stats["special_passes"] = sp.value
+        stats["special_passes"] = sp.value % 1000
+        stats["staged_passes"] = sp.value // 1000
     return out, int(nerr), msg.value.decode()

@@ -12,6 +12,7 @@
 // only lets the index arithmetic be checked before a kernel runs.
 
 #include <array>
+#include <type_traits>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -20,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "fft_split.h"
 #include "fft_stage.h"
 #include "kernel_shapes.h"
 #include "planner.h"
@@ -42,6 +44,9 @@ struct Ctx {
   int64_t epoch = 0;
   int64_t errors = 0;
   int64_t special_passes = 0;
+  int64_t staged_passes = 0;
+  const cf* staging = nullptr;  // staged kernel: whole-transform buffer (TMA target)
+  int staging_len = 0;
   std::string first_error;
 };
 Ctx g;
@@ -72,6 +77,10 @@ struct CheckMem {
     return *p;
   }
   static cf lds(const cf* s, int i) {
+    if (g.staging && s == g.staging) {
+      if (i < 0 || i >= g.staging_len) { err("staging load out of bounds", i); return mk(0, 0); }
+      return s[i];
+    }
     if (i < 0 || i >= g.smem_len) { err("shared load out of bounds", i); return mk(0, 0); }
     if ((*g.slot_epoch)[i] != g.epoch) err("shared load of a slot not written in the last phase", i);
     return s[i];
@@ -139,6 +148,61 @@ bool run_special(int R, int lmap, int smap, const PassDesc& d, const cf* in, cf*
   }
   GB_SHAPES(GB_TRY)
 #undef GB_TRY
+  return false;
+}
+
+// Staged kernel (fft_split.h): the TMA copy of a tile into the staging buffer
+// becomes a memcpy; the phase order and barriers follow the kernel.
+template <class SH>
+void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
+  using B = SplitBody<SH, CheckMem>;
+  constexpr int R = SH::kR;
+  std::vector<cf> st(SH::kL), x(SH::kHalfSlots);
+  std::vector<int64_t> ep(x.size(), -1), wr(x.size(), -1);
+  g.slot_epoch = &ep;
+  g.slot_write = &wr;
+  g.smem_len = SH::kHalfSlots;
+  g.staging = st.data();
+  g.staging_len = SH::kL;
+  std::vector<std::array<cf, R>> V(SH::kT);
+  auto reg = [&](int t) -> cf (&)[R] { return *reinterpret_cast<cf(*)[R]>(V[t].data()); };
+  for (int64_t tile = 0; tile < d.tiles; ++tile) {
+    for (int a = 0; a < SH::kL; ++a) st[a] = CheckMem::ldg(in, tile * SH::kL + a);
+    for (int t = 0; t < SH::kT; ++t) {
+      if (d.conj_in) B::template first<true>(reg(t), st.data(), t);
+      else B::template first<false>(reg(t), st.data(), t);
+    }
+    auto exchange = [&](auto S_) {
+      constexpr int S = decltype(S_)::value;
+      ++g.epoch;
+      for (int t = 0; t < SH::kT; ++t) B::template write_half<S, 0>(reg(t), x.data(), t);
+      for (int t = 0; t < SH::kT; ++t) B::template read_half<S, 0>(reg(t), x.data(), t);
+      ++g.epoch;
+      for (int t = 0; t < SH::kT; ++t) B::template write_half<S, 1>(reg(t), x.data(), t);
+      for (int t = 0; t < SH::kT; ++t) {
+        B::template read_half<S, 1>(reg(t), x.data(), t);
+        B::template compute<S>(reg(t), d, t);
+      }
+    };
+    exchange(std::integral_constant<int, 0>());
+    if constexpr (SH::kNst > 2) exchange(std::integral_constant<int, 1>());
+    if constexpr (SH::kNst > 3) exchange(std::integral_constant<int, 2>());
+    for (int t = 0; t < SH::kT; ++t) {
+      if (d.conj_out) B::template store<true>(reg(t), out + tile * SH::kL, t);
+      else B::template store<false>(reg(t), out + tile * SH::kL, t);
+    }
+  }
+  g.staging = nullptr;
+}
+
+bool run_staged(const PassDesc& d, const cf* in, cf* out) {
+#define GB_TRY_STAGED(LOGL, SCHED, NST, MINB)                 \
+  if (staged_shape_matches(d, LOGL, SCHED, NST)) {            \
+    run_staged_t<SplitShape<LOGL, SCHED, NST>>(d, in, out);   \
+    return true;                                              \
+  }
+  GB_STAGED_SHAPES(GB_TRY_STAGED)
+#undef GB_TRY_STAGED
   return false;
 }
 
@@ -217,7 +281,8 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
     g.out_hits = &hits;
     g.tw = tables.data();
     g.tw_len = s.table_elems;
-    if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
+    if (specialised && !s.generic_only && run_staged(d, src, dst)) ++g.staged_passes;
+    else if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
     else if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
     else if (p.lmap == MAP_COLS && p.smap == MAP_COLS) run_maps<1, 1>(p.R, d, src, dst);
     else run_maps<0, 1>(p.R, d, src, dst);
@@ -225,7 +290,7 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
       if (hits[i] != 1) { err("output element not written exactly once", i); break; }
   }
   snprintf(msg, msg_len, "%s", g.first_error.c_str());
-  if (special_passes) *special_passes = g.special_passes;
+  if (special_passes) *special_passes = g.special_passes + 1000 * g.staged_passes;
   return g.errors;
 }
 

@@ -41,7 +41,9 @@ def test_compile_time_shapes(oracle, logn, direction, specialised):
     x = synth.uniform(9, batch, n)
     y, nerr, msg = emu.run(x, (n,), direction=direction, specialised=specialised, stats=st)
     assert nerr == 0, msg
-    assert st["special_passes"] == (1 if specialised else 0)
+    expect_staged = specialised and logn >= 12      # staged kernel for 2^12 .. 2^14
+    assert st["staged_passes"] == (1 if expect_staged else 0)
+    assert st["special_passes"] == (1 if specialised and not expect_staged else 0)
     assert np.max(oracle.rel_l2(y, oracle.fft(x, direction))) <= 1e-6 * logn
 
 
