@@ -195,7 +195,10 @@ def ours(args, rank: int, world: int) -> None:
     plans = {}
     for lg in LOGS:
         for d in DIRS:
-            plans[(lg, d)] = gbfft.Plan(2 ** lg, E >> lg, d, autotune=args.autotune)
+            opts = {"autotune": args.autotune}
+            if args.variant:
+                opts["variant"] = args.variant
+            plans[(lg, d)] = gbfft.Plan(2 ** lg, E >> lg, d, **opts)
     launches_per_step = sum(p.launch_count for p in plans.values())
     stream = torch.cuda.current_stream()
     order = [(lg, d) for lg in LOGS for d in DIRS]
@@ -312,7 +315,7 @@ def ours(args, rank: int, world: int) -> None:
             "config": {"workload": WORKLOAD, "sizes": [2 ** l for l in LOGS],
                        "elements_per_launch": E, "precision": "FP32",
                        "l2": "inputs larger than L2 (1 GiB per launch), no flush",
-                       "autotune": bool(args.autotune),
+                       "autotune": bool(args.autotune), "variant": args.variant,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(frac, 4),
@@ -340,6 +343,9 @@ def main() -> None:
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--autotune", type=int, default=0)
     ap.add_argument("--only", type=int, default=0, help="run only N = 2^ONLY (profiling)")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="contiguous-pass kernel variant (0 library choice, 1 register, "
+                         "2 TMA-staged, 3 L2 prefetch)")
     ap.add_argument("--total-log", type=int, default=TOTAL_LOG,
                     help="log2 of elements per launch (profiling of smaller cases)")
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -100,6 +100,12 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *   tile          transforms per thread block for passes that allow a choice.
  *   generic       1: run every pass with the run-time-parameter kernel even
  *                 where a compile-time specialisation of the shape exists.
+ *   variant       kernel variant for batched contiguous passes: 0 library
+ *                 choice, 1 register kernel (one tile per block), 2 TMA-staged
+ *                 kernel (N = 2^12..2^14: the next transform is copied into
+ *                 shared memory while the current one is computed), 3 register
+ *                 kernel on a persistent grid that prefetches its next tile
+ *                 into L2.
  */
 typedef struct {
   int autotune;
@@ -108,7 +114,8 @@ typedef struct {
   int max_block_log2;
   int tile;
   int generic;      /* 1: never use the compile-time specialised kernels (testing) */
-  int reserved[7];
+  int variant;      /* contiguous-pass kernel variant, see above */
+  int reserved[6];
 } fft_plan_options_t;
 
 GBFFT_API fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,

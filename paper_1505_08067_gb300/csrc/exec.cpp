@@ -25,10 +25,20 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
       cudaError_t e = prepare_launch(l);
       if (e != cudaSuccess) return e;
-      l.has_staged = resolve_staged(l.d, s.generic_only, &l.staged);
+      const bool want_staged = p.variant == 0 || p.variant == 2;
+      l.has_staged = want_staged && resolve_staged(l.d, s.generic_only, &l.staged);
       if (l.has_staged) {
         e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
         if (e != cudaSuccess) return e;
+      }
+      if (p.variant == 3 && l.specialised && p.batch_is_tiles) {
+        int per_sm = 0;
+        e = occupancy(l, &per_sm);
+        if (e != cudaSuccess) return e;
+        const int64_t g = (int64_t)std::max(per_sm, 1) * caps.sm_count;
+        l.grid = (int)std::min<int64_t>(g, l.grid);
+        l.persistent_grid = l.grid;
+        l.d.l2_prefetch = 1;
       }
     }
     launches[i] = l;
@@ -66,7 +76,9 @@ cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const 
         l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
         e = prepare_launch(l);
         if (e != cudaSuccess) return e;
-        l.grid = (int)std::min<int64_t>(d.tiles, 0x7fffffff);
+        d.l2_prefetch = launches[i].d.l2_prefetch;
+        l.d.l2_prefetch = d.l2_prefetch;
+        l.grid = (int)std::min<int64_t>(d.tiles, l.persistent_grid ? l.persistent_grid : 0x7fffffff);
       }
       if (l.d.tiles == 0) continue;
       if (l.has_staged && ((uintptr_t)src & 15) == 0) {

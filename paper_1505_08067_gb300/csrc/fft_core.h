@@ -150,6 +150,7 @@ struct PassDesc {
   int32_t conj_in, conj_out;  // backward transform = conj(forward(conj(x)))
   int32_t epi;                // 1: multiply output (n2, k1) by w_N^{n2*k1}
   int32_t epi_lo_bits;        // w_N^m = hi[m >> lo_bits] * lo[m & (2^lo_bits - 1)]
+  int32_t l2_prefetch;        // contiguous passes on a persistent grid: prefetch next tile
   const cf* tw;
   const cf* epi_hi;
   const cf* epi_lo;

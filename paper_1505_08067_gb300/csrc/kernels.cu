@@ -60,6 +60,19 @@ stockham_pass(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
     const typename B::Tile tl = B::tile_of(d, tile);
+    if constexpr (TR::kContig) {
+      // Persistent grids: pull this block's next tile into L2 while the
+      // current one is computed (one 128-byte line per thread and pass of
+      // this loop), so its stage-0 loads hit L2 instead of DRAM.
+      if (d.l2_prefetch && tile + gridDim.x < d.tiles) {
+        const int64_t L = int64_t(1) << TR::logL(d);
+        const int64_t tile_elems = (int64_t)TR::G(d) * L;
+        const int64_t valid = min(tile_elems, d.count_inner * L - (tile + gridDim.x) * tile_elems);
+        const char* base = reinterpret_cast<const char*>(in + (tile + gridDim.x) * tile_elems);
+        for (int64_t line = tid; line * 16 < valid; line += blockDim.x)
+          asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(base + line * 128));
+      }
+    }
     cf v[R];
     B::first(v, d, in, out, sm, tl, tid);
     int Ns = 1 << TR::rlog(d, 0);

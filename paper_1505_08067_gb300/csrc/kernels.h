@@ -17,6 +17,7 @@ struct PassLaunch {
   const void* fn = nullptr;  // resolved kernel (specialised or generic)
   bool specialised = false;
   bool has_staged = false;   // a staged kernel exists for this shape (see below)
+  int persistent_grid = 0;   // nonzero: grid capped at resident blocks (L2-prefetch variant)
   struct StagedLaunchData {
     const void* fn = nullptr;
     int grid = 0, block = 0;

@@ -187,6 +187,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
     { fail(FFT_ERR_NOT_IMPLEMENTED, "tensor-core precision classes are not built yet"); return; }
   if (o.radix && (o.radix < 2 || o.radix > 16 || !is_pow2(o.radix)))
     { fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16"); return; }
+  if (o.variant < 0 || o.variant > 3) { fail(FFT_ERR_INVALID_ARG, "variant must be 0..3"); return; }
   if (o.tile < 0 || o.tile > 1024 || (o.tile && !is_pow2(o.tile)))
     { fail(FFT_ERR_INVALID_ARG, "tile option must be a power of two <= 1024"); return; }
   s.dims = dims;
@@ -309,6 +310,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   // launch shapes and twiddle tables
   int64_t off = 0;
   for (auto& p : s.passes) {
+    if (p.batch_is_tiles) p.variant = o.variant;
     const char* err = nullptr;
     if (!fill_launch(p, caps, err)) { fail(FFT_ERR_INVALID_ARG, err); return; }
     if (p.kind != PASS_FFT) continue;
@@ -402,7 +404,8 @@ std::string describe(const PlanSpec& s) {
         << ",\"out\":[" << p.out.o << "," << p.out.t << "," << p.out.g << "," << p.out.e << "]"
         << ",\"block\":" << p.block << ",\"grid\":" << p.grid << ",\"smem\":" << p.smem
         << ",\"pitch\":" << p.pitch << ",\"epi\":" << p.epi << ",\"epi_logN\":" << p.epi_logN
-        << ",\"conj_in\":" << p.conj_in << ",\"conj_out\":" << p.conj_out;
+        << ",\"conj_in\":" << p.conj_in << ",\"conj_out\":" << p.conj_out
+        << ",\"variant\":" << p.variant;
     } else {
       o << ",\"count\":" << p.copy_count;
     }

@@ -64,6 +64,7 @@ struct PassSpec {
   int smem_elems = 0;
   size_t smem = 0;
   int grid = 0;
+  int variant = 0;              // contiguous passes: 0 auto, 1 register, 2 staged, 3 L2 prefetch
   bool batch_is_tiles = false;  // contiguous pass: batch maps to tiles of G transforms
   int64_t units_per_batch = 1;  // contiguous pass: transforms per batch entry
   // PASS_COPY

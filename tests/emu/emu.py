@@ -20,7 +20,8 @@ _lib = None
 class Options(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int), ("radix", ctypes.c_int), ("schedule", ctypes.c_uint32),
                 ("max_block_log2", ctypes.c_int), ("tile", ctypes.c_int),
-                ("generic", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("generic", ctypes.c_int), ("variant", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 def load():

@@ -272,3 +272,18 @@ def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
             gb.fft_plan_sync_status(p.handle, torch.cuda.current_stream().cuda_stream)
         y = out.view(batch, n).cpu().numpy()
         assert np.max(oracle.rel_l2(y, oracle.fft(x_np))) <= _tol(n), shift
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("logn", [8, 11, 12, 13, 14])
+def test_kernel_variants(gb, oracle, variant, logn):
+    """Each contiguous-pass kernel variant, on a batch spanning several waves of
+    the persistent grid and a ragged last tile."""
+    n = 2 ** logn
+    batch = 2 ** 21 // n + 3
+    x = synth.uniform(9200 + logn, batch, n)
+    for d in (-1, 1):
+        y = _run(gb, x, (n,), d, variant=variant)
+        idx = np.unique(np.r_[0, batch - 1, np.arange(1, batch, 97)])
+        ref = oracle.fft_select(x, idx, d)
+        assert np.max(oracle.rel_l2(y[idx], ref)) <= _tol(n)
