@@ -180,6 +180,83 @@ def reference_arm(args, rank: int) -> None:
 
 # ------------------------------------------------------------------ ours ----
 
+def ours_other(args, rank: int, world: int) -> None:
+    """Other configs (not the headline line): multi-pass 1D and the 2D SAR frame.
+    One step = every item forward and inverse; roofline with 16 B per element
+    per pass (two passes each)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1505_08067_gb300 import gbfft, synth
+
+    if args.workload == "multipass":
+        items = [((2 ** 20,), 64), ((2 ** 22,), 16), ((2 ** 24,), 4)]
+        desc = ("large multi-pass 1D complex64 FFTs: N=2^20 batch 64, N=2^22 batch 16, "
+                "N=2^24 batch 4 (2^26 elements each), forward and inverse")
+    else:
+        items = [((4096, 8192), 1)]
+        desc = ("2D SAR frame 4096 azimuth x 8192 range complex64 (LFM chirp echoes, "
+                "50 scatterers, SNR 10 dB), forward and inverse")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    E = max(int(np.prod(s)) * b for s, b in items)
+    if args.workload == "sar":
+        x = torch.from_numpy(synth.sar_frame(31).reshape(-1)).to(dev)
+    else:
+        x = torch.from_numpy(synth.uniform(3, 1, E)[0]).to(dev)
+    y = torch.empty_like(x)
+    plans, order = {}, []
+    for shape, batch in items:
+        for d in DIRS:
+            key = (shape, d)
+            plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d)
+            order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for key, e, _lg in order:
+            plans[key].execute(x[:e], y[:e], stream)
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in order] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    bnd = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in range(args.steps):
+        for i, (key, e, _lg) in enumerate(order):
+            ev[s][i][0].record(stream)
+            plans[key].execute(x[:e], y[:e], stream)
+            ev[s][i][1].record(stream)
+    bnd.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(bnd)
+    flops = sum(5.0 * e * lg for _k, e, lg in order)
+    peaks = load_peaks()
+    per = {}
+    for i, (key, e, lg) in enumerate(order):
+        t = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
+        passes = len(plans[key].describe()["passes"])
+        per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'}"] = {
+            "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
+            "passes": passes, "gbs": round(16.0 * passes * e / (t * 1e-3) / 1e9, 1),
+            "frac": round(16.0 * passes * e / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+    if rank == 0:
+        tot_bytes = sum(16.0 * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
+        print(json.dumps({
+            "metric": METRIC, "value": world * flops * args.steps / (ms * 1e-3) / 1e9,
+            "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "dtype": "f32", "data": "synthetic", "config": {"workload": desc},
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                         "achieved": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9, 1),
+                         "frac": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
+            "per_item": per}))
+    for p in plans.values():
+        p.close()
+
+
 def ours(args, rank: int, world: int) -> None:
     import numpy as np
     import torch
@@ -341,6 +418,9 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["sweep", "multipass", "sar"], default="sweep",
+                    help="sweep: the headline batched N=2^8..2^14 line; multipass / sar: "
+                         "the large-transform configs, reported as separate lines")
     ap.add_argument("--autotune", type=int, default=0)
     ap.add_argument("--only", type=int, default=0, help="run only N = 2^ONLY (profiling)")
     ap.add_argument("--variant", type=int, default=0,
@@ -367,7 +447,10 @@ def main() -> None:
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    ours(args, rank, world)
+    if args.workload == "sweep":
+        ours(args, rank, world)
+    else:
+        ours_other(args, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -14,7 +14,16 @@
   GB_SHAPE(11, 0x344, 3, 16, 2, 0, 0, true, 0)                \
   GB_SHAPE(12, 0x444, 3, 16, 1, 0, 0, true, 0)                \
   GB_SHAPE(13, 0x1444, 4, 16, 1, 0, 0, true, 0)               \
-  GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)
+  GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)               \
+  /* four-step N = 2^20, 2^22, 2^24: column pass (twiddle on store) and */ \
+  /* row pass (transposed store); 2D column (azimuth) pass of 4096 rows */ \
+  GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 1)              \
+  GB_SHAPE(10, 0x244, 3, 16, 16, 0, 1, false, 0)              \
+  GB_SHAPE(11, 0x344, 3, 16, 8, 1, 1, false, 1)               \
+  GB_SHAPE(11, 0x344, 3, 16, 8, 0, 1, false, 0)               \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 1)               \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 0, 1, false, 0)               \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)
 
 // Contiguous transforms that run the staged kernel (fft_split.h): whole
 // transform per block, TMA prefetch of the next one, half-size exchanges.
