@@ -198,6 +198,8 @@ def ours_other(args, rank: int, world: int) -> None:
         items = [((4096, 8192), 1)]
         desc = ("2D SAR frame 4096 azimuth x 8192 range complex64 (LFM chirp echoes, "
                 "50 scatterers, SNR 10 dB), forward and inverse")
+    if args.only:
+        items = [it for it in items if int(np.log2(np.prod(it[0]))) == args.only] or items
     dev = torch.device("cuda", torch.cuda.current_device())
     E = max(int(np.prod(s)) * b for s, b in items)
     if args.workload == "sar":
@@ -209,7 +211,8 @@ def ours_other(args, rank: int, world: int) -> None:
     for shape, batch in items:
         for d in DIRS:
             key = (shape, d)
-            plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d)
+            opts = {"epilogue": args.epilogue} if args.epilogue else {}
+            plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, **opts)
             order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -426,6 +429,8 @@ def main() -> None:
     ap.add_argument("--variant", type=int, default=0,
                     help="contiguous-pass kernel variant (0 library choice, 1 register, "
                          "2 TMA-staged, 3 L2 prefetch)")
+    ap.add_argument("--epilogue", type=int, default=0,
+                    help="four-step twiddle source for two-pass plans (0 library choice)")
     ap.add_argument("--total-log", type=int, default=TOTAL_LOG,
                     help="log2 of elements per launch (profiling of smaller cases)")
     ap.add_argument("--e2e-steps", type=int, default=3)

@@ -106,6 +106,12 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *                 shared memory while the current one is computed), 3 register
  *                 kernel on a persistent grid that prefetches its next tile
  *                 into L2.
+ *   epilogue      how a two-pass 1D plan finds the twiddle w_N^{n2 k1} applied
+ *                 between its passes: 0 library choice, 1 two small tables
+ *                 (w = hi[m >> b] * lo[m mod 2^b]), 2 one table of N entries laid
+ *                 out like the first pass's output (coalesced loads, N*8 bytes
+ *                 more plan memory), 3 computed in-kernel from the exact FP32
+ *                 angle 2m/N with sincospi.
  */
 typedef struct {
   int autotune;
@@ -115,7 +121,8 @@ typedef struct {
   int tile;
   int generic;      /* 1: never use the compile-time specialised kernels (testing) */
   int variant;      /* contiguous-pass kernel variant, see above */
-  int reserved[6];
+  int epilogue;     /* four-step twiddle source, see above */
+  int reserved[5];
 } fft_plan_options_t;
 
 GBFFT_API fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,

@@ -13,8 +13,8 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
     if (p.kind == PASS_FFT) {
       l.d = pass_desc(p, 0, s.batch, s.batch);
       l.d.tw = tables;
-      l.d.epi_hi = p.epi ? tables + p.epi_hi_off : nullptr;
-      l.d.epi_lo = p.epi ? tables + p.epi_lo_off : nullptr;
+      l.d.epi_hi = (p.epi == 1 || p.epi == 2) ? tables + p.epi_hi_off : nullptr;
+      l.d.epi_lo = (p.epi == 1 || p.epi == 2) ? tables + p.epi_lo_off : nullptr;
       l.d.status = status;
       l.R = p.R;
       l.lmap = p.lmap;

@@ -148,8 +148,12 @@ struct PassDesc {
   int64_t count_inner; // valid transforms per outer index (ragged last tile)
   Strides in, out;
   int32_t conj_in, conj_out;  // backward transform = conj(forward(conj(x)))
-  int32_t epi;                // 1: multiply output (n2, k1) by w_N^{n2*k1}
-  int32_t epi_lo_bits;        // w_N^m = hi[m >> lo_bits] * lo[m & (2^lo_bits - 1)]
+  int32_t epi;                // multiply output (n2, k1) by w_N^{n2*k1}; how w is found:
+                              //   1 two-level tables hi[m >> lo_bits] * lo[m & (2^lo_bits - 1)]
+                              //   2 full table in the output's layout: epi_lo[n2 + k1 * N2]
+                              //   3 computed: sincospi of the exact FP32 angle 2 m / N
+  int32_t epi_lo_bits;
+  int32_t epi_logN;
   int32_t l2_prefetch;        // contiguous passes on a persistent grid: prefetch next tile
   const cf* tw;
   const cf* epi_hi;

@@ -190,19 +190,27 @@ GB_UNROLL
     const int64_t col = tl.inner * TR::G(d) + g;  // column index n2 in a four-step pass
     const int64_t e = TR::out_e(d);
     cf* tb = out + (tl.outer * d.out.o + tl.inner * d.out.t + (int64_t)g * TR::out_g(d));
-    const bool epi = TR::kEpi < 0 ? d.epi != 0 : TR::kEpi != 0;
+    const int epi = TR::kEpi < 0 ? d.epi : TR::kEpi;
+    // full-table mode: the twiddle of output (col, a) sits at col + a * columns
+    const cf* tfull = d.epi_lo + col;
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * TR::T(d) + t;
       cf* p = tb + (int64_t)jb * e;
+      const cf* pt = tfull + (int64_t)jb * d.count_inner;
 GB_UNROLL
       for (int i = 0; i < RR; ++i) {
         cf x = v[q * RR + i];
-        if (epi) {
+        if (epi == 1) {
           const int64_t m = col * (int64_t)(jb + i * Ns);
           const cf w = cmul(Mem::ldtw(d.epi_hi + (m >> d.epi_lo_bits)),
                             Mem::ldtw(d.epi_lo + (m & ((int64_t(1) << d.epi_lo_bits) - 1))));
           x = cmul(x, w);
+        } else if (epi == 2) {
+          x = cmul(x, Mem::ldtw(pt + (int64_t)(i * Ns) * d.count_inner));
+        } else if (epi == 3) {
+          const int64_t m = col * (int64_t)(jb + i * Ns);  // < N <= 2^24: exact in FP32
+          x = cmul(x, Mem::rotor(m, d.epi_logN));
         }
         Mem::stg(p, (int64_t)(i * Ns) * e, SWAP ? mk(x.y, x.x) : x);
       }

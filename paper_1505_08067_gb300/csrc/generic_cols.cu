@@ -1,0 +1,17 @@
+// Generic stockham_pass instantiations (every parameter from the
+// descriptor) for load map 1 / store map 1; see kernels.cu.
+#include "kernels_impl.cuh"
+
+namespace gbfft {
+
+const void* generic_kernel_cols(int R) {
+  switch (R) {
+    case 2: return (const void*)kfn<2, 1, 1, RtTraits>();
+    case 4: return (const void*)kfn<4, 1, 1, RtTraits>();
+    case 8: return (const void*)kfn<8, 1, 1, RtTraits>();
+    case 16: return (const void*)kfn<16, 1, 1, RtTraits>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace gbfft

@@ -6,22 +6,29 @@
 // kernel, which computes the same transform with run-time parameters.
 #pragma once
 
-#define GB_SHAPES(GB_SHAPE)                                   \
-  /* batched contiguous transforms, radix-16 stages, remainder last */ \
+#define GB_SHAPES(GB_SHAPE) GB_SHAPES_CONTIG(GB_SHAPE) GB_SHAPES_FOURSTEP(GB_SHAPE)
+
+/* batched contiguous transforms, radix-16 stages, remainder last */
+#define GB_SHAPES_CONTIG(GB_SHAPE)                            \
   GB_SHAPE(8, 0x44, 2, 16, 16, 0, 0, true, 0)                 \
   GB_SHAPE(9, 0x144, 3, 16, 8, 0, 0, true, 0)                 \
   GB_SHAPE(10, 0x244, 3, 16, 4, 0, 0, true, 0)                \
   GB_SHAPE(11, 0x344, 3, 16, 2, 0, 0, true, 0)                \
   GB_SHAPE(12, 0x444, 3, 16, 1, 0, 0, true, 0)                \
   GB_SHAPE(13, 0x1444, 4, 16, 1, 0, 0, true, 0)               \
-  GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)               \
-  /* four-step N = 2^20, 2^22, 2^24: column pass (twiddle on store) and */ \
-  /* row pass (transposed store); 2D column (azimuth) pass of 4096 rows */ \
-  GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 1)              \
+  GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)
+
+/* four-step N = 2^20, 2^22, 2^24: column pass (twiddle on store, full-table */
+/* or computed) and row pass (transposed store); 2D column pass of 4096 rows */
+#define GB_SHAPES_FOURSTEP(GB_SHAPE)                          \
+  GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 2)              \
+  GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 3)              \
   GB_SHAPE(10, 0x244, 3, 16, 16, 0, 1, false, 0)              \
-  GB_SHAPE(11, 0x344, 3, 16, 8, 1, 1, false, 1)               \
+  GB_SHAPE(11, 0x344, 3, 16, 8, 1, 1, false, 2)               \
+  GB_SHAPE(11, 0x344, 3, 16, 8, 1, 1, false, 3)               \
   GB_SHAPE(11, 0x344, 3, 16, 8, 0, 1, false, 0)               \
-  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 1)               \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 2)               \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 3)               \
   GB_SHAPE(12, 0x444, 3, 16, 4, 0, 1, false, 0)               \
   GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)
 

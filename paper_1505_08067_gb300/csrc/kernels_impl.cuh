@@ -1,0 +1,239 @@
+// Kernel templates shared by the translation units that instantiate them
+// (kernels.cu: generic kernels and launch glue; shapes_contig.cu and
+// shapes_fourstep.cu: compile-time shapes).  See kernels.cu for an overview.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fft_split.h"
+#include "fft_stage.h"
+#include "kernel_shapes.h"
+#include "kernels.h"
+
+namespace gbfft {
+
+using KernelFn = void (*)(const cf*, cf*, PassDesc);
+
+struct DevMem {
+  // Input is read exactly once: stream it with an evict-first hint.
+  GB_HD static cf ldg(const cf* p, int64_t off) {
+#ifdef __CUDA_ARCH__
+    float2 r = __ldcs(reinterpret_cast<const float2*>(p) + off);
+    return mk(r.x, r.y);
+#else
+    return p[off];
+#endif
+  }
+  GB_HD static void stg(cf* p, int64_t off, cf v) {
+#ifdef __CUDA_ARCH__
+    *(reinterpret_cast<float2*>(p) + off) = make_float2(v.x, v.y);
+#else
+    p[off] = v;
+#endif
+  }
+  GB_HD static cf ldtw(const cf* p) {
+#ifdef __CUDA_ARCH__
+    float2 r = __ldg(reinterpret_cast<const float2*>(p));
+    return mk(r.x, r.y);
+#else
+    return *p;
+#endif
+  }
+  GB_HD static cf lds(const cf* s, int i) { return s[i]; }
+  GB_HD static void sts(cf* s, int i, cf v) { s[i] = v; }
+  // w_N^m for 0 <= m < N = 2^logN <= 2^24: the angle 2m/N is exact in FP32.
+  GB_HD static cf rotor(int64_t m, int logN) {
+#ifdef __CUDA_ARCH__
+    float s, c;
+    sincospif(__int2float_rn((int)m) * __int_as_float((127 + 1 - logN) << 23), &s, &c);
+    return mk(c, -s);
+#else
+    (void)m;
+    (void)logN;
+    return mk(1.f, 0.f);
+#endif
+  }
+};
+
+template <int R, int LMAP, int SMAP, class TR>
+__global__ void __launch_bounds__(1024)
+stockham_pass(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* sm = reinterpret_cast<cf*>(smem_raw);
+  using B = PassBody<R, LMAP, SMAP, DevMem, TR>;
+  const int tid = threadIdx.x;
+  for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
+    const typename B::Tile tl = B::tile_of(d, tile);
+    if constexpr (TR::kContig) {
+      // Persistent grids: pull this block's next tile into L2 while the
+      // current one is computed (one 128-byte line per thread and pass of
+      // this loop), so its stage-0 loads hit L2 instead of DRAM.
+      if (d.l2_prefetch && tile + gridDim.x < d.tiles) {
+        const int64_t L = int64_t(1) << TR::logL(d);
+        const int64_t tile_elems = (int64_t)TR::G(d) * L;
+        const int64_t valid = min(tile_elems, d.count_inner * L - (tile + gridDim.x) * tile_elems);
+        const char* base = reinterpret_cast<const char*>(in + (tile + gridDim.x) * tile_elems);
+        for (int64_t line = tid; line * 16 < valid; line += blockDim.x)
+          asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(base + line * 128));
+      }
+    }
+    cf v[R];
+    B::first(v, d, in, out, sm, tl, tid);
+    int Ns = 1 << TR::rlog(d, 0);
+    if constexpr (TR::kMaxStages < 15) {
+      // compile-time schedule: unrolled, every radix and offset a constant
+#pragma unroll
+      for (int s = 1; s < TR::kMaxStages; ++s) {
+        __syncthreads();
+        B::read(v, d, s, Ns, out, sm, tl, tid);
+        if (s < TR::kMaxStages - 1) {
+          __syncthreads();
+          B::write(v, d, s, Ns, sm, tid);
+        }
+        Ns <<= TR::rlog(d, s);
+      }
+    } else {
+#pragma unroll 1
+      for (int s = 1; s < d.nst; ++s) {
+        __syncthreads();
+        B::read(v, d, s, Ns, out, sm, tl, tid);
+        if (s < d.nst - 1) {
+          __syncthreads();
+          B::write(v, d, s, Ns, sm, tid);
+        }
+        Ns <<= d.rlog[s];
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next tile
+  }
+}
+
+// ------------------------------------------------------- staged pass --
+// TMA bulk copy global -> shared, mbarrier completion (sm_90+ PTX).
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Expect `bytes` on the barrier and start the copies (one thread).  src and
+// dst are 16-byte aligned and bytes is a multiple of 16.
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  const uint32_t b = smem_u32(bar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
+               : "memory");
+  constexpr uint32_t kChunk = 32768;
+  for (uint32_t off = 0; off < bytes; off += kChunk) {
+    const uint32_t n = bytes - off < kChunk ? bytes - off : kChunk;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(static_cast<char*>(dst) + off)),
+        "l"(static_cast<const char*>(src) + off), "r"(n), "r"(b)
+        : "memory");
+  }
+}
+
+// Wait for phase `parity` of the barrier; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  const uint32_t b = smem_u32(bar);
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(128);
+  }
+  return false;
+}
+
+constexpr uint32_t kWaitPolls = 1u << 22;  // ~0.5 s of polling before giving up
+
+template <class SH, int S, bool FIRST_EXCHANGE>
+__device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
+                                               uint64_t* bar, const cf* next_src, int tid) {
+  using B = SplitBody<SH, DevMem>;
+  B::template write_half<S, 0>(v, x, tid);
+  __syncthreads();
+  if (FIRST_EXCHANGE && tid == 0 && next_src)  // staging is free: every thread has read it
+    tma_load(st, next_src, SH::kL * 8, bar);
+  B::template read_half<S, 0>(v, x, tid);
+  __syncthreads();
+  B::template write_half<S, 1>(v, x, tid);
+  __syncthreads();
+  B::template read_half<S, 1>(v, x, tid);
+  B::template compute<S>(v, d, tid);
+  __syncthreads();
+}
+
+// One contiguous transform per block, persistent over tiles; the next
+// transform streams into shared memory by TMA while this one is computed.
+template <class SH, int MINB>
+__global__ void __launch_bounds__(SH::kT, MINB)
+stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
+  extern __shared__ __align__(128) unsigned char smem_staged[];
+  cf* st = reinterpret_cast<cf*>(smem_staged);
+  cf* x = st + SH::kL;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(x + SH::kHalfSlots);
+  using B = SplitBody<SH, DevMem>;
+  const int tid = threadIdx.x;
+  const int64_t step = gridDim.x;
+  int64_t tile = blockIdx.x;
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (tid == 0 && tile < d.tiles) tma_load(st, in + tile * SH::kL, SH::kL * 8, bar);
+  uint32_t parity = 0;
+  for (; tile < d.tiles; tile += step) {
+    const bool ok = mbar_wait(bar, parity, kWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(d.status, 1);
+        mbar_wait(bar, parity, kWaitPolls);  // let the copy in flight land before leaving
+      }
+      return;
+    }
+    parity ^= 1u;
+    const cf* next = tile + step < d.tiles ? in + (tile + step) * SH::kL : nullptr;
+    cf v[SH::kR];
+    if (d.conj_in) B::template first<true>(v, st, tid);
+    else B::template first<false>(v, st, tid);
+    split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid);
+    if constexpr (SH::kNst > 2) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid);
+    if constexpr (SH::kNst > 3) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
+    cf* o = out + tile * SH::kL;
+    if (d.conj_out) B::template store<true>(v, o, tid);
+    else B::template store<false>(v, o, tid);
+  }
+}
+
+
+template <int R, int LMAP, int SMAP, class TR>
+KernelFn kfn() {
+  return stockham_pass<R, LMAP, SMAP, TR>;
+}
+
+template <class SH, int MINB>
+KernelFn staged_fn() {
+  return stockham_staged<SH, MINB>;
+}
+
+// Generic (run-time-parameter) kernels by thread maps, one translation unit each.
+const void* generic_kernel_rows(int R);         // rows -> rows
+const void* generic_kernel_cols(int R);         // columns -> columns
+const void* generic_kernel_transposing(int R);  // rows -> columns
+
+// Resolvers of the compile-time shapes, one per translation unit.
+const void* resolve_contig_shape(int R, int lmap, int smap, const PassDesc& d);
+const void* resolve_fourstep_shape(int R, int lmap, int smap, const PassDesc& d);
+bool resolve_staged_shape(const PassDesc& d, StagedLaunch* s);
+
+}  // namespace gbfft

@@ -188,6 +188,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   if (o.radix && (o.radix < 2 || o.radix > 16 || !is_pow2(o.radix)))
     { fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16"); return; }
   if (o.variant < 0 || o.variant > 3) { fail(FFT_ERR_INVALID_ARG, "variant must be 0..3"); return; }
+  if (o.epilogue < 0 || o.epilogue > 3) { fail(FFT_ERR_INVALID_ARG, "epilogue must be 0..3"); return; }
   if (o.tile < 0 || o.tile > 1024 || (o.tile && !is_pow2(o.tile)))
     { fail(FFT_ERR_INVALID_ARG, "tile option must be a power of two <= 1024"); return; }
   s.dims = dims;
@@ -244,7 +245,9 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p1.src = BUF_IN;
       p1.dst = BUF_WORK;
       p1.conj_in = inv;
-      p1.epi = 1;
+      // four-step twiddle source: a full table while it stays L2-sized,
+      // computed in-kernel beyond that
+      p1.epi = o.epilogue ? o.epilogue : (logN <= 22 ? 2 : 3);
       p1.epi_logN = logN;
       p1.epi_lo_bits = (logN + 1) / 2;
       // pass 2: row FFTs of length N2 over N1 rows, transposed store
@@ -325,7 +328,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       off = (off + 1) & ~int64_t(1);  // keep 16-byte alignment of segments
       Ns *= r;
     }
-    if (p.epi) {
+    if (p.epi == 1) {
       const int64_t N = int64_t(1) << p.epi_logN;
       const int64_t lo = int64_t(1) << p.epi_lo_bits;
       p.epi_lo_off = off;
@@ -334,6 +337,14 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p.epi_hi_off = off;
       s.tables.push_back(TwSegment{off, N / lo, N, lo, 1, 1});
       off += N / lo;
+      off = (off + 1) & ~int64_t(1);
+    } else if (p.epi == 2) {
+      // entry n2 + k1 * N2 = w_N^{k1 n2}: a stage-style table with r = N2
+      const int64_t N = int64_t(1) << p.epi_logN;
+      p.epi_lo_off = off;
+      p.epi_hi_off = off;
+      s.tables.push_back(TwSegment{off, N, N, 1, 0, (int)p.count_inner});
+      off += N;
       off = (off + 1) & ~int64_t(1);
     }
   }
@@ -377,6 +388,7 @@ PassDesc pass_desc(const PassSpec& p, int64_t b0, int64_t nb, int64_t n_total) {
   d.conj_out = p.conj_out;
   d.epi = p.epi;
   d.epi_lo_bits = p.epi_lo_bits;
+  d.epi_logN = p.epi_logN;
   return d;
 }
 

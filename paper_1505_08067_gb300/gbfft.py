@@ -45,7 +45,8 @@ class fft_plan_options_t(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int), ("radix", ctypes.c_int),
                 ("schedule", ctypes.c_uint32), ("max_block_log2", ctypes.c_int),
                 ("tile", ctypes.c_int), ("generic", ctypes.c_int),
-                ("variant", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("variant", ctypes.c_int), ("epilogue", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 _lib = None
@@ -118,7 +119,7 @@ def _options(opts: dict) -> fft_plan_options_t:
     o = fft_plan_options_t()
     for k, v in opts.items():
         if k not in ("autotune", "radix", "schedule", "max_block_log2", "tile", "generic",
-                     "variant"):
+                     "variant", "epilogue"):
             raise TypeError(f"unknown plan option {k!r}")
         setattr(o, k, int(v))
     return o

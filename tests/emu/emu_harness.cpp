@@ -85,6 +85,12 @@ struct CheckMem {
     if ((*g.slot_epoch)[i] != g.epoch) err("shared load of a slot not written in the last phase", i);
     return s[i];
   }
+  static cf rotor(int64_t m, int logN) {
+    const int64_t N = int64_t(1) << logN;
+    if (m < 0 || m >= N) err("rotor exponent out of range", m);
+    const double a = -2.0 * M_PI * (double)m / (double)N;
+    return mk((float)cos(a), (float)sin(a));
+  }
   static void sts(cf* s, int i, cf v) {
     if (i < 0 || i >= g.smem_len) { err("shared store out of bounds", i); return; }
     if ((*g.slot_write)[i] == g.epoch) err("two writes to one shared slot in one phase", i);
@@ -264,8 +270,8 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
     }
     PassDesc d = pass_desc(p, 0, batch, batch);
     d.tw = tables.data();
-    d.epi_hi = tables.data() + p.epi_hi_off;
-    d.epi_lo = tables.data() + p.epi_lo_off;
+    d.epi_hi = (p.epi == 1 || p.epi == 2) ? tables.data() + p.epi_hi_off : nullptr;
+    d.epi_lo = (p.epi == 1 || p.epi == 2) ? tables.data() + p.epi_lo_off : nullptr;
     // In-place passes read and write the same buffer: copy the source so the
     // checker can tell loads from stores.
     std::vector<cf> src_copy;

@@ -83,3 +83,12 @@ def test_empty_batch(oracle):
 def test_largest_four_step_slice(oracle):
     """The widest tile shapes of the 2^24 plan on a cheaper 2^20 replay."""
     _check(oracle, (2 ** 20,), 1)
+
+
+@pytest.mark.parametrize("epilogue", [1, 2, 3])
+@pytest.mark.parametrize("logn", [15, 20])
+def test_four_step_twiddle_sources(oracle, epilogue, logn):
+    """Two-level tables, the full table and the in-kernel rotor give the same
+    transform (the host replay evaluates the rotor in FP64)."""
+    _check(oracle, (2 ** logn,), 1, epilogue=epilogue)
+    _check(oracle, (2 ** logn,), 1, +1, epilogue=epilogue)

@@ -287,3 +287,17 @@ def test_kernel_variants(gb, oracle, variant, logn):
         idx = np.unique(np.r_[0, batch - 1, np.arange(1, batch, 97)])
         ref = oracle.fft_select(x, idx, d)
         assert np.max(oracle.rel_l2(y[idx], ref)) <= _tol(n)
+
+
+@pytest.mark.parametrize("epilogue", [1, 2, 3])
+@pytest.mark.parametrize("logn", [16, 20, 22])
+def test_four_step_twiddle_sources(gb, oracle, epilogue, logn):
+    """The three sources of the four-step twiddle w_N^{n2 k1} (two small tables,
+    one full table, sincospi of the exact angle) agree with the oracle."""
+    n = 2 ** logn
+    batch = max(1, 2 ** 22 // n)
+    x = synth.uniform(9300 + logn, batch, n)
+    for d in (-1, 1):
+        y = _run(gb, x, (n,), d, epilogue=epilogue)
+        idx = np.unique([0, batch - 1])
+        assert np.max(oracle.rel_l2(y[idx], oracle.fft_select(x, idx, d))) <= _tol(n)
