@@ -424,7 +424,7 @@ def main() -> None:
     ap.add_argument("--workload", choices=["sweep", "multipass", "sar"], default="sweep",
                     help="sweep: the headline batched N=2^8..2^14 line; multipass / sar: "
                          "the large-transform configs, reported as separate lines")
-    ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--only", type=int, default=0, help="run only N = 2^ONLY (profiling)")
     ap.add_argument("--variant", type=int, default=0,
                     help="contiguous-pass kernel variant (0 library choice, 1 register, "

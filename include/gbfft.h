@@ -112,6 +112,8 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *                 out like the first pass's output (coalesced loads, N*8 bytes
  *                 more plan memory), 3 computed in-kernel from the exact FP32
  *                 angle 2m/N with sincospi.
+ *   split_log2    two-pass 1D plans: log2 of the first (column) pass length N1
+ *                 (0 = library choice, N1 <= N2).
  */
 typedef struct {
   int autotune;
@@ -122,7 +124,8 @@ typedef struct {
   int generic;      /* 1: never use the compile-time specialised kernels (testing) */
   int variant;      /* contiguous-pass kernel variant, see above */
   int epilogue;     /* four-step twiddle source, see above */
-  int reserved[5];
+  int split_log2;   /* two-pass split N = N1 * N2, log2 N1 */
+  int reserved[4];
 } fft_plan_options_t;
 
 GBFFT_API fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,

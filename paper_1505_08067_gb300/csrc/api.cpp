@@ -84,6 +84,17 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
   PlanSpec spec;
   make_plan(spec, n, dims, batch, direction, precision, opt, caps);
   if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
+  if (opt && opt->autotune) {
+    // choose the options on this GPU, then plan with them
+    fft_plan_options_t chosen{};
+    char report[sizeof spec.tuning];
+    st = autotune_options(n, dims, batch, direction, *opt, caps, dev, &chosen, report,
+                          sizeof report);
+    if (st != FFT_OK) return st;
+    make_plan(spec, n, dims, batch, direction, precision, &chosen, caps);
+    if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
+    memcpy(spec.tuning, report, sizeof spec.tuning);
+  }
   fft_plan_t p = new (std::nothrow) fft_plan_s();
   if (!p) return fail(FFT_ERR_OUT_OF_MEMORY, "host allocation of the plan failed");
   p->device = dev;
@@ -121,21 +132,7 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
     fft_plan_destroy(p);
     return cuda_fail(e, "twiddle generation");
   }
-  if (opt && opt->autotune) {
-    st = autotune_plan(p->spec, p->caps, p->tables, p->work);
-    if (st != FFT_OK) {
-      char msg[sizeof g_err];
-      memcpy(msg, g_err, sizeof msg);
-      fft_plan_destroy(p);
-      memcpy(g_err, msg, sizeof msg);
-      return st;
-    }
-    e = bind_launches(p->spec, p->caps, static_cast<const cf*>(p->tables), p->status, p->launches);
-    if (e != cudaSuccess) {
-      fft_plan_destroy(p);
-      return cuda_fail(e, "kernel attributes");
-    }
-  }
+
   *out = p;
   return FFT_OK;
 }

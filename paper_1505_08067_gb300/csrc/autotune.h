@@ -1,16 +1,19 @@
-// Plan-time autotuner (Sec. 3.2): per-(radix, start stage) stage costs are
-// benchmarked on this GPU, the shortest path over the schedule digraph gives
-// the model's best radix schedule, and the model's choice is checked against
-// timings of whole passes before it is kept.
+// Plan-time autotuner (Sec. 3.2 model + runtime validation); see autotune.cpp.
 #pragma once
+#include <stddef.h>
+
 #include "../../include/gbfft.h"
 #include "planner.h"
 
 namespace gbfft {
 
-// Retunes the passes of `spec` in place (radix schedule, elements per thread,
-// tile) using the plan's device tables and workspace for trial launches.
-fft_status_t autotune_plan(PlanSpec& spec, const Caps& caps, void* tables, void* work);
+// Chooses plan options for (n, dims, batch, direction) on the current device
+// (`device`), starting from the caller's options `base` (fields the caller set
+// are kept).  Times candidate plans on trial buffers; may allocate device
+// memory while it runs.  Writes a JSON report of what it measured.
+fft_status_t autotune_options(const int64_t* n, int dims, int64_t batch, int direction,
+                              const fft_plan_options_t& base, const Caps& caps, int device,
+                              fft_plan_options_t* chosen, char* report, size_t report_len);
 
 fft_status_t set_error(fft_status_t st, const char* msg);
 

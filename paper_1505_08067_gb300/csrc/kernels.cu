@@ -119,6 +119,26 @@ cudaError_t occupancy(const PassLaunch& p, int* ctas_per_sm) {
                                                        p.smem);
 }
 
+cudaError_t launch_stage_bench(int R, const PassDesc& d, int Ns, int reps, int grid, int block,
+                               size_t smem, void* sink, cudaStream_t st) {
+  const void* f = nullptr;
+  switch (R) {
+    case 2: f = (const void*)stage_bench<2>; break;
+    case 4: f = (const void*)stage_bench<4>; break;
+    case 8: f = (const void*)stage_bench<8>; break;
+    case 16: f = (const void*)stage_bench<16>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  using BenchFn = void (*)(PassDesc, int, int, cf*);
+  reinterpret_cast<BenchFn>(const_cast<void*>(f))<<<grid, block, smem, st>>>(d, Ns, reps,
+                                                                                 static_cast<cf*>(sink));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_copy(const void* in, void* out, int64_t count, int64_t in_stride,
                         int64_t out_stride, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;

@@ -47,6 +47,9 @@ cudaError_t prepare_launch(PassLaunch& p);
 
 cudaError_t launch_pass(const PassLaunch& p, const void* in, void* out, cudaStream_t st);
 cudaError_t occupancy(const PassLaunch& p, int* ctas_per_sm);
+// Times one Stockham stage in isolation (see stage_bench).
+cudaError_t launch_stage_bench(int R, const PassDesc& d, int Ns, int reps, int grid, int block,
+                               size_t smem, void* sink, cudaStream_t st);
 cudaError_t launch_copy(const void* in, void* out, int64_t count, int64_t in_stride,
                         int64_t out_stride, cudaStream_t st);
 cudaError_t launch_twiddle_gen(void* out, int64_t count, int64_t den, int mode, int r,

@@ -216,6 +216,33 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
 }
 
 
+// Stage micro-benchmark (Bergach et al. Sec. 3.2: every (radix, start stage)
+// pair is timed on its own): repeats stage 1 of descriptor `d` -- radix
+// 2^d.rlog[1] after stages whose radices multiply to Ns -- on shared memory,
+// `reps` times: read + twiddle + DFT, barrier, write, barrier.  No global
+// traffic except the twiddle loads the real stage makes.
+template <int R>
+__global__ void __launch_bounds__(1024)
+stage_bench(const __grid_constant__ PassDesc d, int Ns, int reps, cf* sink) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* sm = reinterpret_cast<cf*>(smem_raw);
+  using B = PassBody<R, MAP_ROWS, MAP_ROWS, DevMem, RtTraits>;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < d.smem_elems; i += blockDim.x) sm[i] = mk(1e-3f * (float)(i & 1023), 1.f);
+  __syncthreads();
+  cf v[R];
+  typename B::Tile tl;
+  tl.outer = 0;
+  tl.inner = 0;
+  for (int rep = 0; rep < reps; ++rep) {
+    B::read(v, d, 1, Ns, nullptr, sm, tl, tid);
+    __syncthreads();
+    B::write(v, d, 1, Ns, sm, tid);
+    __syncthreads();
+  }
+  if (v[0].x == 12345.f && v[0].y == -12345.f) sink[blockIdx.x] = v[0];
+}
+
 template <int R, int LMAP, int SMAP, class TR>
 KernelFn kfn() {
   return stockham_pass<R, LMAP, SMAP, TR>;

@@ -226,7 +226,11 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       // Four-step split N = N1 * N2 (Sec. 3.3): columns of length N1, then
       // rows of length N2 written transposed.  N1 <= N2 keeps the strided
       // column tiles wide.
-      const int l1 = logN / 2, l2 = logN - l1;
+      const int l1 = o.split_log2 ? o.split_log2 : logN / 2, l2 = logN - l1;
+      if (l1 < 1 || l2 < 2 || l1 > bmax) {
+        fail(FFT_ERR_INVALID_ARG, "split_log2 must leave both passes between 2 and the block limit");
+        return;
+      }
       if (l2 > bmax) { fail(FFT_ERR_UNSUPPORTED_SIZE, "length needs more than two passes"); return; }
       const int64_t N1 = int64_t(1) << l1, N2 = int64_t(1) << l2;
       const int64_t B = int64_t(1) << bmax;
@@ -247,7 +251,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p1.conj_in = inv;
       // four-step twiddle source: a full table while it stays L2-sized,
       // computed in-kernel beyond that
-      p1.epi = o.epilogue ? o.epilogue : (logN <= 22 ? 2 : 3);
+      p1.epi = o.epilogue ? o.epilogue : (logN <= 20 ? 2 : 3);
       p1.epi_logN = logN;
       p1.epi_lo_bits = (logN + 1) / 2;
       // pass 2: row FFTs of length N2 over N1 rows, transposed store
@@ -423,7 +427,9 @@ std::string describe(const PlanSpec& s) {
     }
     o << ",\"src\":" << p.src << ",\"dst\":" << p.dst << "}";
   }
-  o << "]}";
+  o << "]";
+  if (s.tuning[0]) o << ",\"tuning\":" << s.tuning;
+  o << "}";
   return o.str();
 }
 

@@ -93,6 +93,7 @@ struct PlanSpec {
   int64_t work_elems = 0;
   fft_status_t status = FFT_OK;
   char error[256] = {0};
+  char tuning[4096] = {0};  // autotuner report (JSON), empty if not tuned
 };
 
 // Largest on-chip block 2^k for these limits: the shared-memory exchange

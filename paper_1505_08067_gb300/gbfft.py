@@ -46,7 +46,7 @@ class fft_plan_options_t(ctypes.Structure):
                 ("schedule", ctypes.c_uint32), ("max_block_log2", ctypes.c_int),
                 ("tile", ctypes.c_int), ("generic", ctypes.c_int),
                 ("variant", ctypes.c_int), ("epilogue", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("split_log2", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -119,7 +119,7 @@ def _options(opts: dict) -> fft_plan_options_t:
     o = fft_plan_options_t()
     for k, v in opts.items():
         if k not in ("autotune", "radix", "schedule", "max_block_log2", "tile", "generic",
-                     "variant", "epilogue"):
+                     "variant", "epilogue", "split_log2"):
             raise TypeError(f"unknown plan option {k!r}")
         setattr(o, k, int(v))
     return o

@@ -21,7 +21,8 @@ class Options(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int), ("radix", ctypes.c_int), ("schedule", ctypes.c_uint32),
                 ("max_block_log2", ctypes.c_int), ("tile", ctypes.c_int),
                 ("generic", ctypes.c_int), ("variant", ctypes.c_int),
-                ("epilogue", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("epilogue", ctypes.c_int), ("split_log2", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 def load():

@@ -301,3 +301,29 @@ def test_four_step_twiddle_sources(gb, oracle, epilogue, logn):
         y = _run(gb, x, (n,), d, epilogue=epilogue)
         idx = np.unique([0, batch - 1])
         assert np.max(oracle.rel_l2(y[idx], oracle.fft_select(x, idx, d))) <= _tol(n)
+
+
+@pytest.mark.parametrize("shape,batch", [((1024,), 2048), ((2 ** 14,), 128), ((2 ** 20,), 4),
+                                         ((256, 512), 2)])
+def test_autotuned_plans(gb, oracle, shape, batch):
+    """Autotuned plans: the report carries the stage-cost model (single pass)
+    and the timed candidates; the chosen plan is correct; a second plan of the
+    same shape reuses the choice."""
+    n = int(np.prod(shape))
+    x = synth.uniform(9400 + n, batch, n).reshape((batch,) + shape)
+    arg = shape if len(shape) > 1 else shape[0]
+    with gb.Plan(arg, batch, -1, autotune=1) as p:
+        rep = p.describe()["tuning"]
+        y = p.execute(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+    assert len(rep["candidates"]) >= 2
+    assert all(c["ms"] > 0 for c in rep["candidates"] if c["ms"] >= 0)
+    if len(shape) == 1 and n <= 2 ** 14:
+        sched = rep["model"]["schedule"]
+        assert int(np.prod(sched)) == n and rep["model"]["cost_ns_per_element"] > 0
+    idx = np.unique([0, batch // 2, batch - 1])
+    yr = y.cpu().numpy().reshape(batch, -1)[idx]
+    ref = (oracle.fft(x[idx]) if len(shape) == 1 else oracle.fft2d(x[idx])).reshape(len(idx), -1)
+    assert np.max(oracle.rel_l2(yr, ref)) <= _tol(n)
+    with gb.Plan(arg, batch, -1, autotune=1) as p2:
+        assert "cached" in p2.describe()["tuning"]
