@@ -180,6 +180,13 @@ def reference_arm(args, rank: int) -> None:
 
 # ------------------------------------------------------------------ ours ----
 
+def _tuned(plan):
+    t = plan.describe().get("tuning")
+    if not t:
+        return None
+    return t.get("chosen") or t.get("cached")
+
+
 def ours_other(args, rank: int, world: int) -> None:
     """Other configs (not the headline line): multi-pass 1D and the 2D SAR frame.
     One step = every item forward and inverse; roofline with 16 B per element
@@ -212,6 +219,7 @@ def ours_other(args, rank: int, world: int) -> None:
         for d in DIRS:
             key = (shape, d)
             opts = {"epilogue": args.epilogue} if args.epilogue else {}
+            opts["autotune"] = args.autotune
             plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, **opts)
             order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
     stream = torch.cuda.current_stream()
@@ -244,7 +252,8 @@ def ours_other(args, rank: int, world: int) -> None:
         per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'}"] = {
             "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
             "passes": passes, "gbs": round(16.0 * passes * e / (t * 1e-3) / 1e9, 1),
-            "frac": round(16.0 * passes * e / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+            "frac": round(16.0 * passes * e / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+            "tuned": _tuned(plans[key])}
     if rank == 0:
         tot_bytes = sum(16.0 * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
         print(json.dumps({
@@ -347,7 +356,8 @@ def ours(args, rank: int, world: int) -> None:
                                "gflops": round(flops_of(lg, E) / (tms * 1e-3) / 1e9, 1),
                                "gbs": round(alg_bytes / (tms * 1e-3) / 1e9, 1),
                                "frac": round(alg_bytes / (tms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
-                               "radices": plans[(lg, -1)].describe()["passes"][0]["radices"]}
+                               "radices": plans[(lg, -1)].describe()["passes"][0]["radices"],
+                               "tuned": _tuned(plans[(lg, -1)])}
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
