@@ -128,6 +128,24 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# ------------------------------------------------------------- replicas ----
+
+def replica_throughput(local_ms: float, units_per_rank: float, world: int, device=None) -> tuple:
+    """Whole-job throughput of independent replicas: every rank did
+    `units_per_rank` units in `local_ms`; the job takes as long as the slowest
+    rank.  Returns (max_ms over ranks, all ranks' units / that time per second).
+    With world > 1 this is the only collective (one max all-reduce of a scalar,
+    outside the timed region)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 # --------------------------------------------------------------- oracle ----
 
 def oracle_gflops(seconds: float, steps: int = 1):
@@ -338,12 +356,9 @@ def ours(args, rank: int, world: int) -> None:
     for s in range(args.steps):
         for i, key in enumerate(order):
             per_launch[key].append(ev[s][i][0].elapsed_time(ev[s][i][1]))
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, flops_per_s = replica_throughput(ms, step_flops(E) * args.steps, world, dev)
     ms_per_step = ms_max / args.steps
-    value = world * step_flops(E) * args.steps / (ms_max * 1e-3) / 1e9
+    value = flops_per_s / 1e9
 
     # roofline of the Stockham pass kernel (every launch here is one pass)
     peaks = load_peaks()
