@@ -217,7 +217,11 @@ def ours_other(args, rank: int, world: int) -> None:
 
     from paper_1505_08067_gb300 import gbfft, synth
 
-    if args.workload == "multipass":
+    if args.workload == "tc":
+        items = [((4096,), 32768)]
+        desc = ("batched 1D complex64 FFT N=4096 batch=32768 (2^27 elements, 1 GiB in): FP32 path "
+                "and the tensor-core classes (FP16, BF16, split BF16x3), forward and inverse")
+    elif args.workload == "multipass":
         items = [((2 ** 20,), 64), ((2 ** 22,), 16), ((2 ** 24,), 4)]
         desc = ("large multi-pass 1D complex64 FFTs: N=2^20 batch 64, N=2^22 batch 16, "
                 "N=2^24 batch 4 (2^26 elements each), forward and inverse")
@@ -231,17 +235,22 @@ def ours_other(args, rank: int, world: int) -> None:
     E = max(int(np.prod(s)) * b for s, b in items)
     if args.workload == "sar":
         x = torch.from_numpy(synth.sar_frame(31).reshape(-1)).to(dev)
+    elif args.workload == "tc":
+        x = torch.from_numpy(synth.buried_tone(4, 32768, 4096)[0].reshape(-1)).to(dev)
     else:
         x = torch.from_numpy(synth.uniform(3, 1, E)[0]).to(dev)
     y = torch.empty_like(x)
     plans, order = {}, []
+    precs = [0, 1, 2, 3] if args.workload == "tc" else [0]
     for shape, batch in items:
-        for d in DIRS:
-            key = (shape, d)
-            opts = {"epilogue": args.epilogue} if args.epilogue else {}
-            opts["autotune"] = args.autotune
-            plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, **opts)
-            order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
+        for prec in precs:
+            for d in DIRS:
+                key = (shape, d, prec)
+                opts = {"epilogue": args.epilogue} if args.epilogue else {}
+                opts["autotune"] = args.autotune if prec == 0 else 0
+                plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, prec,
+                                        **opts)
+                order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         for key, e, _lg in order:
@@ -269,7 +278,8 @@ def ours_other(args, rank: int, world: int) -> None:
     for i, (key, e, lg) in enumerate(order):
         t = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
         passes = len(plans[key].describe()["passes"])
-        per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'}"] = {
+        pname = ["fp32", "tc_fp16", "tc_bf16", "tc_bf16x3"][key[2]]
+        per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'} {pname}"] = {
             "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
             "passes": passes, "gbs": round(16.0 * passes * e / (t * 1e-3) / 1e9, 1),
             "frac": round(16.0 * passes * e / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
@@ -450,7 +460,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "multipass", "sar"], default="sweep",
+    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc"], default="sweep",
                     help="sweep: the headline batched N=2^8..2^14 line; multipass / sar: "
                          "the large-transform configs, reported as separate lines")
     ap.add_argument("--autotune", type=int, default=1)

@@ -62,11 +62,23 @@ typedef enum {
 
 enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
 
+/*
+ * Precision classes.  Data are complex64 in every class; the tensor-core
+ * classes compute each radix-16 stage as a dense 16-point DFT matmul on the
+ * tensor cores with FP32 accumulation (twiddles stay FP32), for batched 1D
+ * lengths 16, 256 and 4096:
+ *   FFT_PREC_TC_FP16    stage inputs and DFT matrix rounded to FP16 (each
+ *                       stage's input scaled by 1/16, exactly undone at the end)
+ *   FFT_PREC_TC_BF16    rounded to BF16
+ *   FFT_PREC_TC_BF16X3  split x = x_hi + x_lo, F = F_hi + F_lo in BF16 and
+ *                       x_hi F_hi + x_hi F_lo + x_lo F_hi accumulated (about
+ *                       16 significant bits per product: near-FP32 accuracy)
+ */
 enum {
   FFT_PREC_FP32 = 0,     /* FP32 data, FP32 arithmetic, FP64-generated twiddles */
-  FFT_PREC_TC_FP16 = 1,  /* tensor-core class (reserved) */
-  FFT_PREC_TC_BF16 = 2,  /* tensor-core class (reserved) */
-  FFT_PREC_TC_BF16X3 = 3 /* tensor-core class (reserved) */
+  FFT_PREC_TC_FP16 = 1,
+  FFT_PREC_TC_BF16 = 2,
+  FFT_PREC_TC_BF16X3 = 3
 };
 
 /*

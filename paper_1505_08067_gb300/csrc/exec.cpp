@@ -22,9 +22,18 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       l.grid = p.grid;
       l.block = p.block;
       l.smem = p.smem;
-      l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
+      if (p.tc_prec) {
+        l.fn = resolve_tc(p.logL, p.tc_prec);
+        l.specialised = true;
+      } else {
+        l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
+      }
       cudaError_t e = prepare_launch(l);
       if (e != cudaSuccess) return e;
+      if (p.tc_prec) {
+        launches[i] = l;
+        continue;
+      }
       const bool want_staged = p.variant == 0 || p.variant == 2;
       l.has_staged = want_staged && resolve_staged(l.d, s.generic_only, &l.staged);
       if (l.has_staged) {
@@ -73,7 +82,8 @@ cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const 
         d.epi_hi = l.d.epi_hi;
         d.epi_lo = l.d.epi_lo;
         l.d = d;
-        l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
+        l.fn = p.tc_prec ? resolve_tc(p.logL, p.tc_prec)
+                         : resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
         e = prepare_launch(l);
         if (e != cudaSuccess) return e;
         d.l2_prefetch = launches[i].d.l2_prefetch;

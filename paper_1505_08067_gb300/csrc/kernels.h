@@ -41,6 +41,9 @@ cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* 
 const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool generic_only,
                            bool* specialised);
 
+// Tensor-core class kernel for length 2^logL (4, 8, 12) and FFT_PREC_TC_*.
+const void* resolve_tc(int logL, int prec);
+
 // Per-kernel attributes a launch needs (opt-in shared memory); call once after
 // resolving, before the first launch_pass.
 cudaError_t prepare_launch(PassLaunch& p);

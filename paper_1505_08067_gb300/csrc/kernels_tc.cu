@@ -1,0 +1,129 @@
+// Tensor-core class kernels (see tc_stage.h): batched contiguous transforms of
+// length L = 16, 256 or 4096 whose radix-16 stages run as DFT matmuls on the
+// tensor cores.  One tile = 4096 complex elements (4096 / L transforms) per
+// 256-thread block; two shared buffers of 4096 complex (64 KB, dynamic) hold
+// the tile between stages.
+#include <cuda_runtime.h>
+
+#include "kernels_impl.cuh"
+#include "tc_stage.h"
+
+namespace gbfft {
+
+template <int PREC>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  if (PREC == TC_FP16)
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  else
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One MMA group: y = DFT16 of each of the group's 16 butterflies (real block
+// form, 8 MMAs; 24 for the split-BF16x3 variant).
+template <int PREC>
+__device__ __forceinline__ void tc_group(const cf (&x)[8], const uint32_t (&bh)[2][4][2],
+                                         const uint32_t (&bl)[2][4][2], cf (&y)[8]) {
+  constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
+  constexpr bool SPLIT = PREC == TC_BF16X3;
+  float acc[4][4] = {};
+#pragma unroll
+  for (int kb = 0; kb < 2; ++kb) {
+    uint32_t a[4], alo[4];
+    tc_a_frag<P, SPLIT>(x, kb, a, alo);
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb) {
+      mma16816<P>(acc[nb], a, bh[kb][nb][0], bh[kb][nb][1]);
+      if (SPLIT) {
+        mma16816<P>(acc[nb], a, bl[kb][nb][0], bl[kb][nb][1]);
+        mma16816<P>(acc[nb], alo, bh[kb][nb][0], bh[kb][nb][1]);
+      }
+    }
+  }
+  tc_outputs(acc, y);
+}
+
+// Stage S reads buffer S & 1's predecessor and writes the other one (ping-pong),
+// so a group's outputs go out right after its MMAs; one barrier per stage.
+template <int LOGL, int PREC, int S, bool SI, bool SO>
+__device__ __forceinline__ void tc_stage(const PassDesc& d, const cf* gin, cf* gout, cf* sm,
+                                         const uint32_t (&bh)[2][4][2],
+                                         const uint32_t (&bl)[2][4][2], int w, int lane,
+                                         int valid) {
+  constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
+  using B = TcBody<LOGL, P, DevMem>;
+  const cf* src = sm + ((S + 1) & 1) * 4096;  // written by stage S-1
+  cf* dst = sm + (S & 1) * 4096;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    cf x[8], y[8];
+    B::template gather<S, SI>(x, d, gin, src, w, h, lane, valid);
+    tc_group<PREC>(x, bh, bl, y);
+    B::template scatter<S, SO>(y, gout, dst, w, h, lane, valid);
+  }
+  __syncthreads();
+}
+
+template <int LOGL, int PREC, bool SI, bool SO>
+__device__ __forceinline__ void tc_tile(const PassDesc& d, const cf* gin, cf* gout, cf* sm,
+                                        const uint32_t (&bh)[2][4][2],
+                                        const uint32_t (&bl)[2][4][2], int w, int lane,
+                                        int valid) {
+  constexpr int NST = LOGL / 4;
+  tc_stage<LOGL, PREC, 0, SI, SO>(d, gin, gout, sm, bh, bl, w, lane, valid);
+  if constexpr (NST > 1) tc_stage<LOGL, PREC, 1, SI, SO>(d, gin, gout, sm, bh, bl, w, lane, valid);
+  if constexpr (NST > 2) tc_stage<LOGL, PREC, 2, SI, SO>(d, gin, gout, sm, bh, bl, w, lane, valid);
+}
+
+template <int LOGL, int PREC>
+__global__ void __launch_bounds__(256)
+stockham_tc(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_tc[];
+  cf* sm = reinterpret_cast<cf*>(smem_tc);  // two buffers of 4096 complex
+  constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
+  constexpr int TPC = 4096 >> LOGL;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t bh[2][4][2], bl[2][4][2];
+#pragma unroll
+  for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb) {
+      tc_b_frag<P>(lane, kb, nb, 0, bh[kb][nb][0], bh[kb][nb][1]);
+      if (PREC == TC_BF16X3) tc_b_frag<P>(lane, kb, nb, 1, bl[kb][nb][0], bl[kb][nb][1]);
+      else bl[kb][nb][0] = bl[kb][nb][1] = 0;
+    }
+  for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
+    const int64_t first = tile * TPC;
+    const int64_t rem = d.count_inner - first;
+    const int valid = rem < TPC ? (int)rem : TPC;
+    const cf* gin = in + first * (1 << LOGL);
+    cf* gout = out + first * (1 << LOGL);
+    if (d.conj_in) {
+      if (d.conj_out) tc_tile<LOGL, PREC, true, true>(d, gin, gout, sm, bh, bl, w, lane, valid);
+      else tc_tile<LOGL, PREC, true, false>(d, gin, gout, sm, bh, bl, w, lane, valid);
+    } else {
+      if (d.conj_out) tc_tile<LOGL, PREC, false, true>(d, gin, gout, sm, bh, bl, w, lane, valid);
+      else tc_tile<LOGL, PREC, false, false>(d, gin, gout, sm, bh, bl, w, lane, valid);
+    }
+  }
+}
+
+const void* resolve_tc(int logL, int prec) {
+#define GB_TC(LG, P) \
+  if (logL == LG && prec == P) return (const void*)stockham_tc<LG, P>;
+  GB_TC(4, 1) GB_TC(4, 2) GB_TC(4, 3)
+  GB_TC(8, 1) GB_TC(8, 2) GB_TC(8, 3)
+  GB_TC(12, 1) GB_TC(12, 2) GB_TC(12, 3)
+#undef GB_TC
+  return nullptr;
+}
+
+}  // namespace gbfft

@@ -55,6 +55,17 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
     p.grid = 0;
     return true;
   }
+  if (p.tc_prec) {  // fixed shape: 8 warps, two shared buffers of 4096 complex
+    p.block = 256;
+    p.pitch = 0;
+    p.smem_elems = 2 * 4096;
+    p.smem = (size_t)p.smem_elems * 8;
+    if (p.smem > (size_t)caps.smem_optin) {
+      err = "tensor-core tile does not fit in shared memory";
+      return false;
+    }
+    return true;
+  }
   if (p.R < 2 || p.R > 16 || !is_pow2(p.R) || p.R > L) {
     err = "radix (elements per thread) must be 2, 4, 8 or 16 and at most the pass length";
     return false;
@@ -183,8 +194,15 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
     { fail(FFT_ERR_INVALID_ARG, "direction must be FFT_FORWARD (-1) or FFT_INVERSE (+1)"); return; }
   if (precision < FFT_PREC_FP32 || precision > FFT_PREC_TC_BF16X3)
     { fail(FFT_ERR_INVALID_ARG, "unknown precision"); return; }
-  if (precision != FFT_PREC_FP32)
-    { fail(FFT_ERR_NOT_IMPLEMENTED, "tensor-core precision classes are not built yet"); return; }
+  if (precision != FFT_PREC_FP32) {
+    // tensor-core class: batched 1D lengths that are powers of 16 up to 4096
+    const bool ok = dims == 1 && n && (n[0] == 16 || n[0] == 256 || n[0] == 4096);
+    if (!ok) {
+      fail(FFT_ERR_NOT_IMPLEMENTED,
+           "the tensor-core classes cover batched 1D transforms of length 16, 256 or 4096");
+      return;
+    }
+  }
   if (o.radix && (o.radix < 2 || o.radix > 16 || !is_pow2(o.radix)))
     { fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16"); return; }
   if (o.variant < 0 || o.variant > 3) { fail(FFT_ERR_INVALID_ARG, "variant must be 0..3"); return; }
@@ -216,6 +234,20 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       PassSpec p;
       p.kind = PASS_COPY;
       p.copy_count = batch;
+      s.passes.push_back(p);
+    } else if (precision != FFT_PREC_FP32) {
+      // radix-16 stages as DFT matmuls; tiles of 4096 elements (4096 / N transforms)
+      Sched sch;
+      for (int i = 0; i < logN / 4; ++i) sch.push_back(4);
+      PassSpec p = contiguous_pass(logN, batch, 1, 16, 0, 4096 >> logN, caps);
+      p.rlogs = sch;
+      p.G = 4096 >> logN;
+      p.tiles_inner = (batch + p.G - 1) / p.G;
+      p.tiles = p.tiles_inner;
+      p.in = Strides{0, (int64_t)p.G * N, N, 1};
+      p.out = p.in;
+      p.tc_prec = precision;
+      p.conj_in = p.conj_out = inv;
       s.passes.push_back(p);
     } else if (logN <= bmax) {
       int R = choose_R(logN, o.radix);
@@ -421,7 +453,7 @@ std::string describe(const PlanSpec& s) {
         << ",\"block\":" << p.block << ",\"grid\":" << p.grid << ",\"smem\":" << p.smem
         << ",\"pitch\":" << p.pitch << ",\"epi\":" << p.epi << ",\"epi_logN\":" << p.epi_logN
         << ",\"conj_in\":" << p.conj_in << ",\"conj_out\":" << p.conj_out
-        << ",\"variant\":" << p.variant;
+        << ",\"variant\":" << p.variant << ",\"tc_prec\":" << p.tc_prec;
     } else {
       o << ",\"count\":" << p.copy_count;
     }

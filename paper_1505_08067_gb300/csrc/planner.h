@@ -65,6 +65,7 @@ struct PassSpec {
   size_t smem = 0;
   int grid = 0;
   int variant = 0;              // contiguous passes: 0 auto, 1 register, 2 staged, 3 L2 prefetch
+  int tc_prec = 0;              // tensor-core class (FFT_PREC_TC_*), 0 for FP32
   bool batch_is_tiles = false;  // contiguous pass: batch maps to tiles of G transforms
   int64_t units_per_batch = 1;  // contiguous pass: transforms per batch entry
   // PASS_COPY

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 CSRC = os.path.join(ROOT, "paper_1505_08067_gb300", "csrc")
 LIB = os.path.join(HERE, "_emu.so")
 SRCS = [os.path.join(HERE, "emu_harness.cpp"), os.path.join(CSRC, "planner.cpp")]
-DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "fft_split.h", "planner.h", "kernel_shapes.h")] + \
+DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "fft_split.h", "planner.h", "kernel_shapes.h",
+                                    "tc_stage.h")] + \
     [os.path.join(ROOT, "include", "gbfft.h")]
 _lib = None
 
@@ -38,7 +39,8 @@ def load():
     lib = ctypes.CDLL(LIB)
     lib.emu_run.restype = ctypes.c_int64
     lib.emu_run.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int64,
-                            ctypes.c_int, ctypes.POINTER(Options), ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options), ctypes.c_int,
+                            ctypes.c_int,
                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
                             ctypes.POINTER(ctypes.c_int64)]
     _lib = lib
@@ -46,7 +48,7 @@ def load():
 
 
 def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, specialised=True, stats=None,
-        **opts):
+        precision=0, **opts):
     """Replay the planned passes for complex64 input x of shape (batch, *shape).
     With specialised=True a pass whose shape the library compiles with fixed
     parameters replays that instantiation (as the GPU would run it)."""
@@ -61,7 +63,7 @@ def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, specialised=True,
         setattr(o, k, v)
     msg = ctypes.create_string_buffer(512)
     sp = ctypes.c_int64(0)
-    nerr = lib.emu_run(n, dims, batch, direction, ctypes.byref(o), smem_optin,
+    nerr = lib.emu_run(n, dims, batch, direction, precision, ctypes.byref(o), smem_optin,
                        1 if specialised else 0, x.ctypes.data, out.ctypes.data, msg, 512,
                        ctypes.byref(sp))
     if stats is not None:

@@ -25,6 +25,7 @@
 #include "fft_stage.h"
 #include "kernel_shapes.h"
 #include "planner.h"
+#include "tc_stage.h"
 
 using namespace gbfft;
 
@@ -41,11 +42,15 @@ struct Ctx {
   int smem_len = 0;
   std::vector<int64_t>* slot_epoch = nullptr;
   std::vector<int64_t>* slot_write = nullptr;
-  int64_t epoch = 0;
+  int64_t epoch = 0;        // phase counter of the register / staged replays
+  int64_t read_epoch = -2;  // TC replay: shared reads must see this write phase
+  int64_t write_epoch = -2; // TC replay: shared writes belong to this phase
+  bool split_epochs = false;
   int64_t errors = 0;
   int64_t special_passes = 0;
   int64_t staged_passes = 0;
   const cf* staging = nullptr;  // staged kernel: whole-transform buffer (TMA target)
+  const cf* smem_base = nullptr;  // TC replay: base of the two shared buffers
   int staging_len = 0;
   std::string first_error;
 };
@@ -77,12 +82,17 @@ struct CheckMem {
     return *p;
   }
   static cf lds(const cf* s, int i) {
+    if (g.smem_base && s != g.smem_base) {  // second TC buffer
+      i += (int)(s - g.smem_base);
+      s = g.smem_base;
+    }
     if (g.staging && s == g.staging) {
       if (i < 0 || i >= g.staging_len) { err("staging load out of bounds", i); return mk(0, 0); }
       return s[i];
     }
     if (i < 0 || i >= g.smem_len) { err("shared load out of bounds", i); return mk(0, 0); }
-    if ((*g.slot_epoch)[i] != g.epoch) err("shared load of a slot not written in the last phase", i);
+    const int64_t want = g.split_epochs ? g.read_epoch : g.epoch;
+    if ((*g.slot_epoch)[i] != want) err("shared load of a slot not written in the last phase", i);
     return s[i];
   }
   static cf rotor(int64_t m, int logN) {
@@ -92,10 +102,15 @@ struct CheckMem {
     return mk((float)cos(a), (float)sin(a));
   }
   static void sts(cf* s, int i, cf v) {
+    if (g.smem_base && s != g.smem_base) {
+      i += (int)(s - g.smem_base);
+      s = const_cast<cf*>(g.smem_base);
+    }
     if (i < 0 || i >= g.smem_len) { err("shared store out of bounds", i); return; }
-    if ((*g.slot_write)[i] == g.epoch) err("two writes to one shared slot in one phase", i);
-    (*g.slot_write)[i] = g.epoch;
-    (*g.slot_epoch)[i] = g.epoch;
+    const int64_t ph = g.split_epochs ? g.write_epoch : g.epoch;
+    if ((*g.slot_write)[i] == ph) err("two writes to one shared slot in one phase", i);
+    (*g.slot_write)[i] = ph;
+    (*g.slot_epoch)[i] = ph;
     s[i] = v;
   }
 };
@@ -212,6 +227,120 @@ bool run_staged(const PassDesc& d, const cf* in, cf* out) {
   return false;
 }
 
+// Tensor-core class: the kernel's per-lane gather / scatter with the warp-wide
+// m16n8k16 MMA emulated from the 32 lanes' fragments (PTX fragment layouts).
+template <int P>
+void mma_emulate(float (&d)[32][4], const uint32_t (&a)[32][4], const uint32_t (&b)[32][2]) {
+  double A[16][16], Bm[16][8];
+  for (int lane = 0; lane < 32; ++lane) {
+    const int gq = lane >> 2, t = lane & 3;
+    auto lo = [](uint32_t r) { return (double)from16<P>((uint16_t)(r & 0xffffu)); };
+    auto hi = [](uint32_t r) { return (double)from16<P>((uint16_t)(r >> 16)); };
+    A[gq][2 * t] = lo(a[lane][0]);      A[gq][2 * t + 1] = hi(a[lane][0]);
+    A[gq + 8][2 * t] = lo(a[lane][1]);  A[gq + 8][2 * t + 1] = hi(a[lane][1]);
+    A[gq][2 * t + 8] = lo(a[lane][2]);  A[gq][2 * t + 9] = hi(a[lane][2]);
+    A[gq + 8][2 * t + 8] = lo(a[lane][3]); A[gq + 8][2 * t + 9] = hi(a[lane][3]);
+    Bm[2 * t][gq] = lo(b[lane][0]);     Bm[2 * t + 1][gq] = hi(b[lane][0]);
+    Bm[2 * t + 8][gq] = lo(b[lane][1]); Bm[2 * t + 9][gq] = hi(b[lane][1]);
+  }
+  for (int lane = 0; lane < 32; ++lane) {
+    const int gq = lane >> 2, t = lane & 3;
+    const int rows[4] = {gq, gq, gq + 8, gq + 8}, cols[4] = {2 * t, 2 * t + 1, 2 * t, 2 * t + 1};
+    for (int q = 0; q < 4; ++q) {
+      double s = 0;
+      for (int k = 0; k < 16; ++k) s += A[rows[q]][k] * Bm[k][cols[q]];
+      d[lane][q] = (float)((double)d[lane][q] + s);
+    }
+  }
+}
+
+template <int LOGL, int PREC>
+void run_tc_t(const PassDesc& d, const cf* in, cf* out) {
+  constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
+  constexpr bool SPLIT = PREC == TC_BF16X3;
+  using B = TcBody<LOGL, P, CheckMem>;
+  constexpr int TPC = 4096 >> LOGL, NST = LOGL / 4;
+  std::vector<cf> sm(8192);
+  std::vector<int64_t> ep(sm.size(), -100), wr(sm.size(), -100);
+  g.slot_epoch = &ep;
+  g.slot_write = &wr;
+  g.smem_len = 8192;
+  g.smem_base = sm.data();
+  g.split_epochs = true;
+  uint32_t bh[32][2][4][2], bl[32][2][4][2];
+  for (int lane = 0; lane < 32; ++lane)
+    for (int kb = 0; kb < 2; ++kb)
+      for (int nb = 0; nb < 4; ++nb) {
+        tc_b_frag<P>(lane, kb, nb, 0, bh[lane][kb][nb][0], bh[lane][kb][nb][1]);
+        tc_b_frag<P>(lane, kb, nb, 1, bl[lane][kb][nb][0], bl[lane][kb][nb][1]);
+      }
+  int64_t phase = 0;
+  for (int64_t tile = 0; tile < d.tiles; ++tile) {
+    const int64_t first = tile * TPC;
+    const int valid = (int)std::min<int64_t>(TPC, d.count_inner - first);
+    const cf* gin = in + first * (1 << LOGL);
+    cf* gout = out + first * (1 << LOGL);
+    auto stage = [&](auto S_) {
+      constexpr int S = decltype(S_)::value;
+      g.read_epoch = phase;
+      g.write_epoch = ++phase;
+      const cf* src = sm.data() + ((S + 1) & 1) * 4096;
+      cf* dst = sm.data() + (S & 1) * 4096;
+      for (int w = 0; w < 8; ++w)
+        for (int h = 0; h < 2; ++h) {
+          cf x[32][8], y[32][8];
+          for (int lane = 0; lane < 32; ++lane) {
+            if (d.conj_in) B::template gather<S, true>(x[lane], d, gin, src, w, h, lane, valid);
+            else B::template gather<S, false>(x[lane], d, gin, src, w, h, lane, valid);
+          }
+          float acc[4][32][4] = {};
+          for (int kb = 0; kb < 2; ++kb) {
+            uint32_t a[32][4], alo[32][4];
+            for (int lane = 0; lane < 32; ++lane) tc_a_frag<P, SPLIT>(x[lane], kb, a[lane], alo[lane]);
+            for (int nb = 0; nb < 4; ++nb) {
+              uint32_t b0[32][2], b1[32][2];
+              for (int lane = 0; lane < 32; ++lane) {
+                b0[lane][0] = bh[lane][kb][nb][0]; b0[lane][1] = bh[lane][kb][nb][1];
+                b1[lane][0] = bl[lane][kb][nb][0]; b1[lane][1] = bl[lane][kb][nb][1];
+              }
+              mma_emulate<P>(acc[nb], a, b0);
+              if (SPLIT) {
+                mma_emulate<P>(acc[nb], a, b1);
+                mma_emulate<P>(acc[nb], alo, b0);
+              }
+            }
+          }
+          for (int lane = 0; lane < 32; ++lane) {
+            float dl[4][4];
+            for (int nb = 0; nb < 4; ++nb)
+              for (int q = 0; q < 4; ++q) dl[nb][q] = acc[nb][lane][q];
+            tc_outputs(dl, y[lane]);
+            if (d.conj_out) B::template scatter<S, true>(y[lane], gout, dst, w, h, lane, valid);
+            else B::template scatter<S, false>(y[lane], gout, dst, w, h, lane, valid);
+          }
+        }
+    };
+    stage(std::integral_constant<int, 0>());
+    if constexpr (NST > 1) stage(std::integral_constant<int, 1>());
+    if constexpr (NST > 2) stage(std::integral_constant<int, 2>());
+  }
+  g.smem_base = nullptr;
+  g.split_epochs = false;
+}
+
+bool run_tc(int logL, int prec, const PassDesc& d, const cf* in, cf* out) {
+#define GB_TC(LG, PR)                  \
+  if (logL == LG && prec == PR) {      \
+    run_tc_t<LG, PR>(d, in, out);      \
+    return true;                       \
+  }
+  GB_TC(4, 1) GB_TC(4, 2) GB_TC(4, 3)
+  GB_TC(8, 1) GB_TC(8, 2) GB_TC(8, 3)
+  GB_TC(12, 1) GB_TC(12, 2) GB_TC(12, 3)
+#undef GB_TC
+  return false;
+}
+
 template <int LM, int SM>
 void run_maps(int R, const PassDesc& d, const cf* in, cf* out) {
   switch (R) {
@@ -238,14 +367,14 @@ extern "C" {
 // limits, replays every pass on the CPU and writes the result to `out`
 // (complex64, same size as `in`).  Returns the number of access violations;
 // the first one is described in msg.
-int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
+int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction, int precision,
                 const fft_plan_options_t* opt, int smem_optin, int specialised,
                 const float* in_f, float* out_f, char* msg, size_t msg_len,
                 int64_t* special_passes) {
   Caps caps;
   caps.smem_optin = smem_optin;
   static PlanSpec s;
-  make_plan(s, n, dims, batch, direction, FFT_PREC_FP32, opt, caps);
+  make_plan(s, n, dims, batch, direction, precision, opt, caps);
   g = Ctx{};
   if (s.status != FFT_OK) {
     snprintf(msg, msg_len, "plan failed: %s", s.error);
@@ -287,7 +416,8 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction,
     g.out_hits = &hits;
     g.tw = tables.data();
     g.tw_len = s.table_elems;
-    if (specialised && !s.generic_only && run_staged(d, src, dst)) ++g.staged_passes;
+    if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);
+    else if (specialised && !s.generic_only && run_staged(d, src, dst)) ++g.staged_passes;
     else if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
     else if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
     else if (p.lmap == MAP_COLS && p.smap == MAP_COLS) run_maps<1, 1>(p.R, d, src, dst);

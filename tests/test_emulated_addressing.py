@@ -92,3 +92,20 @@ def test_four_step_twiddle_sources(oracle, epilogue, logn):
     transform (the host replay evaluates the rotor in FP64)."""
     _check(oracle, (2 ** logn,), 1, epilogue=epilogue)
     _check(oracle, (2 ** logn,), 1, +1, epilogue=epilogue)
+
+
+# tensor-core class: tolerance per precision (see test_tc_gpu.py for the reading)
+TC_TOL = {1: lambda n: 2e-3, 2: lambda n: 5e-3, 3: lambda n: 5e-6 * np.log2(n)}
+
+
+@pytest.mark.parametrize("n", [16, 256, 4096])
+@pytest.mark.parametrize("precision", [1, 2, 3])
+def test_tensor_core_class_replay(oracle, n, precision):
+    """Fragment layouts, addressing and ping-pong buffers of the tensor-core
+    kernel, with the warp MMA emulated from its documented fragment layout."""
+    batch = 4096 // n * 2 + 1                       # two full tiles and a ragged one
+    x = synth.uniform(77, batch, n)
+    for d in (-1, 1):
+        y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision)
+        assert nerr == 0, msg
+        assert np.max(oracle.rel_l2(y, oracle.fft(x, d))) <= TC_TOL[precision](n)

@@ -1,0 +1,70 @@
+"""Tensor-core class on the GPU (radix-16 stages as DFT matmuls, FP32
+accumulation) against the FP64 oracle.
+
+Tolerances (relative L2 per transform): FP16 2e-3; split BF16x3 5e-6 log2 N;
+plain BF16 5e-3.  Plain BF16 keeps 8 significant bits: rounding both the stage
+inputs and the DFT matrix gives about 3.5e-3 at N = 4096 (three stages), above
+the 2e-3 aimed for; the bound here is what that arithmetic reaches, and the
+miss is recorded in the design notes."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1505_08067_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {1: lambda n: 2e-3, 2: lambda n: 5e-3, 3: lambda n: 5e-6 * np.log2(n)}
+NAMES = {0: "fp32", 1: "tc_fp16", 2: "tc_bf16", 3: "tc_bf16x3"}
+
+
+def _run(gb, x_np, n, direction, precision):
+    x = torch.from_numpy(x_np).cuda()
+    with gb.Plan(n, x_np.shape[0], direction, precision) as p:
+        y = p.execute(x)
+        torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [16, 256, 4096])
+@pytest.mark.parametrize("precision", [1, 2, 3])
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_tc_class(gb, oracle, n, precision, direction):
+    batch = 4096 // n * 5 + 3
+    x = synth.uniform(9500 + n + precision, batch, n)
+    y = _run(gb, x, n, direction, precision)
+    err = oracle.rel_l2(y, oracle.fft(x, direction))
+    assert np.max(err) <= TOL[precision](n), float(np.max(err))
+
+
+def test_tc_rejects_other_lengths(gb):
+    with pytest.raises(gb.GbfftError) as e:
+        gb.fft_plan_create(1024, 4, -1, 2)
+    assert e.value.status == gb.FFT_ERR_NOT_IMPLEMENTED
+
+
+def test_tc_buried_tone_accuracy_report(gb, oracle, capsys):
+    """N = 4096, batch 32768: uniform noise plus a 1e-3 tone per transform.
+    Relative L2 per precision class and the error at the tone's bin relative
+    to the tone's exact contribution N * 1e-3 (sampled transforms)."""
+    n, batch = 4096, 32768
+    x, bins = synth.buried_tone(8000, batch, n)
+    xt = torch.from_numpy(x).cuda()
+    idx = np.arange(0, batch, 1023)
+    ref = oracle.fft_select(x, idx)
+    report = {}
+    for prec in (0, 1, 2, 3):
+        with gb.Plan(n, batch, -1, prec) as p:
+            y = p.execute(xt)
+            torch.cuda.synchronize()
+        ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+        err = oracle.rel_l2(ys, ref)
+        tone = np.abs(ys[np.arange(idx.size), bins[idx]] - ref[np.arange(idx.size), bins[idx]])
+        report[NAMES[prec]] = {"rel_l2_max": float(err.max()), "rel_l2_mean": float(err.mean()),
+                               "tone_bin_err_rel": float(tone.max() / (n * 1e-3))}
+        tol = 1e-6 * np.log2(n) if prec == 0 else TOL[prec](n)
+        assert err.max() <= tol
+    with capsys.disabled():
+        print("TC_ACCURACY " + json.dumps(report))
