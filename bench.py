@@ -299,6 +299,123 @@ def ours_other(args, rank: int, world: int) -> None:
         p.close()
 
 
+def ours_serve(args, rank: int, world: int) -> None:
+    """Serving (BASELINE configs[4] shape): a Poisson stream of FFT jobs, sizes
+    log-uniform over N = 2^8..2^22, batch 1..256, forward / inverse 50/50, 80%
+    FP32 and 20% tensor-core class (those take N = 256 or 4096, the lengths the
+    class covers), admitted under a 64 GB budget.  Offered load: algorithmic
+    bytes per second = `load` x measured HBM bandwidth.  Inputs are slices of
+    one seeded device buffer; outputs rotate through a ring that is reused only
+    after the job holding it completes.  Reports p50/p99 latency and aggregate
+    GFLOP/s (5 N log2 N of completed jobs over the wall time of the stream)."""
+    import threading
+    from collections import deque
+
+    import numpy as np
+    import torch
+
+    from paper_1505_08067_gb300 import gbfft, synth
+
+    rng = np.random.default_rng(5)
+    njobs = args.jobs
+    logn = rng.integers(8, 23, njobs)
+    batch = rng.integers(1, 257, njobs)
+    dirs = np.where(rng.random(njobs) < 0.5, -1, 1)
+    prec = np.where(rng.random(njobs) < 0.2, rng.integers(1, 4, njobs), 0)
+    logn = np.where(prec > 0, np.where(rng.random(njobs) < 0.5, 8, 12), logn)
+    elems = (2 ** logn) * batch
+    passes = np.where(logn > 14, 2, 1)
+    alg_bytes = 16.0 * passes * elems
+    peaks = load_peaks()
+    rate = args.load * peaks["hbm_gbs"] * 1e9 / alg_bytes.mean()      # jobs per second
+    gaps = rng.exponential(1.0 / rate, njobs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    in_elems = 1 << 30                                                 # 8 GiB of inputs
+    xin = torch.empty(in_elems, dtype=torch.complex64, device=dev)
+    chunk = torch.from_numpy(synth.uniform(5, 1, 1 << 24)[0]).to(dev)
+    for off in range(0, in_elems, chunk.numel()):
+        xin[off:off + chunk.numel()].copy_(chunk)
+    ring_elems = 6 << 30                                               # 48 GiB of outputs
+    yout = torch.empty(ring_elems, dtype=torch.complex64, device=dev)
+    srv = gbfft.fft_server_create(memory_budget_bytes=64 * 10 ** 9, streams=args.streams)
+    # warm the plans of every key outside the measured stream
+    keys = sorted(set(zip(logn.tolist(), dirs.tolist(), prec.tolist())))
+    for lg, d, p in keys:
+        t = gbfft.fft_server_submit(srv, 2 ** lg, 1, d, p, xin.data_ptr(), yout.data_ptr())
+        gbfft.fft_server_wait(srv, t)
+    outstanding = deque()          # (ticket, ring start, ring end)
+    lock = threading.Lock()
+    results = []
+    done_flag = threading.Event()
+
+    def waiter():
+        while True:
+            with lock:
+                item = outstanding[0] if outstanding else None
+            if item is None:
+                if done_flag.is_set():
+                    return
+                time.sleep(0.0002)
+                continue
+            r = gbfft.fft_server_wait(srv, item[0])
+            results.append(r)
+            with lock:
+                outstanding.popleft()
+
+    base_stats = gbfft.fft_server_stats(srv)
+    th = threading.Thread(target=waiter)
+    th.start()
+    ring = 0
+    t0 = time.perf_counter()
+    t_next = t0
+    for j in range(njobs):
+        need = int(elems[j])
+        if ring + need > ring_elems:
+            ring = 0
+        while True:                 # the ring slice must be free
+            with lock:
+                busy = any(not (ring + need <= s or ring >= e) for _, s, e in outstanding)
+            if not busy:
+                break
+            time.sleep(0.0002)
+        t_next += gaps[j]
+        while time.perf_counter() < t_next:
+            pass
+        src = int(rng.integers(0, in_elems - need + 1)) & ~1
+        t = gbfft.fft_server_submit(srv, 2 ** int(logn[j]), int(batch[j]), int(dirs[j]),
+                                    int(prec[j]), xin.data_ptr() + 8 * src,
+                                    yout.data_ptr() + 8 * ring)
+        with lock:
+            outstanding.append((t, ring, ring + need))
+        ring += need
+    t_sub = time.perf_counter() - t0
+    done_flag.set()
+    th.join()
+    wall = time.perf_counter() - t0
+    stats = gbfft.fft_server_stats(srv)
+    gbfft.fft_server_destroy(srv)
+    lat = np.array([r["latency_ms"] for r in results])
+    ok = sum(r["status"] == 0 for r in results)
+    flops = float(np.sum(5.0 * elems * logn))
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": flops / wall / 1e9, "unit": "GFLOP/s", "n_gpus": world,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32+tc", "data": "synthetic",
+            "config": {"workload": "serving: Poisson stream of FFT jobs (configs[4] shape)",
+                       "jobs": njobs, "offered_load_frac_of_hbm": args.load,
+                       "offered_jobs_per_s": rate, "streams": args.streams,
+                       "budget_bytes": 64 * 10 ** 9, "mean_job_elements": float(elems.mean()),
+                       "tc_share": float((prec > 0).mean())},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "completed": int(ok), "submit_s": t_sub, "wall_s": wall,
+            "achieved_alg_gbs": float(alg_bytes.sum() / wall / 1e9),
+            "server": {k: stats[k] - base_stats.get(k, 0) if k in ("launches", "groups",
+                       "coalesced_jobs", "completed") else stats[k]
+                       for k in ("launches", "groups", "coalesced_jobs", "completed",
+                                 "peak_bytes_in_flight", "workspace_allocations")}}))
+
+
 def ours(args, rank: int, world: int) -> None:
     import numpy as np
     import torch
@@ -460,7 +577,12 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc"], default="sweep",
+    ap.add_argument("--jobs", type=int, default=20000, help="serve workload: number of jobs")
+    ap.add_argument("--load", type=float, default=0.5,
+                    help="serve workload: offered algorithmic bytes/s as a fraction of HBM")
+    ap.add_argument("--streams", type=int, default=4, help="serve workload: server streams")
+    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve"],
+                    default="sweep",
                     help="sweep: the headline batched N=2^8..2^14 line; multipass / sar: "
                          "the large-transform configs, reported as separate lines")
     ap.add_argument("--autotune", type=int, default=1)
@@ -493,6 +615,8 @@ def main() -> None:
         dist.init_process_group("nccl")
     if args.workload == "sweep":
         ours(args, rank, world)
+    elif args.workload == "serve":
+        ours_serve(args, rank, world)
     else:
         ours_other(args, rank, world)
     if world > 1:

@@ -220,6 +220,73 @@ GBFFT_API fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream);
 GBFFT_API fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction,
                                            const void* in, void* out, void* stream);
 
+/* ------------------------------------------------------- serving loop --
+ * Continuous batching of FFT jobs on one GPU (the paper's top level, Sec. 3.4:
+ * a batch of independent transforms spread over the compute units, each
+ * reading and writing the shared memory hierarchy once, with a dataflow model
+ * of reads, compute and writes).  Jobs reference caller-owned device buffers.
+ * A worker thread admits jobs in arrival order while the bytes they hold when
+ * running (input + output + workspace) fit the memory budget, coalesces every
+ * waiting job of the same shape, direction and precision into one launch (for
+ * batched 1D single-pass FP32 shapes: one kernel over all their buffers),
+ * spreads launches over several streams so they overlap, and keeps plans and
+ * twiddle tables resident per shape.  Jobs that arrive while others run are
+ * admitted as soon as memory frees up.
+ */
+typedef struct fft_server_s* fft_server_t;
+
+typedef struct {
+  size_t memory_budget_bytes; /* default 64 GiB */
+  int streams;                /* default 4 */
+  int max_group;              /* most jobs coalesced into one group, default 256 */
+  int max_running;            /* most groups on the GPU at once, default 4 x streams */
+  int fail_workspace_alloc;   /* testing: workspace allocations fail (host-side fault) */
+  int reserved[7];
+} fft_server_options_t;
+
+typedef struct {
+  int dims;          /* 1 or 2 */
+  int64_t n[2];      /* lengths as in fft_plan_create */
+  int64_t batch;     /* >= 1 */
+  int direction;     /* FFT_FORWARD / FFT_INVERSE */
+  int precision;     /* FFT_PREC_* */
+  const void* in;    /* device, batch x n complex64, untouched until the job ends */
+  void* out;         /* device, same size */
+} fft_job_t;
+
+typedef struct {
+  int status;        /* fft_status_t of the job */
+  double latency_ms; /* submit -> completion observed */
+  double queue_ms;   /* submit -> launch */
+} fft_job_result_t;
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t launches;        /* kernel-level launches issued */
+  uint64_t groups;          /* admitted groups */
+  uint64_t coalesced_jobs;  /* jobs that shared a coalesced launch */
+  uint64_t workspace_allocations;
+  size_t peak_bytes_in_flight, budget_bytes;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed jobs */
+  double wall_s;            /* first submit -> last completion */
+  double gflops;            /* 5 N log2 N of completed jobs / wall_s */
+} fft_server_stats_t;
+
+/* Start a server on the current device (options may be NULL). */
+GBFFT_API fft_status_t fft_server_create(fft_server_t* server, const fft_server_options_t* options);
+/* Queue a job; returns a ticket.  Shape errors and jobs larger than the budget
+ * are rejected here. */
+GBFFT_API fft_status_t fft_server_submit(fft_server_t server, const fft_job_t* job, uint64_t* ticket);
+/* Wait for a job (timeout_s < 0: no limit); FFT_ERR_TIMEOUT if it is not done
+ * in time (it keeps running).  Each ticket can be waited for once. */
+GBFFT_API fft_status_t fft_server_wait(fft_server_t server, uint64_t ticket, double timeout_s,
+                                       fft_job_result_t* result);
+/* Wait until nothing is queued or running. */
+GBFFT_API fft_status_t fft_server_drain(fft_server_t server, double timeout_s);
+GBFFT_API fft_status_t fft_server_stats(fft_server_t server, fft_server_stats_t* stats);
+/* Stop the worker, wait for running work, free plans and workspaces. */
+GBFFT_API fft_status_t fft_server_destroy(fft_server_t server);
+
 /* Message of the last failure on the calling thread ("" if none). */
 GBFFT_API const char* fft_last_error(void);
 

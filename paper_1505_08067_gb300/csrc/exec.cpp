@@ -93,7 +93,7 @@ cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const 
       if (l.d.tiles == 0) continue;
       if (l.has_staged && ((uintptr_t)src & 15) == 0) {
         StagedLaunch sl = l.staged;
-        if (sl.grid > l.d.tiles) sl.grid = (int)l.d.tiles;
+        sl.grid = (int)std::min<int64_t>(sl.max_grid > 0 ? sl.max_grid : sl.grid, l.d.tiles);
         e = launch_staged(sl, l.d, src, dst, st);
       } else {
         e = launch_pass(l, src, dst, st);

@@ -81,6 +81,7 @@ cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count) {
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t g = (int64_t)per_sm * sm_count;
+  s.max_grid = (int)g;
   s.grid = (int)(g < tiles ? g : tiles);
   return cudaSuccess;
 }
@@ -136,6 +137,26 @@ cudaError_t launch_stage_bench(int R, const PassDesc& d, int Ns, int reps, int g
   using BenchFn = void (*)(PassDesc, int, int, cf*);
   reinterpret_cast<BenchFn>(const_cast<void*>(f))<<<grid, block, smem, st>>>(d, Ns, reps,
                                                                                  static_cast<cf*>(sink));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grouped(int R, const PassDesc& d0, const GroupTable& gt, int grid, int block,
+                           size_t smem, cudaStream_t st) {
+  if (gt.n < 1 || gt.n > kMaxGroup) return cudaErrorInvalidValue;
+  const void* f = nullptr;
+  switch (R) {
+    case 2: f = (const void*)stockham_grouped<2>; break;
+    case 4: f = (const void*)stockham_grouped<4>; break;
+    case 8: f = (const void*)stockham_grouped<8>; break;
+    case 16: f = (const void*)stockham_grouped<16>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  using GFn = void (*)(PassDesc, GroupTable);
+  reinterpret_cast<GFn>(const_cast<void*>(f))<<<grid, block, smem, st>>>(d0, gt);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,21 @@
 
 namespace gbfft {
 
+// Job table of a coalesced launch (see stockham_grouped): up to kMaxGroup jobs
+// of one contiguous single-pass shape, each with its own buffers.
+constexpr int kMaxGroup = 64;
+struct GroupEntry {
+  const cf* in;
+  cf* out;
+  int64_t tile_begin;  // first tile of this job in the launch
+  int64_t tiles;       // tiles of this job
+  int64_t count;       // transforms of this job
+};
+struct GroupTable {
+  int n;
+  GroupEntry e[kMaxGroup];
+};
+
 // Everything needed to launch one stockham_pass.
 struct PassLaunch {
   PassDesc d;
@@ -21,6 +36,7 @@ struct PassLaunch {
   struct StagedLaunchData {
     const void* fn = nullptr;
     int grid = 0, block = 0;
+    int max_grid = 0;  // resident blocks per SM x SMs (persistent grid)
     size_t smem = 0;
   } staged;
 };
@@ -53,6 +69,10 @@ cudaError_t occupancy(const PassLaunch& p, int* ctas_per_sm);
 // Times one Stockham stage in isolation (see stage_bench).
 cudaError_t launch_stage_bench(int R, const PassDesc& d, int Ns, int reps, int grid, int block,
                                size_t smem, void* sink, cudaStream_t st);
+// One launch over the jobs of `gt` with the generic row kernel of R elements
+// per thread; d0 is the pass descriptor of one job (tables, shape, strides).
+cudaError_t launch_grouped(int R, const PassDesc& d0, const GroupTable& gt, int grid, int block,
+                           size_t smem, cudaStream_t st);
 cudaError_t launch_copy(const void* in, void* out, int64_t count, int64_t in_stride,
                         int64_t out_stride, cudaStream_t st);
 cudaError_t launch_twiddle_gen(void* out, int64_t count, int64_t den, int mode, int r,

@@ -54,6 +54,62 @@ struct DevMem {
   }
 };
 
+// One tile of a pass: load, every stage, store.
+template <int R, int LMAP, int SMAP, class TR>
+__device__ __forceinline__ void pass_tile(const cf* __restrict__ in, cf* out, const PassDesc& d,
+                                          int64_t tile, cf* sm, int tid) {
+  using B = PassBody<R, LMAP, SMAP, DevMem, TR>;
+  const typename B::Tile tl = B::tile_of(d, tile);
+  cf v[R];
+  B::first(v, d, in, out, sm, tl, tid);
+  int Ns = 1 << TR::rlog(d, 0);
+  if constexpr (TR::kMaxStages < 15) {
+#pragma unroll
+    for (int s = 1; s < TR::kMaxStages; ++s) {
+      __syncthreads();
+      B::read(v, d, s, Ns, out, sm, tl, tid);
+      if (s < TR::kMaxStages - 1) {
+        __syncthreads();
+        B::write(v, d, s, Ns, sm, tid);
+      }
+      Ns <<= TR::rlog(d, s);
+    }
+  } else {
+#pragma unroll 1
+    for (int s = 1; s < d.nst; ++s) {
+      __syncthreads();
+      B::read(v, d, s, Ns, out, sm, tl, tid);
+      if (s < d.nst - 1) {
+        __syncthreads();
+        B::write(v, d, s, Ns, sm, tid);
+      }
+      Ns <<= d.rlog[s];
+    }
+  }
+  __syncthreads();  // shared memory is reused by the next tile
+}
+
+// Coalesced launch of several same-shape jobs (separate buffers): the job
+// table rides in the kernel parameters; tile t belongs to the job whose range
+// [tile_begin, next tile_begin) contains it.
+template <int R>
+__global__ void __launch_bounds__(1024)
+stockham_grouped(const __grid_constant__ PassDesc d0, const __grid_constant__ GroupTable gt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* sm = reinterpret_cast<cf*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int64_t total = gt.e[gt.n - 1].tile_begin + gt.e[gt.n - 1].tiles;
+  int j = 0;
+  for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    while (j + 1 < gt.n && gt.e[j + 1].tile_begin <= tile) ++j;  // tiles only grow
+    PassDesc d = d0;
+    d.count_inner = gt.e[j].count;
+    d.tiles_inner = d.tiles = gt.e[j].tiles;
+    pass_tile<R, MAP_ROWS, MAP_ROWS, RtTraits>(gt.e[j].in, gt.e[j].out, d,
+                                               tile - gt.e[j].tile_begin, sm, tid);
+  }
+}
+
 template <int R, int LMAP, int SMAP, class TR>
 __global__ void __launch_bounds__(1024)
 stockham_pass(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {

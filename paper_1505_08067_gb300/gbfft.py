@@ -49,6 +49,34 @@ class fft_plan_options_t(ctypes.Structure):
                 ("split_log2", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
+class fft_server_options_t(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int),
+                ("max_group", ctypes.c_int), ("max_running", ctypes.c_int),
+                ("fail_workspace_alloc", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class fft_job_t(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("n", ctypes.c_int64 * 2), ("batch", ctypes.c_int64),
+                ("direction", ctypes.c_int), ("precision", ctypes.c_int),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class fft_job_result_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double)]
+
+
+class fft_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("groups", ctypes.c_uint64), ("coalesced_jobs", ctypes.c_uint64),
+                ("workspace_allocations", ctypes.c_uint64),
+                ("peak_bytes_in_flight", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("wall_s", ctypes.c_double), ("gflops", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -68,6 +96,12 @@ _SIGS = {
                          ctypes.POINTER(fft_plan_options_t), ctypes.c_int, ctypes.c_int,
                          ctypes.c_char_p, ctypes.c_size_t],
     "fft_plan_sync_status": [_vp, _vp],
+    "fft_server_create": [ctypes.POINTER(_vp), ctypes.POINTER(fft_server_options_t)],
+    "fft_server_submit": [_vp, ctypes.POINTER(fft_job_t), ctypes.POINTER(ctypes.c_uint64)],
+    "fft_server_wait": [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(fft_job_result_t)],
+    "fft_server_drain": [_vp, ctypes.c_double],
+    "fft_server_stats": [_vp, ctypes.POINTER(fft_server_stats_t)],
+    "fft_server_destroy": [_vp],
     "fft_schedule_count": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                            ctypes.POINTER(ctypes.c_uint64)],
     "fft_schedule_shortest_path": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -314,3 +348,51 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- serving --
+
+def fft_server_create(memory_budget_bytes: int = 0, streams: int = 0, max_group: int = 0,
+                      max_running: int = 0, fail_workspace_alloc: int = 0) -> int:
+    o = fft_server_options_t(memory_budget_bytes, streams, max_group, max_running,
+                             fail_workspace_alloc)
+    h = _vp()
+    _check(load().fft_server_create(ctypes.byref(h), ctypes.byref(o)))
+    return h.value
+
+
+def fft_server_submit(server: int, n, batch: int, direction: int, precision: int, in_ptr: int,
+                      out_ptr: int) -> int:
+    shape = _shape(n)
+    j = fft_job_t(len(shape), (ctypes.c_int64 * 2)(*shape, *([1] * (2 - len(shape)))), int(batch),
+                  direction, precision, in_ptr, out_ptr)
+    t = ctypes.c_uint64()
+    _check(load().fft_server_submit(server, ctypes.byref(j), ctypes.byref(t)))
+    return t.value
+
+
+def fft_server_wait(server: int, ticket: int, timeout_s: float = -1.0) -> dict:
+    """Waits for a job.  Returns its status (FFT_OK or the job's error, or
+    FFT_ERR_TIMEOUT if it is still running); raises for a bad ticket/server."""
+    r = fft_job_result_t()
+    r.status = -1
+    st = load().fft_server_wait(server, ticket, timeout_s, ctypes.byref(r))
+    if st == FFT_ERR_TIMEOUT:
+        return {"status": st, "latency_ms": -1.0, "queue_ms": -1.0}
+    if st != FFT_OK and r.status == -1:
+        raise GbfftError(st, fft_last_error())
+    return {"status": r.status, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
+
+
+def fft_server_drain(server: int, timeout_s: float = -1.0) -> None:
+    _check(load().fft_server_drain(server, timeout_s))
+
+
+def fft_server_stats(server: int) -> dict:
+    s = fft_server_stats_t()
+    _check(load().fft_server_stats(server, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in fft_server_stats_t._fields_}
+
+
+def fft_server_destroy(server: int) -> None:
+    _check(load().fft_server_destroy(server))
