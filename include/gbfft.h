@@ -281,6 +281,10 @@ GBFFT_API fft_status_t fft_server_submit(fft_server_t server, const fft_job_t* j
  * in time (it keeps running).  Each ticket can be waited for once. */
 GBFFT_API fft_status_t fft_server_wait(fft_server_t server, uint64_t ticket, double timeout_s,
                                        fft_job_result_t* result);
+/* Hold (paused = 1) or resume (0) admissions: jobs submitted while held are
+ * queued and then considered together, so a burst of same-shape jobs is
+ * coalesced; running work is unaffected. */
+GBFFT_API fft_status_t fft_server_pause(fft_server_t server, int paused);
 /* Wait until nothing is queued or running. */
 GBFFT_API fft_status_t fft_server_drain(fft_server_t server, double timeout_s);
 GBFFT_API fft_status_t fft_server_stats(fft_server_t server, fft_server_stats_t* stats);

@@ -91,6 +91,7 @@ struct fft_server_s {
   std::condition_variable cv_work, cv_done;
   std::thread worker;
   bool stop = false;
+  bool paused = false;  // admissions held (fft_server_pause)
   std::vector<cudaStream_t> streams;
   int next_stream = 0;
   std::map<JobKey, PlanEntry*, KeyLess> plans;
@@ -303,7 +304,7 @@ void worker_loop(fft_server_t s) {
     if (progress) s->cv_done.notify_all();
     // 2. launches
     SchedGroup g;
-    while ((int)s->running.size() < s->opt.max_running && s->sched.next(g)) {
+    while (!s->paused && (int)s->running.size() < s->opt.max_running && s->sched.next(g)) {
       Running r;
       r.group = g;
       if (launch_group(s, r)) {
@@ -481,12 +482,23 @@ fft_status_t fft_server_stats(fft_server_t s, fft_server_stats_t* out) {
   return FFT_OK;
 }
 
+fft_status_t fft_server_pause(fft_server_t s, int paused) {
+  if (!server_ok(s)) return set_error(FFT_ERR_BAD_PLAN, "null or destroyed server");
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->paused = paused != 0;
+  }
+  s->cv_work.notify_all();
+  return FFT_OK;
+}
+
 fft_status_t fft_server_destroy(fft_server_t s) {
   if (!s) return FFT_OK;
   if (!server_ok(s)) return set_error(FFT_ERR_BAD_PLAN, "destroyed or foreign server");
   {
     std::lock_guard<std::mutex> lock(s->mu);
     s->stop = true;
+    s->paused = false;
   }
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();

@@ -100,6 +100,7 @@ _SIGS = {
     "fft_server_submit": [_vp, ctypes.POINTER(fft_job_t), ctypes.POINTER(ctypes.c_uint64)],
     "fft_server_wait": [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(fft_job_result_t)],
     "fft_server_drain": [_vp, ctypes.c_double],
+    "fft_server_pause": [_vp, ctypes.c_int],
     "fft_server_stats": [_vp, ctypes.POINTER(fft_server_stats_t)],
     "fft_server_destroy": [_vp],
     "fft_schedule_count": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -382,6 +383,10 @@ def fft_server_wait(server: int, ticket: int, timeout_s: float = -1.0) -> dict:
     if st != FFT_OK and r.status == -1:
         raise GbfftError(st, fft_last_error())
     return {"status": r.status, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
+
+
+def fft_server_pause(server: int, paused: bool) -> None:
+    _check(load().fft_server_pause(server, 1 if paused else 0))
 
 
 def fft_server_drain(server: int, timeout_s: float = -1.0) -> None:

@@ -33,14 +33,20 @@ def _mix(seed, count):
 
 def test_mixed_stream_matches_alone(gb, oracle):
     jobs = _mix(11, 48)
-    srv = gb.fft_server_create(memory_budget_bytes=512 << 20, streams=4)
     bufs, tickets = [], []
+    for k, (shape, batch, d, prec) in enumerate(jobs):
+        n = int(np.prod(shape))
+        x = torch.from_numpy(synth.uniform(12000 + k, batch, n)).cuda()
+        bufs.append((x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    srv = gb.fft_server_create(memory_budget_bytes=512 << 20, streams=4)
     try:
-        for k, (shape, batch, d, prec) in enumerate(jobs):
-            n = int(np.prod(shape))
-            x = torch.from_numpy(synth.uniform(12000 + k, batch, n)).cuda()
-            y = torch.full_like(x, float("nan"))
-            bufs.append((x, y))
+        # the first half arrives as one held burst (coalesced), the second half
+        # one by one while the first half runs
+        gb.fft_server_pause(srv, True)
+        for k, ((shape, batch, d, prec), (x, y)) in enumerate(zip(jobs, bufs)):
+            if k == len(jobs) // 2:
+                gb.fft_server_pause(srv, False)
             tickets.append(gb.fft_server_submit(srv, shape if len(shape) > 1 else shape[0], batch,
                                                 d, prec, x.data_ptr(), y.data_ptr()))
         results = [gb.fft_server_wait(srv, t, 120.0) for t in tickets]
@@ -50,7 +56,7 @@ def test_mixed_stream_matches_alone(gb, oracle):
     assert all(r["status"] == 0 for r in results)
     assert stats["completed"] == len(jobs) and stats["failed"] == 0
     assert stats["peak_bytes_in_flight"] <= 512 << 20
-    assert stats["groups"] < len(jobs)                     # coalescing happened
+    assert stats["groups"] < len(jobs) and stats["coalesced_jobs"] > 0   # coalescing happened
     assert 0 < stats["p50_ms"] <= stats["p99_ms"] <= stats["max_ms"]
     torch.cuda.synchronize()
     for k, ((shape, batch, d, prec), (x, y)) in enumerate(zip(jobs, bufs)):
