@@ -67,7 +67,7 @@ def test_mixed_stream_matches_alone(gb, oracle):
         ym, ya = y.cpu().numpy().reshape(batch, -1), alone.cpu().numpy().reshape(batch, -1)
         assert np.max(oracle.rel_l2(ym, ya)) <= TOL[prec](n), (k, shape, batch, prec)
         if k % 6 == 0:                                     # sample against the oracle
-            xn = x.cpu().numpy()
+            xn = x.cpu().numpy().reshape((batch,) + shape)
             ref = oracle.fft(xn, d) if len(shape) == 1 else oracle.fft2d(xn, d)
             assert np.max(oracle.rel_l2(ym, ref.reshape(batch, -1))) <= TOL[prec](n)
 
