@@ -348,19 +348,25 @@ def ours_serve(args, rank: int, world: int) -> None:
     results = []
     done_flag = threading.Event()
 
+    errors = []
+
     def waiter():
-        while True:
-            with lock:
-                item = outstanding[0] if outstanding else None
-            if item is None:
-                if done_flag.is_set():
-                    return
-                time.sleep(0.0002)
-                continue
-            r = gbfft.fft_server_wait(srv, item[0])
-            results.append(r)
-            with lock:
-                outstanding.popleft()
+        try:
+            while True:
+                with lock:
+                    item = outstanding[0] if outstanding else None
+                if item is None:
+                    if done_flag.is_set():
+                        return
+                    time.sleep(0.0002)
+                    continue
+                r = gbfft.fft_server_wait(srv, item[0])
+                results.append(r)
+                with lock:
+                    outstanding.popleft()
+        except BaseException as exc:  # surfaced by the main thread
+            errors.append(repr(exc))
+            done_flag.set()
 
     base_stats = gbfft.fft_server_stats(srv)
     th = threading.Thread(target=waiter)
@@ -375,7 +381,7 @@ def ours_serve(args, rank: int, world: int) -> None:
         while True:                 # the ring slice must be free
             with lock:
                 busy = any(not (ring + need <= s or ring >= e) for _, s, e in outstanding)
-            if not busy:
+            if not busy or errors:
                 break
             time.sleep(0.0002)
         t_next += gaps[j]
@@ -391,11 +397,16 @@ def ours_serve(args, rank: int, world: int) -> None:
     t_sub = time.perf_counter() - t0
     done_flag.set()
     th.join()
+    if errors:
+        raise RuntimeError("serving waiter failed: " + errors[0])
     wall = time.perf_counter() - t0
     stats = gbfft.fft_server_stats(srv)
     gbfft.fft_server_destroy(srv)
-    lat = np.array([r["latency_ms"] for r in results])
+    lat = np.array([r["latency_ms"] for r in results if r["status"] == 0])
     ok = sum(r["status"] == 0 for r in results)
+    status_counts = {}
+    for r in results:
+        status_counts[str(r["status"])] = status_counts.get(str(r["status"]), 0) + 1
     flops = float(np.sum(5.0 * elems * logn))
     if rank == 0:
         print(json.dumps({
@@ -408,12 +419,50 @@ def ours_serve(args, rank: int, world: int) -> None:
                        "tc_share": float((prec > 0).mean())},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max())},
-            "completed": int(ok), "submit_s": t_sub, "wall_s": wall,
+            "completed": int(ok), "waited": len(results), "status_counts": status_counts,
+            "submit_s": t_sub, "wall_s": wall,
             "achieved_alg_gbs": float(alg_bytes.sum() / wall / 1e9),
             "server": {k: stats[k] - base_stats.get(k, 0) if k in ("launches", "groups",
                        "coalesced_jobs", "completed") else stats[k]
                        for k in ("launches", "groups", "coalesced_jobs", "completed",
                                  "peak_bytes_in_flight", "workspace_allocations")}}))
+
+
+def ours_small(args, rank: int, world: int) -> None:
+    """BASELINE configs[0]: N = 1024, batch 64 (512 KiB), launch-latency bound.
+    Device time per call of fft_execute (one kernel launch) and of
+    fft_execute_graph (the same launch replayed from a CUDA graph), with the
+    calls back to back on one stream."""
+    import torch
+
+    from paper_1505_08067_gb300 import gbfft, synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.from_numpy(synth.uniform(1, 64, 1024)).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    out = {}
+    with gbfft.Plan(1024, 64, -1) as p:
+        for name, fn in (("execute", p.execute), ("graph", p.execute_graph)):
+            for _ in range(20):
+                fn(x, y, stream)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            reps = 2000
+            t0 = time.perf_counter()
+            a.record(stream)
+            for _ in range(reps):
+                fn(x, y, stream)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            host = (time.perf_counter() - t0) / reps * 1e6
+            dev_us = a.elapsed_time(b_) / reps * 1e3
+            out[name] = {"us_per_call_device": round(dev_us, 3), "us_per_call_host": round(host, 3),
+                         "gflops": round(5.0 * 1024 * 10 * 64 / (dev_us * 1e-6) / 1e9, 1)}
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "unit": "us per transform batch", "n_gpus": world,
+                          "config": {"workload": "N=1024 batch 64 complex64 forward (512 KiB)"},
+                          "calls": out}))
 
 
 def ours(args, rank: int, world: int) -> None:
@@ -581,7 +630,7 @@ def main() -> None:
     ap.add_argument("--load", type=float, default=0.5,
                     help="serve workload: offered algorithmic bytes/s as a fraction of HBM")
     ap.add_argument("--streams", type=int, default=4, help="serve workload: server streams")
-    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve"],
+    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve", "small"],
                     default="sweep",
                     help="sweep: the headline batched N=2^8..2^14 line; multipass / sar: "
                          "the large-transform configs, reported as separate lines")
@@ -617,6 +666,8 @@ def main() -> None:
         ours(args, rank, world)
     elif args.workload == "serve":
         ours_serve(args, rank, world)
+    elif args.workload == "small":
+        ours_small(args, rank, world)
     else:
         ours_other(args, rank, world)
     if world > 1:

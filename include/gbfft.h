@@ -166,6 +166,17 @@ GBFFT_API fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, v
 GBFFT_API fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_out,
                               void* dev_in, void* dev_out, void* stream);
 
+/*
+ * Same transform as fft_execute, replayed from a CUDA graph: the first call for
+ * a given (in, out) pair captures the plan's launches into a graph (on a
+ * private stream) and instantiates it; later calls with the same pair launch
+ * that graph on `stream`, which costs one launch instead of one per pass.
+ * Up to 8 pairs are kept per plan (least recently used is replaced).  The
+ * first call for a pair does the capture work; make it before any capture
+ * the caller itself runs on `stream`.
+ */
+GBFFT_API fft_status_t fft_execute_graph(fft_plan_t plan, const void* in, void* out, void* stream);
+
 /* Release the plan, its tables and workspace.  Null is accepted. */
 GBFFT_API fft_status_t fft_plan_destroy(fft_plan_t plan);
 

@@ -53,6 +53,18 @@ struct fft_plan_s {
   cudaStream_t s_h2d = nullptr, s_k = nullptr, s_d2h = nullptr;
   cudaEvent_t ev_start = nullptr, ev_h2d = nullptr, ev_k = nullptr, ev_end = nullptr;
   std::mutex host_mu;
+  // captured executions (fft_execute_graph), keyed by (in, out)
+  struct GraphEntry {
+    const void* in = nullptr;
+    void* out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+  };
+  static constexpr int kGraphs = 8;
+  GraphEntry graphs[kGraphs];
+  uint64_t graph_clock = 0;
+  cudaStream_t s_capture = nullptr;
+  std::mutex graph_mu;
 };
 
 namespace {
@@ -238,6 +250,57 @@ fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_o
   return FFT_OK;
 }
 
+fft_status_t fft_execute_graph(fft_plan_t plan, const void* in, void* out, void* stream) {
+  if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
+  if (plan->spec.batch == 0) return FFT_OK;
+  if (!in || !out) return fail(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
+  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7))
+    return fail(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned (complex64)");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != plan->device) return fail(FFT_ERR_BAD_PLAN, "plan/device mismatch");
+  std::lock_guard<std::mutex> lock(plan->graph_mu);
+  fft_plan_s::GraphEntry* hit = nullptr;
+  fft_plan_s::GraphEntry* victim = &plan->graphs[0];
+  for (auto& g : plan->graphs) {
+    if (g.exec && g.in == in && g.out == out) hit = &g;
+    if (!g.exec || g.last_use < victim->last_use) victim = &g;
+  }
+  if (!hit) {
+    if (!plan->s_capture) {
+      e = cudaStreamCreateWithFlags(&plan->s_capture, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(plan->s_capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    cudaError_t le = enqueue_passes(plan->spec, plan->launches, in, out, plan->work, 0,
+                                    plan->spec.batch, plan->s_capture);
+    e = cudaStreamEndCapture(plan->s_capture, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return cuda_fail(le != cudaSuccess ? le : e, "graph capture");
+    }
+    if (victim->exec) cudaGraphExecDestroy(victim->exec);
+    victim->exec = nullptr;
+    e = cudaGraphInstantiate(&victim->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      victim->exec = nullptr;
+      return cuda_fail(e, "graph instantiation");
+    }
+    victim->in = in;
+    victim->out = out;
+    hit = victim;
+  }
+  hit->last_use = ++plan->graph_clock;
+  e = cudaGraphLaunch(hit->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return FFT_OK;
+}
+
 fft_status_t fft_plan_destroy(fft_plan_t plan) {
   if (!plan) return FFT_OK;
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "destroyed or foreign plan");
@@ -245,6 +308,9 @@ fft_status_t fft_plan_destroy(fft_plan_t plan) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != plan->device && plan->device >= 0) cudaSetDevice(plan->device);
+  for (auto& g : plan->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (plan->s_capture) cudaStreamDestroy(plan->s_capture);
   if (plan->s_h2d) {
     cudaStreamSynchronize(plan->s_h2d);
     cudaStreamSynchronize(plan->s_k);

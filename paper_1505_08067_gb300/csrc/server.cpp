@@ -97,7 +97,8 @@ struct fft_server_s {
   std::map<JobKey, PlanEntry*, KeyLess> plans;
   std::unordered_map<uint64_t, JobRec> jobs;
   std::vector<Running> running;
-  std::multimap<size_t, void*> ws_pool;  // free workspaces by size
+  std::multimap<size_t, void*> ws_pool;  // free workspaces by size class
+  size_t pool_bytes = 0;
   std::vector<cudaEvent_t> free_events;
   uint64_t next_id = 1;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, coalesced = 0;
@@ -164,26 +165,56 @@ PlanEntry* plan_for(fft_server_t s, const JobKey& k, fft_status_t* st) {
   return pe;
 }
 
-// A pooled workspace of exactly `bytes` (sizes repeat: same shapes and batches),
-// else a new one.
+// Workspaces come in power-of-two size classes (at most 2x the request, and the
+// budget accounts for the class size).  Freed workspaces stay pooled up to
+// kPoolCap bytes; beyond that they are released.  If an allocation fails, the
+// pool is released and the allocation retried once.
+constexpr size_t kPoolCap = (size_t)16 << 30;
+
+size_t ws_class(size_t bytes) {
+  size_t c = 1 << 20;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+void ws_flush(fft_server_t s) {
+  for (auto& kv : s->ws_pool) cudaFree(kv.second);
+  s->ws_pool.clear();
+  s->pool_bytes = 0;
+}
+
 void* ws_get(fft_server_t s, size_t bytes) {
-  auto it = s->ws_pool.find(bytes);
+  const size_t c = ws_class(bytes);
+  auto it = s->ws_pool.find(c);
   if (it != s->ws_pool.end()) {
     void* p = it->second;
     s->ws_pool.erase(it);
+    s->pool_bytes -= c;
     return p;
   }
   if (s->opt.fail_workspace_alloc) return nullptr;  // host-side fault injection
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (cudaMalloc(&p, c) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    ws_flush(s);
+    if (cudaMalloc(&p, c) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
   }
   ++s->ws_allocs;
   return p;
 }
 
-void ws_put(fft_server_t s, void* p, size_t bytes) { s->ws_pool.emplace(bytes, p); }
+void ws_put(fft_server_t s, void* p, size_t bytes) {
+  const size_t c = ws_class(bytes);
+  if (s->pool_bytes + c > kPoolCap) {
+    cudaFree(p);
+    return;
+  }
+  s->ws_pool.emplace(c, p);
+  s->pool_bytes += c;
+}
 
 // Launch one admitted group on a stream.  Returns false if it could not.
 bool launch_group(fft_server_t s, Running& r) {
@@ -386,7 +417,8 @@ fft_status_t fft_server_submit(fft_server_t s, const fft_job_t* job, uint64_t* t
   if (((uintptr_t)job->in & 7) || ((uintptr_t)job->out & 7))
     return set_error(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned");
   const int64_t e = job_elems(*job) * job->batch;
-  const size_t bytes = (size_t)e * 16 + (size_t)probe.work_elems * 8 * (size_t)job->batch;
+  const size_t ws = (size_t)probe.work_elems * 8 * (size_t)job->batch;
+  const size_t bytes = (size_t)e * 16 + (ws ? ws_class(ws) : 0);
   std::lock_guard<std::mutex> lock(s->mu);
   SchedJob sj;
   sj.id = s->next_id++;
@@ -507,7 +539,7 @@ fft_status_t fft_server_destroy(fft_server_t s) {
     for (auto& w : r.workspaces) cudaFree(w.first);
     if (r.done) cudaEventDestroy(r.done);
   }
-  for (auto& kv : s->ws_pool) cudaFree(kv.second);
+  ws_flush(s);
   for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
   for (auto& kv : s->plans) {
     cudaFree(kv.second->tables);

@@ -87,6 +87,7 @@ _SIGS = {
                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(fft_plan_options_t)],
     "fft_execute": [_vp, _vp, _vp, _vp],
     "fft_execute_host": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "fft_execute_graph": [_vp, _vp, _vp, _vp],
     "fft_execute_noalloc": [_i64, _i64, ctypes.c_int, _vp, _vp, _vp],
     "fft_plan_destroy": [_vp],
     "fft_plan_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
@@ -180,6 +181,10 @@ def fft_plan_create(n, batch: int, direction: int = FFT_FORWARD,
 
 def fft_execute(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
     _check(load().fft_execute(plan, in_ptr, out_ptr, stream))
+
+
+def fft_execute_graph(plan: int, in_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().fft_execute_graph(plan, in_ptr, out_ptr, stream))
 
 
 def fft_execute_host(plan: int, host_in: int, host_out: int, dev_in: int, dev_out: int,
@@ -315,6 +320,16 @@ class Plan:
             out = torch.empty_like(x)
         self._check_tensor(out, "output")
         fft_execute(self.handle, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def execute_graph(self, x, out=None, stream=None):
+        """Like execute, replayed from a CUDA graph cached for (x, out)."""
+        import torch
+        self._check_tensor(x, "input")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "output")
+        fft_execute_graph(self.handle, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
 
     def execute_host(self, host_in, host_out, dev_in, dev_out, stream=None):
