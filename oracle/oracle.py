@@ -133,6 +133,34 @@ def fft_select(x, indices, sign: int = FORWARD) -> np.ndarray:
     return out
 
 
+def conv(x, h, scale: float, threads: int = 0) -> np.ndarray:
+    """Fast convolution of every line along the last axis, as the library's
+    convolution plans define it: ``scale * IDFT(H . DFT(x))`` with the
+    unnormalised inverse (exponent sign +1, Sec. 2.1).  ``h`` is the filter
+    spectrum, broadcast against ``x`` (shape (n,) for one filter shared by every
+    line, or one row per line).  With ``h = DFT(c)`` and ``scale = 1/n`` this is
+    the circular convolution of each line with ``c``; with ``h = conj(DFT(s))``
+    it is the matched filter of ``s`` (circular cross-correlation), the range /
+    azimuth compression step of the SAR processing chain (Sec. 2.2)."""
+    X = fft(x, FORWARD, threads)
+    Y = X * _c128(h)
+    return fft(Y, BACKWARD, threads) * float(scale)
+
+
+def conv2d(x, h_rows, scale_rows: float, h_cols, scale_cols: float,
+           threads: int = 0) -> np.ndarray:
+    """Fast convolution of row-major frames (..., rows, cols): every row
+    (range line, length cols) with ``h_rows`` first, then every column
+    (azimuth line, length rows) with ``h_cols``.  ``h_rows`` is (cols,) or
+    (rows, cols) with row r's filter in row r; ``h_cols`` is (rows,) or
+    (rows, cols) with column c's filter in column c (frame layout)."""
+    y = conv(x, h_rows, scale_rows, threads)
+    hc = _c128(h_cols)
+    hc = hc if hc.ndim == 1 else hc.T
+    yt = np.ascontiguousarray(np.swapaxes(y, -1, -2))
+    return np.ascontiguousarray(np.swapaxes(conv(yt, hc, scale_cols, threads), -1, -2))
+
+
 def unit_root(m: int, n: int, sign: int = FORWARD) -> complex:
     """The oracle's FP64 value of w_n^m (sign -1) or its conjugate (sign +1)."""
     buf = np.zeros(2, dtype=np.float64)

@@ -111,3 +111,57 @@ def sar_frame(seed: int, rows: int = 4096, cols: int = 8192, scatterers: int = 5
     noise = rng.standard_normal((rows, cols)) + 1j * rng.standard_normal((rows, cols))
     frame += np.sqrt(sigma2 / 2.0) * noise
     return frame.astype(np.complex64)
+
+
+def azimuth_rate(cols: int, col, length: int):
+    """Azimuth chirp rate (cycles / sample^2) of range bin ``col``: 0.8 / length
+    at near range, falling to 0.8 / (1.5 length) at far range, so the
+    azimuth bandwidth stays below the pulse repetition frequency."""
+    return 0.8 / length / (1.0 + 0.5 * np.asarray(col, dtype=np.float64) / cols)
+
+
+def sar_raw(seed: int, rows: int = 4096, cols: int = 8192, scatterers: int = 50,
+            bt: float = 500.0, azimuth_len: int = 512, snr_db: float = 10.0,
+            oversample: float = 1.2):
+    """SAR raw data of point scatterers without range migration, with the
+    replicas a range-Doppler processor correlates against.
+
+    Returns ``(frame, range_replica, azimuth_replicas, positions)``:
+      frame             (rows, cols) complex64, azimuth along rows, range along
+                        the contiguous columns; scatterer s at (r0, c0) adds
+                        exp(i phi_s) * a_{c0}(r - r0) * g(c - c0), circularly;
+      range_replica     (cols,) complex64: the transmitted chirp g (``chirp``),
+                        starting at sample 0, zero-padded;
+      azimuth_replicas  (rows, cols) complex64: column c holds that range bin's
+                        azimuth chirp a_c(t) = exp(i pi K_c t^2) for
+                        t in [-azimuth_len/2, azimuth_len/2), at row t mod rows
+                        (K_c from ``azimuth_rate``);
+      positions         (scatterers, 2) int64 (r0, c0).
+    Complex Gaussian noise is added at ``snr_db`` below the mean signal power."""
+    rng = np.random.default_rng(seed)
+    g = chirp(bt, oversample)
+    lr, la = g.size, int(azimuth_len)
+    if lr > cols or la > rows:
+        raise ValueError("chirps longer than the frame")
+    t = np.arange(la, dtype=np.float64) - la // 2
+    r0 = rng.integers(0, rows, size=scatterers)
+    c0 = rng.integers(0, cols, size=scatterers)
+    phase = rng.uniform(0.0, 2.0 * np.pi, size=scatterers)
+    frame = np.zeros((rows, cols), dtype=np.complex128)
+    ci_base = np.arange(lr)
+    for s in range(scatterers):
+        a = np.exp(1j * np.pi * azimuth_rate(cols, c0[s], la) * t * t)
+        ri = (r0[s] + t.astype(np.int64)) % rows
+        ci = (c0[s] + ci_base) % cols
+        frame[np.ix_(ri, ci)] += np.exp(1j * phase[s]) * np.outer(a, g)
+    power = np.mean(np.abs(frame) ** 2)
+    sigma2 = power / (10.0 ** (snr_db / 10.0))
+    noise = rng.standard_normal((rows, cols)) + 1j * rng.standard_normal((rows, cols))
+    frame += np.sqrt(sigma2 / 2.0) * noise
+    range_replica = np.zeros(cols, dtype=np.complex64)
+    range_replica[:lr] = g
+    k = azimuth_rate(cols, np.arange(cols), la)
+    az = np.zeros((rows, cols), dtype=np.complex64)
+    az[t.astype(np.int64) % rows, :] = np.exp(1j * np.pi * np.outer(t * t, k))
+    return (frame.astype(np.complex64), range_replica, az,
+            np.stack([r0, c0], axis=1).astype(np.int64))
