@@ -207,6 +207,60 @@ GBFFT_API fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batc
  * asynchronous CUDA error it raised. */
 GBFFT_API fft_status_t fft_plan_sync_status(fft_plan_t plan, void* stream);
 
+/* -------------------------------------------------- fast convolution --
+ * Matched filtering of radar lines (Sec. 2.2, the range-Doppler processing
+ * chain of the SAR application: range compression correlates each received
+ * range line with the transmitted chirp; azimuth compression does the same
+ * along each range bin with the azimuth chirp).  Each line goes through one
+ * kernel pass: forward DFT, multiply by a filter spectrum, unnormalised
+ * inverse DFT, read once from and written once to HBM:
+ *
+ *     out_line = scale * IDFT( H_line . DFT(in_line) )
+ *
+ * IDFT is the unnormalised inverse (exponent +2 pi i nk/N); scale = 1/N makes
+ * this the circular convolution of the line with the filter's impulse
+ * response, and H = conj(DFT(chirp)) makes it the matched filter (circular
+ * cross-correlation with the chirp).  For 2D plans (n = {rows, cols}) the
+ * rows (range, cols points each) are filtered first, then the columns
+ * (azimuth, rows points each); the result is back in the signal domain.
+ * Range-cell migration correction is not part of this step.
+ */
+typedef struct {
+  /* Filter spectrum, complex64 in device memory owned by the caller; it must
+   * stay valid and unchanged for the plan's lifetime (the plan keeps the
+   * pointer, not a copy).  8-byte aligned. */
+  const void* h;
+  /* 1: one filter of N points for every line, h[k] for k < N.
+   * Otherwise one filter per line, laid out like one frame of the data with
+   * each line's filter along that line: 1D (lines = batch): h[b*N + k];
+   * 2D rows filter (lines = rows): h[r*cols + k]; 2D columns filter
+   * (lines = cols): h[k*cols + c].  Any other value is FFT_ERR_INVALID_ARG. */
+  int64_t lines;
+  /* Factor applied with the filter (1/N gives the normalised inverse). */
+  float scale;
+  int32_t reserved; /* 0 */
+} fft_filter_t;
+
+/*
+ * Plan a fast convolution of `batch` 1D lines of length n[0] (dims = 1) or of
+ * `batch` frames n = {rows, cols} (dims = 2) with filters[0 .. dims-1]
+ * (filters[0] along the columns / the only dimension, filters[1] along the
+ * rows of a 2D frame).  Every length must be a power of two in [2, 2^14] (one
+ * line per on-chip block); longer lines return FFT_ERR_NOT_IMPLEMENTED.  FP32
+ * only.  Execute with fft_execute / fft_execute_host / fft_execute_graph;
+ * in == out is allowed.  options may be NULL; radix, schedule, tile and
+ * generic apply, autotune and variant are ignored.
+ */
+GBFFT_API fft_status_t fft_conv_plan_create(fft_plan_t* plan, const int64_t* n, int dims,
+                                            int64_t batch, const fft_filter_t* filters,
+                                            const fft_plan_options_t* options);
+
+/* fft_plan_dry_run for a convolution plan (filters[d].h may be NULL here). */
+GBFFT_API fft_status_t fft_conv_plan_dry_run(const int64_t* n, int dims, int64_t batch,
+                                             const fft_filter_t* filters,
+                                             const fft_plan_options_t* options, int sm_count,
+                                             int smem_optin_bytes, char* buf, size_t len);
+
 /*
  * Allocation-free execution.  The paper has no counterpart: this entry point
  * exists for callers that may not allocate GPU memory while they run -- a

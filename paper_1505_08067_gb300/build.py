@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libgbfft.so")
 SOURCES = ["kernels.cu", "generic_rows.cu", "generic_cols.cu", "generic_transposing.cu",
-           "shapes_contig.cu", "shapes_fourstep.cu", "kernels_tc.cu", "noalloc.cu", "api.cpp",
+           "shapes_contig.cu", "shapes_fourstep.cu", "kernels_tc.cu", "conv.cu", "noalloc.cu", "api.cpp",
            "exec.cpp", "server.cpp",
            "planner.cpp", "autotune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

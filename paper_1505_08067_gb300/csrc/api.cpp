@@ -86,7 +86,8 @@ fft_status_t query_caps(Caps& caps, int& device) {
 int64_t elems_per_batch(const PlanSpec& s) { return s.dims == 1 ? s.n[0] : s.n[0] * s.n[1]; }
 
 fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t batch, int direction,
-                        int precision, const fft_plan_options_t* opt) {
+                        int precision, const fft_plan_options_t* opt,
+                        const ConvSpec* conv = nullptr, const void* const* filters = nullptr) {
   if (!out) return fail(FFT_ERR_INVALID_ARG, "plan output pointer is null");
   *out = nullptr;
   Caps caps;
@@ -94,9 +95,11 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
   fft_status_t st = query_caps(caps, dev);
   if (st != FFT_OK) return st;
   PlanSpec spec;
-  make_plan(spec, n, dims, batch, direction, precision, opt, caps);
+  make_plan(spec, n, dims, batch, direction, precision, opt, caps, conv);
   if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
-  if (opt && opt->autotune) {
+  if (conv) {
+    for (int d = 0; d < dims; ++d) spec.filter[d] = filters[d];
+  } else if (opt && opt->autotune) {
     // choose the options on this GPU, then plan with them
     fft_plan_options_t chosen{};
     char report[sizeof spec.tuning];
@@ -369,6 +372,62 @@ fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batch, int dir
   caps.smem_optin = smem_optin_bytes;
   PlanSpec spec;
   make_plan(spec, n, dims, batch, direction, precision, options, caps);
+  if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
+  return copy_text(describe(spec), buf, len);
+}
+
+static fft_status_t conv_spec(const fft_filter_t* filters, int dims, bool need_ptr, ConvSpec& cs,
+                              const void** ptrs) {
+  if (!filters) return fail(FFT_ERR_INVALID_ARG, "filters is null");
+  if (dims != 1 && dims != 2) return fail(FFT_ERR_INVALID_ARG, "dims must be 1 or 2");
+  for (int d = 0; d < dims; ++d) {
+    const fft_filter_t& f = filters[d];
+    if (f.lines < 1) return fail(FFT_ERR_INVALID_ARG, "filter %d: lines must be >= 1", d);
+    if (!(f.scale == f.scale)) return fail(FFT_ERR_INVALID_ARG, "filter %d: scale is NaN", d);
+    if (need_ptr) {
+      if (!f.h) return fail(FFT_ERR_INVALID_ARG, "filter %d: h is null", d);
+      if ((uintptr_t)f.h & 7) return fail(FFT_ERR_INVALID_ARG, "filter %d: h must be 8-byte aligned", d);
+      cudaPointerAttributes a;
+      cudaError_t e = cudaPointerGetAttributes(&a, f.h);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FFT_ERR_INVALID_ARG, "filter %d: h is not a CUDA pointer", d);
+      }
+      if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(FFT_ERR_INVALID_ARG, "filter %d: h must be device (or managed) memory", d);
+    }
+    cs.lines[d] = f.lines;
+    cs.scale[d] = f.scale;
+    ptrs[d] = f.h;
+  }
+  return FFT_OK;
+}
+
+fft_status_t fft_conv_plan_create(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
+                                  const fft_filter_t* filters, const fft_plan_options_t* options) {
+  if (!plan) return fail(FFT_ERR_INVALID_ARG, "plan output pointer is null");
+  *plan = nullptr;
+  ConvSpec cs;
+  const void* ptrs[2] = {nullptr, nullptr};
+  fft_status_t st = conv_spec(filters, dims, true, cs, ptrs);
+  if (st != FFT_OK) return st;
+  return build_plan(plan, n, dims, batch, FFT_FORWARD, FFT_PREC_FP32, options, &cs, ptrs);
+}
+
+fft_status_t fft_conv_plan_dry_run(const int64_t* n, int dims, int64_t batch,
+                                   const fft_filter_t* filters, const fft_plan_options_t* options,
+                                   int sm_count, int smem_optin_bytes, char* buf, size_t len) {
+  if (sm_count <= 0 || smem_optin_bytes <= 0)
+    return fail(FFT_ERR_INVALID_ARG, "device description must be positive");
+  ConvSpec cs;
+  const void* ptrs[2] = {nullptr, nullptr};
+  fft_status_t st = conv_spec(filters, dims, false, cs, ptrs);
+  if (st != FFT_OK) return st;
+  Caps caps;
+  caps.sm_count = sm_count;
+  caps.smem_optin = smem_optin_bytes;
+  PlanSpec spec;
+  make_plan(spec, n, dims, batch, FFT_FORWARD, FFT_PREC_FP32, options, caps, &cs);
   if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
   return copy_text(describe(spec), buf, len);
 }

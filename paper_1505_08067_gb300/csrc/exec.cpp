@@ -16,6 +16,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       l.d.epi_hi = (p.epi == 1 || p.epi == 2) ? tables + p.epi_hi_off : nullptr;
       l.d.epi_lo = (p.epi == 1 || p.epi == 2) ? tables + p.epi_lo_off : nullptr;
       l.d.status = status;
+      l.d.h = p.conv ? static_cast<const cf*>(s.filter[p.h_dim]) : nullptr;
       l.R = p.R;
       l.lmap = p.lmap;
       l.smap = p.smap;
@@ -34,7 +35,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
         launches[i] = l;
         continue;
       }
-      const bool want_staged = p.variant == 0 || p.variant == 2;
+      const bool want_staged = !p.conv && (p.variant == 0 || p.variant == 2);
       l.has_staged = want_staged && resolve_staged(l.d, s.generic_only, &l.staged);
       if (l.has_staged) {
         e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
@@ -81,6 +82,8 @@ cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const 
         d.tw = l.d.tw;
         d.epi_hi = l.d.epi_hi;
         d.epi_lo = l.d.epi_lo;
+        d.status = l.d.status;
+        d.h = l.d.h;
         l.d = d;
         l.fn = p.tc_prec ? resolve_tc(p.logL, p.tc_prec)
                          : resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);

@@ -159,6 +159,16 @@ struct PassDesc {
   const cf* epi_hi;
   const cf* epi_lo;
   int* status;  // device word set to nonzero if a bounded wait gives up
+  // Fast convolution (conv = 1): forward stages, multiply output a of line u
+  // (u = inner tile index * G + g) by h_scale * H_u[a], then the same
+  // stages on swapped data (the unnormalised inverse transform), so that
+  // out = h_scale * IDFT(H_u . DFT(x)).  h_lines = 1: one filter for every
+  // line, H_u[a] = h[a].  Otherwise per-line filters laid out like one frame
+  // of the input: H_u[a] = h[((h_first + u) mod h_lines) * in.g + a * in.e].
+  int32_t conv;
+  float h_scale;
+  int64_t h_lines, h_first;
+  const cf* h;
 };
 
 GB_HD void thread_coords(int map, int tid, int T, int G, int& g, int& t) {

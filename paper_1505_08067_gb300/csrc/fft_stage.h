@@ -102,7 +102,7 @@ struct PassBody {
   }
 
   // ------------------------------------------------------------ stage 0 --
-  template <int RR, bool SWAP>
+  template <int RR, bool SWAP, bool STORE = true>
   GB_HD static void first_r(cf (&v)[R], const PassDesc& d, const cf* in, cf* out, cf* sm,
                             const Tile& tl, int tid) {
     constexpr int NB = R / RR;
@@ -125,6 +125,7 @@ GB_UNROLL
       dft_radix<RR>(v + q * RR);
     }
     if (TR::nst(d) == 1) {
+      if (!STORE) return;
       if (d.conj_out) store_r<RR, true>(v, d, out, tl, tid, 1, LMAP);
       else store_r<RR, false>(v, d, out, tl, tid, 1, LMAP);
     } else {
@@ -133,11 +134,11 @@ GB_UNROLL
   }
 
   // --------------------------------------------- shared -> registers -----
-  template <int RR, bool SWAP>
+  template <int RR, bool SWAP, bool STORE = true>
   GB_HD static void read_r(cf (&v)[R], const PassDesc& d, int s, int Ns, cf* out,
                            const cf* sm, const Tile& tl, int tid) {
     constexpr int NB = R / RR;
-    const bool last = (s == TR::nst(d) - 1);
+    const bool last = STORE && (s == TR::nst(d) - 1);
     const int map = last ? SMAP : LMAP;
     int g, t;
     thread_coords(map, tid, TR::T(d), TR::G(d), g, t);
@@ -214,6 +215,115 @@ GB_UNROLL
         }
         Mem::stg(p, (int64_t)(i * Ns) * e, SWAP ? mk(x.y, x.x) : x);
       }
+    }
+  }
+
+  // --------------------------------------- fast convolution (two rounds) --
+  // Round 1 runs the forward stages without the final store (STORE = false).
+  // conv_mid then multiplies output a (a = jb + i*Ns of the last stage) by
+  // h_scale * H_u[a], swaps re/im and writes it to shared memory in natural
+  // order; round 2 reads it back like a stage-0 load (first_smem) and runs
+  // the forward stages again, the last one storing with the swap undone:
+  // swap(DFT(swap(Y))) is the unnormalised inverse DFT of Y.
+  template <int RR>
+  GB_HD static void conv_mid_r(const cf (&v)[R], const PassDesc& d, cf* sm, const Tile& tl,
+                               int tid, int Ns) {
+    constexpr int NB = R / RR;
+    int g, t;
+    thread_coords(LMAP, tid, TR::T(d), TR::G(d), g, t);
+    const int64_t u = tl.inner * TR::G(d) + g;
+    const cf* hb = d.h;
+    int64_t he = 1;
+    if (d.h_lines > 1) {
+      hb += ((d.h_first + u) % d.h_lines) * TR::in_g(d);
+      he = TR::in_e(d);
+    }
+    const float sc = d.h_scale;
+GB_UNROLL
+    for (int q = 0; q < NB; ++q) {
+      const int jb = q * TR::T(d) + t;
+GB_UNROLL
+      for (int i = 0; i < RR; ++i) {
+        const int a = jb + i * Ns;
+        const cf x = cmul(v[q * RR + i], Mem::ldtw(hb + (int64_t)a * he));
+        Mem::sts(sm, slot(d, g, a), mk(x.y * sc, x.x * sc));
+      }
+    }
+  }
+
+  // Stage 0 of round 2: the loads of first_r, from shared memory.  Results
+  // stay in registers; the caller writes them after a barrier.
+  template <int RR>
+  GB_HD static void first_smem_r(cf (&v)[R], const PassDesc& d, const cf* sm, int tid) {
+    constexpr int NB = R / RR;
+    int g, t;
+    thread_coords(LMAP, tid, TR::T(d), TR::G(d), g, t);
+    const int stride = (1 << TR::logL(d)) / RR;
+GB_UNROLL
+    for (int q = 0; q < NB; ++q) {
+      const int jb = q * TR::T(d) + t;
+GB_UNROLL
+      for (int i = 0; i < RR; ++i) v[q * RR + i] = Mem::lds(sm, slot(d, g, jb + i * stride));
+      dft_radix<RR>(v + q * RR);
+    }
+  }
+
+  GB_HD static void conv_mid(const cf (&v)[R], const PassDesc& d, cf* sm, const Tile& tl, int tid) {
+    const int last = TR::nst(d) - 1;
+    const int Ns = (1 << TR::logL(d)) >> TR::rlog(d, last);
+    switch (TR::rlog(d, last)) {
+      case 1: if (R >= 2) conv_mid_r<(R >= 2 ? 2 : R)>(v, d, sm, tl, tid, Ns); break;
+      case 2: if (R >= 4) conv_mid_r<(R >= 4 ? 4 : R)>(v, d, sm, tl, tid, Ns); break;
+      case 3: if (R >= 8) conv_mid_r<(R >= 8 ? 8 : R)>(v, d, sm, tl, tid, Ns); break;
+      case 4: if (R >= 16) conv_mid_r<(R >= 16 ? 16 : R)>(v, d, sm, tl, tid, Ns); break;
+      default: break;
+    }
+  }
+
+  GB_HD static void first_smem(cf (&v)[R], const PassDesc& d, const cf* sm, int tid) {
+    switch (TR::rlog(d, 0)) {
+      case 1: if (R >= 2) first_smem_r<(R >= 2 ? 2 : R)>(v, d, sm, tid); break;
+      case 2: if (R >= 4) first_smem_r<(R >= 4 ? 4 : R)>(v, d, sm, tid); break;
+      case 3: if (R >= 8) first_smem_r<(R >= 8 ? 8 : R)>(v, d, sm, tid); break;
+      case 4: if (R >= 16) first_smem_r<(R >= 16 ? 16 : R)>(v, d, sm, tid); break;
+      default: break;
+    }
+  }
+
+  // Round 1 stage 0: global -> registers, DFT, shared-memory write (no store
+  // even for a single-stage pass).
+  GB_HD static void first_nostore(cf (&v)[R], const PassDesc& d, const cf* in, cf* sm,
+                                  const Tile& tl, int tid) {
+    switch (TR::rlog(d, 0)) {
+      case 1: if (R >= 2) first_r<(R >= 2 ? 2 : R), false, false>(v, d, in, nullptr, sm, tl, tid); break;
+      case 2: if (R >= 4) first_r<(R >= 4 ? 4 : R), false, false>(v, d, in, nullptr, sm, tl, tid); break;
+      case 3: if (R >= 8) first_r<(R >= 8 ? 8 : R), false, false>(v, d, in, nullptr, sm, tl, tid); break;
+      case 4: if (R >= 16) first_r<(R >= 16 ? 16 : R), false, false>(v, d, in, nullptr, sm, tl, tid); break;
+      default: break;
+    }
+  }
+
+  // Round 1 stages s >= 1: no store after the last one.
+  GB_HD static void read_nostore(cf (&v)[R], const PassDesc& d, int s, int Ns, const cf* sm,
+                                 const Tile& tl, int tid) {
+    switch (TR::rlog(d, s)) {
+      case 1: if (R >= 2) read_r<(R >= 2 ? 2 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 2: if (R >= 4) read_r<(R >= 4 ? 4 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 3: if (R >= 8) read_r<(R >= 8 ? 8 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 4: if (R >= 16) read_r<(R >= 16 ? 16 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      default: break;
+    }
+  }
+
+  // Single-stage round 2: store the registers (swap undone).
+  GB_HD static void store_first(const cf (&v)[R], const PassDesc& d, cf* out, const Tile& tl,
+                                int tid) {
+    switch (TR::rlog(d, 0)) {
+      case 1: if (R >= 2) store_r<(R >= 2 ? 2 : R), true>(v, d, out, tl, tid, 1, LMAP); break;
+      case 2: if (R >= 4) store_r<(R >= 4 ? 4 : R), true>(v, d, out, tl, tid, 1, LMAP); break;
+      case 3: if (R >= 8) store_r<(R >= 8 ? 8 : R), true>(v, d, out, tl, tid, 1, LMAP); break;
+      case 4: if (R >= 16) store_r<(R >= 16 ? 16 : R), true>(v, d, out, tl, tid, 1, LMAP); break;
+      default: break;
     }
   }
 

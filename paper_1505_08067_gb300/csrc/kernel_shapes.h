@@ -32,6 +32,14 @@
   GB_SHAPE(12, 0x444, 3, 16, 4, 0, 1, false, 0)               \
   GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)
 
+/* fast convolution: range lines of 4096 / 8192 / 16384, azimuth columns */
+/* of 4096 (the 2D frame's column pass) */
+#define GB_SHAPES_CONV(GB_SHAPE)                              \
+  GB_SHAPE(12, 0x444, 3, 16, 1, 0, 0, true, 0)                \
+  GB_SHAPE(13, 0x1444, 4, 16, 1, 0, 0, true, 0)               \
+  GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)               \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)
+
 // Contiguous transforms that run the staged kernel (fft_split.h): whole
 // transform per block, TMA prefetch of the next one, half-size exchanges.
 //   GB_STAGED(log2 L, schedule, stages, blocks per SM)
@@ -63,7 +71,7 @@ GB_HD bool staged_shape_matches(const PassDesc& d, int logL, uint32_t sched, int
   for (int i = 0; i < d.nst && i < 8; ++i) s |= (uint32_t)d.rlog[i] << (4 * i);
   if (d.nst > 8) return false;
   const int64_t L = int64_t(1) << d.logL;
-  return d.G == 1 && d.epi == 0 && d.in.e == 1 && d.out.e == 1 && d.in.t == L && d.out.t == L &&
+  return d.G == 1 && d.epi == 0 && d.conv == 0 && d.in.e == 1 && d.out.e == 1 && d.in.t == L && d.out.t == L &&
          d.logL == logL && s == sched && d.nst == nst;
 }
 

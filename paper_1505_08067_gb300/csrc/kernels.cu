@@ -55,6 +55,10 @@ static KernelFn generic_kernel(int R, int lmap, int smap) {
 
 const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool generic_only,
                            bool* specialised) {
+  if (d.conv) {
+    if (lmap != smap) return nullptr;  // convolution passes keep their layout
+    return resolve_conv_kernel(R, lmap, d, generic_only, specialised);
+  }
   if (!generic_only) {
     const void* f = resolve_contig_shape(R, lmap, smap, d);
     if (!f) f = resolve_fourstep_shape(R, lmap, smap, d);

@@ -89,6 +89,74 @@ __device__ __forceinline__ void pass_tile(const cf* __restrict__ in, cf* out, co
   __syncthreads();  // shared memory is reused by the next tile
 }
 
+// Stages s = 1 .. nst-1 of one round of a convolution tile.  Round 1 keeps
+// the last stage's results in registers; round 2 stores them (swap undone).
+template <int R, int MAP, class TR, bool ROUND1>
+__device__ __forceinline__ void conv_stages(cf (&v)[R], const PassDesc& d, cf* out, cf* sm,
+                                            const typename PassBody<R, MAP, MAP, DevMem, TR>::Tile& tl,
+                                            int tid) {
+  using B = PassBody<R, MAP, MAP, DevMem, TR>;
+  int Ns = 1 << TR::rlog(d, 0);
+  if constexpr (TR::kMaxStages < 15) {
+#pragma unroll
+    for (int s = 1; s < TR::kMaxStages; ++s) {
+      __syncthreads();
+      if (ROUND1) B::read_nostore(v, d, s, Ns, sm, tl, tid);
+      else B::template read_s<true>(v, d, s, Ns, out, sm, tl, tid);
+      if (s < TR::kMaxStages - 1) {
+        __syncthreads();
+        B::write(v, d, s, Ns, sm, tid);
+      }
+      Ns <<= TR::rlog(d, s);
+    }
+  } else {
+#pragma unroll 1
+    for (int s = 1; s < d.nst; ++s) {
+      __syncthreads();
+      if (ROUND1) B::read_nostore(v, d, s, Ns, sm, tl, tid);
+      else B::template read_s<true>(v, d, s, Ns, out, sm, tl, tid);
+      if (s < d.nst - 1) {
+        __syncthreads();
+        B::write(v, d, s, Ns, sm, tid);
+      }
+      Ns <<= d.rlog[s];
+    }
+  }
+}
+
+// One tile of a fast-convolution pass: out = h_scale * IDFT(H . DFT(in)) per
+// line, the tile read once and written once (see PassBody's conv phases).
+template <int R, int MAP, class TR>
+__device__ __forceinline__ void conv_tile(const cf* __restrict__ in, cf* out, const PassDesc& d,
+                                          int64_t tile, cf* sm, int tid) {
+  using B = PassBody<R, MAP, MAP, DevMem, TR>;
+  const typename B::Tile tl = B::tile_of(d, tile);
+  cf v[R];
+  B::first_nostore(v, d, in, sm, tl, tid);
+  conv_stages<R, MAP, TR, true>(v, d, out, sm, tl, tid);
+  __syncthreads();  // every round-1 read of shared memory is done
+  B::conv_mid(v, d, sm, tl, tid);
+  __syncthreads();
+  B::first_smem(v, d, sm, tid);
+  if (TR::nst(d) == 1) {
+    B::store_first(v, d, out, tl, tid);
+  } else {
+    __syncthreads();  // stage 0 of round 2 rewrites the slots it read
+    B::write(v, d, 0, 1, sm, tid);
+    conv_stages<R, MAP, TR, false>(v, d, out, sm, tl, tid);
+  }
+  __syncthreads();  // shared memory is reused by the next tile
+}
+
+template <int R, int MAP, class TR>
+__global__ void __launch_bounds__(1024)
+stockham_conv(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cf* sm = reinterpret_cast<cf*>(smem_raw);
+  for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x)
+    conv_tile<R, MAP, TR>(in, out, d, tile, sm, threadIdx.x);
+}
+
 // Coalesced launch of several same-shape jobs (separate buffers): the job
 // table rides in the kernel parameters; tile t belongs to the job whose range
 // [tile_begin, next tile_begin) contains it.
@@ -308,6 +376,11 @@ template <class SH, int MINB>
 KernelFn staged_fn() {
   return stockham_staged<SH, MINB>;
 }
+
+// Fast-convolution kernels (conv.cu): a compile-time shape if one matches,
+// else the generic kernel for (R, map).
+const void* resolve_conv_kernel(int R, int map, const PassDesc& d, bool generic_only,
+                                bool* specialised);
 
 // Generic (run-time-parameter) kernels by thread maps, one translation unit each.
 const void* generic_kernel_rows(int R);         // rows -> rows

@@ -95,7 +95,7 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
   p.block = p.G * T;
   p.pitch = row_pitch(L, p.G);
   p.smem_elems = smem_elems_for(L, p.G, p.lmap);
-  if (p.rlogs.size() == 1) p.smem_elems = 0;  // single stage: registers only
+  if (p.rlogs.size() == 1 && !p.conv) p.smem_elems = 0;  // single stage: registers only
   p.smem = (size_t)p.smem_elems * 8;
   if (p.smem > (size_t)caps.smem_optin) {
     err = "tile does not fit in shared memory";
@@ -178,7 +178,8 @@ static PassSpec contiguous_pass(int logL, int64_t batch, int64_t units_per_batch
 }
 
 void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direction,
-               int precision, const fft_plan_options_t* opt, const Caps& caps) {
+               int precision, const fft_plan_options_t* opt, const Caps& caps,
+               const ConvSpec* conv) {
   s = PlanSpec();
   fft_plan_options_t o{};
   if (opt) o = *opt;
@@ -226,7 +227,65 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   s.generic_only = o.generic != 0;
   const int inv = direction == FFT_INVERSE;
 
-  if (dims == 1) {
+  if (conv) {
+    // Fast convolution: every line on one SM, forward stages, filter, forward
+    // stages on swapped data, one pass per dimension.
+    s.conv = true;
+    s.direction = FFT_FORWARD;
+    if (precision != FFT_PREC_FP32)
+      { fail(FFT_ERR_NOT_IMPLEMENTED, "fast convolution runs in FP32 only"); return; }
+    for (int d = 0; d < dims; ++d) {
+      if (n[d] < 2) { fail(FFT_ERR_UNSUPPORTED_SIZE, "convolution lengths must be >= 2"); return; }
+      if (ilog2(n[d]) > bmax)
+        { fail(FFT_ERR_NOT_IMPLEMENTED, "convolution lines must fit one on-chip block (<= 2^14)"); return; }
+    }
+    // lines along dimension d per frame: the other lengths (1D: the batch)
+    const int64_t lines_of[2] = {dims == 1 ? batch : n[1], dims == 1 ? 0 : n[0]};
+    for (int d = 0; d < dims; ++d) {
+      const int64_t l = conv->lines[d];
+      if (l != 1 && l != lines_of[d]) {
+        fail(FFT_ERR_INVALID_ARG, dims == 1 ? "filter lines must be 1 or the batch"
+                                            : "filter lines must be 1 or the lines of a frame along that dimension");
+        return;
+      }
+    }
+    const int dl = dims == 1 ? 0 : 1;  // contiguous dimension
+    const int lc = ilog2(n[dl]);
+    const int64_t units = dims == 1 ? 1 : n[0];
+    // at least two stages where possible: the shared buffer is there anyway
+    int R = std::min(choose_R(lc, o.radix), std::max(2, 1 << (lc - 1)));
+    PassSpec p = contiguous_pass(lc, batch, units, R, o.schedule, o.tile, caps);
+    p.conv = 1;
+    p.conj_out = 1;
+    p.h_dim = dl;
+    p.h_lines = conv->lines[dl];
+    p.h_scale = conv->scale[dl];
+    s.passes.push_back(p);
+    if (dims == 2) {
+      const int64_t rows = n[0], cols = n[1];
+      const int lr = ilog2(rows);
+      int Rr = std::min(choose_R(lr, o.radix), std::max(2, 1 << (lr - 1)));
+      PassSpec q = fft_pass(lr, Rr, default_schedule(lr, ilog2(Rr)));
+      const int64_t B = int64_t(1) << bmax;
+      int G = (int)std::min<int64_t>({16, B / rows, cols});
+      q.G = G;
+      q.lmap = q.smap = MAP_COLS;
+      q.count_inner = cols;
+      q.tiles_inner = cols / G;
+      q.outer = batch;
+      q.tiles = batch * q.tiles_inner;
+      q.in = Strides{rows * cols, G, 1, cols};
+      q.out = q.in;
+      q.src = BUF_OUT;
+      q.dst = BUF_OUT;
+      q.conv = 1;
+      q.conj_out = 1;
+      q.h_dim = 0;
+      q.h_lines = conv->lines[0];
+      q.h_scale = conv->scale[0];
+      s.passes.push_back(q);
+    }
+  } else if (dims == 1) {
     const int64_t N = n[0];
     const int logN = ilog2(N);
     if (logN > 24) { fail(FFT_ERR_UNSUPPORTED_SIZE, "1D length must be <= 2^24"); return; }
@@ -349,7 +408,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   // launch shapes and twiddle tables
   int64_t off = 0;
   for (auto& p : s.passes) {
-    if (p.batch_is_tiles) p.variant = o.variant;
+    if (p.batch_is_tiles && !p.conv) p.variant = o.variant;
     const char* err = nullptr;
     if (!fill_launch(p, caps, err)) { fail(FFT_ERR_INVALID_ARG, err); return; }
     if (p.kind != PASS_FFT) continue;
@@ -395,7 +454,6 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
 }
 
 PassDesc pass_desc(const PassSpec& p, int64_t b0, int64_t nb, int64_t n_total) {
-  (void)b0;
   (void)n_total;
   PassDesc d{};
   d.logL = p.logL;
@@ -425,6 +483,11 @@ PassDesc pass_desc(const PassSpec& p, int64_t b0, int64_t nb, int64_t n_total) {
   d.epi = p.epi;
   d.epi_lo_bits = p.epi_lo_bits;
   d.epi_logN = p.epi_logN;
+  d.conv = p.conv;
+  d.h_scale = p.h_scale;
+  d.h_lines = p.h_lines > 0 ? p.h_lines : 1;
+  // line u of a sub-batch starting at entry b0 is line b0 * units + u overall
+  d.h_first = p.batch_is_tiles ? (b0 * p.units_per_batch) % d.h_lines : 0;
   return d;
 }
 
@@ -434,7 +497,7 @@ std::string describe(const PlanSpec& s) {
   if (s.dims == 2) o << "," << s.n[1];
   o << "],\"batch\":" << s.batch << ",\"direction\":" << s.direction
     << ",\"precision\":" << s.precision << ",\"max_block_log2\":" << s.max_block_log2
-    << ",\"generic\":" << (s.generic_only ? 1 : 0)
+    << ",\"generic\":" << (s.generic_only ? 1 : 0) << ",\"conv\":" << (s.conv ? 1 : 0)
     << ",\"workspace_bytes\":" << s.work_elems * 8 << ",\"table_elems\":" << s.table_elems
     << ",\"passes\":[";
   for (size_t i = 0; i < s.passes.size(); ++i) {
@@ -454,6 +517,9 @@ std::string describe(const PlanSpec& s) {
         << ",\"pitch\":" << p.pitch << ",\"epi\":" << p.epi << ",\"epi_logN\":" << p.epi_logN
         << ",\"conj_in\":" << p.conj_in << ",\"conj_out\":" << p.conj_out
         << ",\"variant\":" << p.variant << ",\"tc_prec\":" << p.tc_prec;
+      if (p.conv)
+        o << ",\"conv\":1,\"h_dim\":" << p.h_dim << ",\"h_lines\":" << p.h_lines
+          << ",\"h_scale\":" << p.h_scale;
     } else {
       o << ",\"count\":" << p.copy_count;
     }

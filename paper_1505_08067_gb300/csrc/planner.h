@@ -65,6 +65,10 @@ struct PassSpec {
   size_t smem = 0;
   int grid = 0;
   int variant = 0;              // contiguous passes: 0 auto, 1 register, 2 staged, 3 L2 prefetch
+  int conv = 0;                 // fast convolution pass (see PassDesc::conv)
+  int h_dim = 0;                // which dimension's filter
+  int64_t h_lines = 1;          // 1 or the lines per frame along this dimension
+  float h_scale = 1.f;
   int tc_prec = 0;              // tensor-core class (FFT_PREC_TC_*), 0 for FP32
   bool batch_is_tiles = false;  // contiguous pass: batch maps to tiles of G transforms
   int64_t units_per_batch = 1;  // contiguous pass: transforms per batch entry
@@ -80,6 +84,14 @@ struct TwSegment {  // one twiddle_gen launch (mode 0: exponent (j / r) * (j % r
   int mode, r;
 };
 
+// Fast convolution (matched filtering) along every dimension of a plan:
+// per dimension, the number of distinct filters (1, or one per line of a
+// frame along that dimension) and the factor applied with the filter.
+struct ConvSpec {
+  int64_t lines[2] = {1, 1};
+  float scale[2] = {1.f, 1.f};
+};
+
 struct PlanSpec {
   int dims = 1;
   int64_t n[2] = {1, 1};
@@ -88,6 +100,8 @@ struct PlanSpec {
   int precision = FFT_PREC_FP32;
   int max_block_log2 = 14;
   bool generic_only = false;  // never pick compile-time specialisations
+  bool conv = false;          // fast-convolution plan (make_plan with a ConvSpec)
+  const void* filter[2] = {nullptr, nullptr};  // device filter spectra per dimension
   SmallVec<PassSpec, 4> passes;
   SmallVec<TwSegment, 40> tables;
   int64_t table_elems = 0;
@@ -106,9 +120,11 @@ int block_log2_limit(const Caps& caps);
 // thread: as many full-radix stages as fit, the remainder radix last.
 Sched default_schedule(int logL, int logR);
 
-// Heap-free: fills `s` in place.
+// Heap-free: fills `s` in place.  With `conv`, every dimension is a fast
+// convolution pass (direction is ignored; the plan's filters are bound later).
 void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direction,
-               int precision, const fft_plan_options_t* opt, const Caps& caps);
+               int precision, const fft_plan_options_t* opt, const Caps& caps,
+               const ConvSpec* conv = nullptr);
 
 // Rebuild one pass for a different radix / schedule / tile (autotuner); keeps
 // geometry.  Returns false if the combination is invalid.

@@ -49,6 +49,11 @@ class fft_plan_options_t(ctypes.Structure):
                 ("split_log2", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
+class fft_filter_t(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("lines", ctypes.c_int64), ("scale", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
 class fft_server_options_t(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int),
                 ("max_group", ctypes.c_int), ("max_running", ctypes.c_int),
@@ -97,6 +102,11 @@ _SIGS = {
                          ctypes.POINTER(fft_plan_options_t), ctypes.c_int, ctypes.c_int,
                          ctypes.c_char_p, ctypes.c_size_t],
     "fft_plan_sync_status": [_vp, _vp],
+    "fft_conv_plan_create": [ctypes.POINTER(_vp), ctypes.POINTER(_i64), ctypes.c_int, _i64,
+                             ctypes.POINTER(fft_filter_t), ctypes.POINTER(fft_plan_options_t)],
+    "fft_conv_plan_dry_run": [ctypes.POINTER(_i64), ctypes.c_int, _i64, ctypes.POINTER(fft_filter_t),
+                              ctypes.POINTER(fft_plan_options_t), ctypes.c_int, ctypes.c_int,
+                              ctypes.c_char_p, ctypes.c_size_t],
     "fft_server_create": [ctypes.POINTER(_vp), ctypes.POINTER(fft_server_options_t)],
     "fft_server_submit": [_vp, ctypes.POINTER(fft_job_t), ctypes.POINTER(ctypes.c_uint64)],
     "fft_server_wait": [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(fft_job_result_t)],
@@ -235,6 +245,42 @@ def fft_plan_sync_status(plan: int, stream: int = 0) -> None:
     _check(load().fft_plan_sync_status(plan, stream))
 
 
+def _filters(filters) -> ctypes.Array:
+    """[(device pointer or None, lines, scale)] per dimension -> fft_filter_t[]."""
+    arr = (fft_filter_t * max(1, len(filters)))()
+    for i, (ptr, lines, scale) in enumerate(filters):
+        arr[i].h = ptr
+        arr[i].lines = int(lines)
+        arr[i].scale = float(scale)
+    return arr
+
+
+def fft_conv_plan_create(n, batch: int, filters, **options) -> int:
+    """Fast-convolution plan (include/gbfft.h); filters = [(h_ptr, lines, scale)]
+    per dimension.  Returns the plan handle."""
+    shape = _shape(n)
+    arr = (_i64 * len(shape))(*shape)
+    h = _vp()
+    o = _options(options) if options else None
+    _check(load().fft_conv_plan_create(ctypes.byref(h), arr, len(shape), int(batch),
+                                       _filters(filters), ctypes.byref(o) if o else None))
+    return h.value
+
+
+def fft_conv_plan_dry_run(n, batch: int, filters, sm_count: int = 152,
+                          smem_optin_bytes: int = 232448, **options) -> dict:
+    """Convolution plan description for a described device; filters =
+    [(lines, scale)] per dimension."""
+    shape = _shape(n)
+    arr = (_i64 * len(shape))(*shape)
+    o = _options(options)
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().fft_conv_plan_dry_run(arr, len(shape), int(batch),
+                                        _filters([(None, l, sc) for l, sc in filters]),
+                                        ctypes.byref(o), sm_count, smem_optin_bytes, buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
 def _cost_arrays(log2n, radix_logs, cost):
     rl = (ctypes.c_int * len(radix_logs))(*radix_logs)
     flat = [float(cost[j][s]) if s < len(cost[j]) else -1.0
@@ -364,6 +410,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class ConvPlan(Plan):
+    """Fast convolution (matched filtering) of ``batch`` lines / frames of
+    shape ``n`` with ``filters`` = [(h, lines, scale)] per dimension, h a CUDA
+    complex64 tensor holding the filter spectrum (kept alive by the plan).
+    ``execute`` computes scale * IDFT(H . DFT(x)) along every dimension."""
+
+    def __init__(self, n, batch: int, filters, **options):
+        import torch
+        self.shape = _shape(n)
+        self.batch = int(batch)
+        self.direction = FFT_FORWARD
+        self.handle = None
+        self.filters = []
+        spec = []
+        for h, lines, scale in filters:
+            if not isinstance(h, torch.Tensor) or not h.is_cuda or h.dtype != torch.complex64:
+                raise TypeError("filters must be CUDA complex64 tensors")
+            if not h.is_contiguous():
+                raise ValueError("filters must be contiguous")
+            self.filters.append(h)
+            spec.append((h.data_ptr(), lines, scale))
+        self.handle = fft_conv_plan_create(self.shape, self.batch, spec, **options)
 
 
 # ----------------------------------------------------------------- serving --

@@ -43,6 +43,13 @@ def load():
                             ctypes.c_int,
                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
                             ctypes.POINTER(ctypes.c_int64)]
+    lib.emu_conv_run.restype = ctypes.c_int64
+    lib.emu_conv_run.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int64,
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(Options), ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p,
+                                 ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]
     _lib = lib
     return lib
 
@@ -69,4 +76,32 @@ def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, specialised=True,
     if stats is not None:
         stats["special_passes"] = sp.value % 1000
         stats["staged_passes"] = sp.value // 1000
+    return out, int(nerr), msg.value.decode()
+
+
+def run_conv(x: np.ndarray, shape, filters, specialised=True, stats=None, smem_optin=232448,
+             **opts):
+    """Replay a fast-convolution plan: filters = [(h, lines, scale)] per
+    dimension (h complex64, laid out as fft_filter_t describes)."""
+    lib = load()
+    x = np.ascontiguousarray(x, dtype=np.complex64)
+    dims = len(shape)
+    n = (ctypes.c_int64 * 2)(*shape, *([1] * (2 - dims)))
+    batch = x.size // int(np.prod(shape))
+    out = np.zeros_like(x)
+    hs = [np.ascontiguousarray(f[0], dtype=np.complex64) for f in filters]
+    lines = (ctypes.c_int64 * 2)(*[int(f[1]) for f in filters], *([1] * (2 - dims)))
+    scale = (ctypes.c_float * 2)(*[float(f[2]) for f in filters], *([1.0] * (2 - dims)))
+    ptrs = (ctypes.c_void_p * 2)(*[h.ctypes.data for h in hs], *([None] * (2 - dims)))
+    lens = (ctypes.c_int64 * 2)(*[h.size for h in hs], *([0] * (2 - dims)))
+    o = Options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    msg = ctypes.create_string_buffer(512)
+    sp = ctypes.c_int64(0)
+    nerr = lib.emu_conv_run(n, dims, batch, lines, scale, ptrs, lens, ctypes.byref(o), smem_optin,
+                            1 if specialised else 0, x.ctypes.data, out.ctypes.data, msg, 512,
+                            ctypes.byref(sp))
+    if stats is not None:
+        stats["special_passes"] = sp.value % 1000
     return out, int(nerr), msg.value.decode()

@@ -39,6 +39,8 @@ struct Ctx {
   std::vector<uint8_t>* out_hits = nullptr;
   const cf* tw = nullptr;
   int64_t tw_len = 0;
+  const cf* h = nullptr;  // convolution filter of the pass being replayed
+  int64_t h_len = 0;
   int smem_len = 0;
   std::vector<int64_t>* slot_epoch = nullptr;
   std::vector<int64_t>* slot_write = nullptr;
@@ -77,6 +79,11 @@ struct CheckMem {
     g.out[idx] = v;
   }
   static cf ldtw(const cf* p) {
+    if (g.h && !(p >= g.tw && p < g.tw + g.tw_len)) {  // not a twiddle: a filter load
+      const int64_t off = p - g.h;
+      if (off < 0 || off >= g.h_len) { err("filter load out of bounds", off); return mk(1, 0); }
+      return *p;
+    }
     int64_t off = p - g.tw;
     if (off < 0 || off >= g.tw_len) { err("twiddle load out of bounds", off); return mk(1, 0); }
     return *p;
@@ -155,6 +162,73 @@ void run_pass_t(const PassDesc& d, const cf* in, cf* out) {
       Ns <<= d.rlog[s];
     }
   }
+}
+
+// Fast-convolution tile (conv_tile in the library): round 1 without the final
+// store, the filter phase writing natural order, round 2 with the store.
+template <int R, int MAP, class TR = RtTraits>
+void run_conv_t(const PassDesc& d, const cf* in, cf* out) {
+  using B = PassBody<R, MAP, MAP, CheckMem, TR>;
+  const int nthr = d.G * d.T;
+  std::vector<cf> smem(std::max(1, d.smem_elems));
+  std::vector<int64_t> ep(smem.size(), -1), wr(smem.size(), -1);
+  g.slot_epoch = &ep;
+  g.slot_write = &wr;
+  g.smem_len = d.smem_elems;
+  std::vector<std::array<cf, R>> V(nthr);
+  auto reg = [&](int t) -> cf (&)[R] { return *reinterpret_cast<cf(*)[R]>(V[t].data()); };
+  for (int64_t tile = 0; tile < d.tiles; ++tile) {
+    typename B::Tile tl = B::tile_of(d, tile);
+    ++g.epoch;
+    for (int t = 0; t < nthr; ++t) B::first_nostore(reg(t), d, in, smem.data(), tl, t);
+    auto stages = [&](bool round1) {
+      int Ns = 1 << d.rlog[0];
+      for (int s = 1; s < d.nst; ++s) {
+        for (int t = 0; t < nthr; ++t) {
+          if (round1) B::read_nostore(reg(t), d, s, Ns, smem.data(), tl, t);
+          else B::template read_s<true>(reg(t), d, s, Ns, out, smem.data(), tl, t);
+        }
+        if (s < d.nst - 1) {
+          ++g.epoch;
+          for (int t = 0; t < nthr; ++t) B::write(reg(t), d, s, Ns, smem.data(), t);
+        }
+        Ns <<= d.rlog[s];
+      }
+    };
+    stages(true);
+    ++g.epoch;
+    for (int t = 0; t < nthr; ++t) B::conv_mid(reg(t), d, smem.data(), tl, t);
+    for (int t = 0; t < nthr; ++t) B::first_smem(reg(t), d, smem.data(), t);
+    if (d.nst == 1) {
+      for (int t = 0; t < nthr; ++t) B::store_first(reg(t), d, out, tl, t);
+    } else {
+      ++g.epoch;
+      for (int t = 0; t < nthr; ++t) B::write(reg(t), d, 0, 1, smem.data(), t);
+      stages(false);
+    }
+  }
+}
+
+template <int MAP>
+void run_conv_maps(int R, const PassDesc& d, const cf* in, cf* out) {
+  switch (R) {
+    case 2: run_conv_t<2, MAP>(d, in, out); break;
+    case 4: run_conv_t<4, MAP>(d, in, out); break;
+    case 8: run_conv_t<8, MAP>(d, in, out); break;
+    case 16: run_conv_t<16, MAP>(d, in, out); break;
+    default: err("bad R", R);
+  }
+}
+
+bool run_conv_special(int R, int map, const PassDesc& d, const cf* in, cf* out) {
+#define GB_TRY(LOGL, SCHED, NST, RR, G, LMAP_, SMAP_, CONTIG, EPI)                          \
+  if (shape_matches(d, R, map, map, LOGL, SCHED, NST, RR, G, LMAP_, SMAP_, CONTIG, EPI)) {   \
+    run_conv_t<RR, LMAP_, CtTraits<LOGL, SCHED, NST, RR, G, CONTIG, EPI>>(d, in, out);      \
+    return true;                                                                         \
+  }
+  GB_SHAPES_CONV(GB_TRY)
+#undef GB_TRY
+  return false;
 }
 
 // The same compile-time shapes the GPU library instantiates.
@@ -357,24 +431,15 @@ void run_ct(const PassDesc& d, const cf* in, cf* out) {
   run_pass_t<R, LM, SM, TR>(d, in, out);
 }
 
-}  // namespace
-
-
-
-extern "C" {
-
-// Plans (n, dims, batch, direction, options) for a device with the given
-// limits, replays every pass on the CPU and writes the result to `out`
-// (complex64, same size as `in`).  Returns the number of access violations;
-// the first one is described in msg.
-int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction, int precision,
-                const fft_plan_options_t* opt, int smem_optin, int specialised,
-                const float* in_f, float* out_f, char* msg, size_t msg_len,
-                int64_t* special_passes) {
+int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int precision,
+               const fft_plan_options_t* opt, int smem_optin, int specialised,
+               const float* in_f, float* out_f, char* msg, size_t msg_len,
+               int64_t* special_passes, const ConvSpec* conv, const float* const* filters,
+               const int64_t* filter_len) {
   Caps caps;
   caps.smem_optin = smem_optin;
   static PlanSpec s;
-  make_plan(s, n, dims, batch, direction, precision, opt, caps);
+  make_plan(s, n, dims, batch, direction, precision, opt, caps, conv);
   g = Ctx{};
   if (s.status != FFT_OK) {
     snprintf(msg, msg_len, "plan failed: %s", s.error);
@@ -416,7 +481,16 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction, int pr
     g.out_hits = &hits;
     g.tw = tables.data();
     g.tw_len = s.table_elems;
-    if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);
+    g.h = nullptr;
+    g.h_len = 0;
+    if (p.conv) {
+      d.h = reinterpret_cast<const cf*>(filters[p.h_dim]);
+      g.h = d.h;
+      g.h_len = filter_len[p.h_dim];
+      if (specialised && !s.generic_only && run_conv_special(p.R, p.lmap, d, src, dst)) ++g.special_passes;
+      else if (p.lmap == MAP_ROWS) run_conv_maps<0>(p.R, d, src, dst);
+      else run_conv_maps<1>(p.R, d, src, dst);
+    } else if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);
     else if (specialised && !s.generic_only && run_staged(d, src, dst)) ++g.staged_passes;
     else if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
     else if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
@@ -428,6 +502,38 @@ int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction, int pr
   snprintf(msg, msg_len, "%s", g.first_error.c_str());
   if (special_passes) *special_passes = g.special_passes + 1000 * g.staged_passes;
   return g.errors;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Plans (n, dims, batch, direction, options) for a device with the given
+// limits, replays every pass on the CPU and writes the result to `out`
+// (complex64, same size as `in`).  Returns the number of access violations;
+// the first one is described in msg.
+int64_t emu_run(const int64_t* n, int dims, int64_t batch, int direction, int precision,
+                const fft_plan_options_t* opt, int smem_optin, int specialised,
+                const float* in_f, float* out_f, char* msg, size_t msg_len,
+                int64_t* special_passes) {
+  return replay(n, dims, batch, direction, precision, opt, smem_optin, specialised, in_f, out_f,
+                msg, msg_len, special_passes, nullptr, nullptr, nullptr);
+}
+
+// The same for a fast-convolution plan: filters[d] (complex64, filter_len[d]
+// elements) with lines[d] and scale[d] as in fft_filter_t.
+int64_t emu_conv_run(const int64_t* n, int dims, int64_t batch, const int64_t* lines,
+                     const float* scale, const float* const* filters, const int64_t* filter_len,
+                     const fft_plan_options_t* opt, int smem_optin, int specialised,
+                     const float* in_f, float* out_f, char* msg, size_t msg_len,
+                     int64_t* special_passes) {
+  ConvSpec cs;
+  for (int d = 0; d < dims && d < 2; ++d) {
+    cs.lines[d] = lines[d];
+    cs.scale[d] = scale[d];
+  }
+  return replay(n, dims, batch, -1, 0, opt, smem_optin, specialised, in_f, out_f, msg, msg_len,
+                special_passes, &cs, filters, filter_len);
 }
 
 }  // extern "C"

@@ -96,3 +96,34 @@ def test_sar_frame_plan():
 def test_smaller_device_forces_more_passes():
     d = g.fft_plan_dry_run(2 ** 14, 1, smem_optin_bytes=48 * 1024)
     assert d["max_block_log2"] == 12 and len(d["passes"]) == 2
+
+
+def test_conv_plan_shapes():
+    """SAR compression: range pass over contiguous rows, azimuth pass over
+    strided columns in place, both fused forward/filter/inverse passes."""
+    d = g.fft_conv_plan_dry_run((4096, 8192), 2, [(8192, 1.0 / 4096), (1, 1.0 / 8192)])
+    assert d["conv"] == 1 and d["workspace_bytes"] == 0
+    rg, az = d["passes"]
+    assert rg["L"] == 8192 and rg["lmap"] == rg["smap"] == "rows" and rg["h_dim"] == 1
+    assert rg["h_lines"] == 1 and rg["conj_in"] == 0 and rg["conj_out"] == 1
+    assert az["L"] == 4096 and az["lmap"] == az["smap"] == "cols" and az["h_dim"] == 0
+    assert az["h_lines"] == 8192 and az["src"] == az["dst"] == 1
+    for logn in range(1, 15):
+        p = g.fft_conv_plan_dry_run(2 ** logn, 3, [(3, 1.0)])["passes"][0]
+        assert p["conv"] == 1 and p["smem"] > 0 and p["block"] <= 1024
+        assert len(p["radices"]) >= min(2, logn)
+
+
+@pytest.mark.parametrize("n,batch,filters,status", [
+    ((2 ** 15,), 1, [(1, 1.0)], g.FFT_ERR_NOT_IMPLEMENTED),
+    ((1,), 1, [(1, 1.0)], g.FFT_ERR_UNSUPPORTED_SIZE),
+    ((12,), 1, [(1, 1.0)], g.FFT_ERR_UNSUPPORTED_SIZE),
+    ((64,), 4, [(2, 1.0)], g.FFT_ERR_INVALID_ARG),
+    ((64,), 4, [(0, 1.0)], g.FFT_ERR_INVALID_ARG),
+    ((16, 32), 1, [(16, 1.0), (1, 1.0)], g.FFT_ERR_INVALID_ARG),   # columns filter: 1 or 32
+    ((16, 32), 1, [(32, 1.0), (32, 1.0)], g.FFT_ERR_INVALID_ARG),  # rows filter: 1 or 16
+    ((16, 32), 1, [(1, float("nan")), (1, 1.0)], g.FFT_ERR_INVALID_ARG)])
+def test_conv_dry_run_rejects(n, batch, filters, status):
+    with pytest.raises(g.GbfftError) as e:
+        g.fft_conv_plan_dry_run(n, batch, filters)
+    assert e.value.status == status

@@ -109,3 +109,77 @@ def test_tensor_core_class_replay(oracle, n, precision):
         y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision)
         assert nerr == 0, msg
         assert np.max(oracle.rel_l2(y, oracle.fft(x, d))) <= TC_TOL[precision](n)
+
+
+# ---------------------------------------------------------------- convolution --
+
+def _conv_filters(oracle, shape, batch, per_line, seed):
+    """Filter spectra (complex64, the oracle's FP64 DFT of seeded kernels) in
+    the layout fft_filter_t describes, and the matching oracle arguments."""
+    if len(shape) == 1:
+        n = shape[0]
+        c = synth.uniform(seed, batch if per_line[0] else 1, n)
+        h = oracle.fft(c).astype(np.complex64)
+        h = h if per_line[0] else h[0]
+        return [(h, batch if per_line[0] else 1, 1.0 / n)]
+    rows, cols = shape
+    cr = synth.uniform(seed, rows if per_line[1] else 1, cols)
+    hr = oracle.fft(cr).astype(np.complex64)
+    hr = hr if per_line[1] else hr[0]
+    ca = synth.uniform(seed + 1, cols if per_line[0] else 1, rows)   # one kernel per column
+    ha = oracle.fft(ca).astype(np.complex64)
+    ha = np.ascontiguousarray(ha.T) if per_line[0] else ha[0]      # column c's filter in column c
+    return [(ha, cols if per_line[0] else 1, 1.0 / rows), (hr, rows if per_line[1] else 1, 1.0 / cols)]
+
+
+def conv_reference(oracle, x, shape, filters):
+    if len(shape) == 1:
+        h, _, sc = filters[0]
+        return oracle.conv(x, h.astype(np.complex128), sc)
+    (ha, _, sa), (hr, _, sr) = filters
+    return oracle.conv2d(x, hr.astype(np.complex128), sr, ha.astype(np.complex128), sa)
+
+
+def _check_conv(oracle, shape, batch, per_line=(False, False), seed=3, specialised=True,
+                expect_special=None, **opts):
+    n = int(np.prod(shape))
+    x = synth.uniform(seed, batch, n).reshape((batch,) + tuple(shape))
+    filters = _conv_filters(oracle, shape, batch, per_line, seed + 10)
+    st = {}
+    y, nerr, msg = emu.run_conv(x, shape, filters, specialised=specialised, stats=st, **opts)
+    assert nerr == 0, msg
+    if expect_special is not None:
+        assert st["special_passes"] == expect_special
+    ref = conv_reference(oracle, x, shape, filters)
+    err = oracle.rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1))
+    # two transforms per line (forward, inverse): twice the single-FFT bound
+    tol = 2e-6 * max(1.0, np.log2(max(shape)))
+    assert np.max(err) <= tol, (shape, batch, per_line, np.max(err))
+
+
+@pytest.mark.parametrize("logn", range(1, 15))
+@pytest.mark.parametrize("per_line", [False, True])
+def test_conv_lines(oracle, logn, per_line):
+    _check_conv(oracle, (2 ** logn,), 3, (per_line, False))
+
+
+@pytest.mark.parametrize("logn", [12, 13, 14])
+def test_conv_compile_time_shapes(oracle, logn):
+    _check_conv(oracle, (2 ** logn,), 2, expect_special=1)
+    _check_conv(oracle, (2 ** logn,), 2, specialised=False, expect_special=0)
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (8, 16), (16, 8), (64, 32), (4, 8192)])
+@pytest.mark.parametrize("per_line", [(False, False), (True, True), (True, False)])
+def test_conv_frames(oracle, shape, per_line):
+    _check_conv(oracle, shape, 2, per_line)
+
+
+def test_conv_azimuth_shape(oracle):
+    """4096-point columns run the compile-time column shape (4 per tile)."""
+    _check_conv(oracle, (4096, 8), 1, (True, False), expect_special=1)
+
+
+@pytest.mark.parametrize("radix,tile", [(4, 0), (8, 2), (2, 4), (16, 8)])
+def test_conv_forced_radix_and_tile(oracle, radix, tile):
+    _check_conv(oracle, (1024,), 7, (True, False), radix=radix, tile=tile)
