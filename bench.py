@@ -468,9 +468,10 @@ def ours_compress(args, rank: int, world: int) -> None:
     with gbfft.Plan(rows, cols, -1) as p:
         ha = p.execute(az_t.reshape(-1)).reshape(cols, rows).t().conj().resolve_conj().contiguous()
     del az_t
+    vopt = {"variant": args.variant} if args.variant else {}
     full = gbfft.ConvPlan((rows, cols), 1, [(ha.reshape(-1), cols, 1.0 / rows),
-                                            (hr, 1, 1.0 / cols)])
-    rng_only = gbfft.ConvPlan(cols, rows, [(hr, 1, 1.0 / cols)])
+                                            (hr, 1, 1.0 / cols)], **vopt)
+    rng_only = gbfft.ConvPlan(cols, rows, [(hr, 1, 1.0 / cols)], **vopt)
     stream = torch.cuda.current_stream()
 
     def timed(plan, steps):
@@ -519,7 +520,7 @@ def ours_compress(args, rank: int, world: int) -> None:
             "data": "synthetic: 50 point scatterers, LFM range chirp BT=500, range-dependent "
                     "azimuth chirps of 512 samples, SNR 10 dB (seed 31)",
             "config": {"workload": "SAR range + azimuth compression, 4096 x 8192 complex64 frame, "
-                                   "per-range-bin azimuth filters",
+                                   "per-range-bin azimuth filters", "variant": args.variant,
                        "l2": "frame and azimuth filters 256 MiB each, larger than L2; no flush"},
             "frames_per_s": 1e3 / ms_full,
             "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],

@@ -112,12 +112,14 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *   tile          transforms per thread block for passes that allow a choice.
  *   generic       1: run every pass with the run-time-parameter kernel even
  *                 where a compile-time specialisation of the shape exists.
- *   variant       kernel variant for batched contiguous passes: 0 library
- *                 choice, 1 register kernel (one tile per block), 2 TMA-staged
- *                 kernel (N = 2^12..2^14: the next transform is copied into
- *                 shared memory while the current one is computed), 3 register
+ *   variant       kernel variant: 0 library choice, 1 register kernel (one
+ *                 tile per block), 2 TMA-staged kernel (batched contiguous
+ *                 N = 2^12..2^14: the next transform is copied into shared
+ *                 memory while the current one is computed), 3 register
  *                 kernel on a persistent grid that prefetches its next tile
- *                 into L2.
+ *                 into L2 (every pass with a compile-time shape: contiguous
+ *                 tiles, and the strided column tiles of two-pass and 2D
+ *                 plans).
  *   epilogue      how a two-pass 1D plan finds the twiddle w_N^{n2 k1} applied
  *                 between its passes: 0 library choice, 1 two small tables
  *                 (w = hi[m >> b] * lo[m mod 2^b]), 2 one table of N entries laid
@@ -134,7 +136,7 @@ typedef struct {
   int max_block_log2;
   int tile;
   int generic;      /* 1: never use the compile-time specialised kernels (testing) */
-  int variant;      /* contiguous-pass kernel variant, see above */
+  int variant;      /* kernel variant, see above */
   int epilogue;     /* four-step twiddle source, see above */
   int split_log2;   /* two-pass split N = N1 * N2, log2 N1 */
   int reserved[4];
@@ -248,8 +250,9 @@ typedef struct {
  * rows of a 2D frame).  Every length must be a power of two in [2, 2^14] (one
  * line per on-chip block); longer lines return FFT_ERR_NOT_IMPLEMENTED.  FP32
  * only.  Execute with fft_execute / fft_execute_host / fft_execute_graph;
- * in == out is allowed.  options may be NULL; radix, schedule, tile and
- * generic apply, autotune and variant are ignored.
+ * in == out is allowed.  options may be NULL; radix, schedule, tile, generic
+ * and variant (3: persistent grid prefetching each block's next tile into L2)
+ * apply, autotune is ignored.
  */
 GBFFT_API fft_status_t fft_conv_plan_create(fft_plan_t* plan, const int64_t* n, int dims,
                                             int64_t batch, const fft_filter_t* filters,

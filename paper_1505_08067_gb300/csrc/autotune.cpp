@@ -317,15 +317,19 @@ fft_status_t autotune_options(const int64_t* n, int dims, int64_t batch, int dir
       }
     }
   } else if (dims == 1 && def.passes.size() == 2) {
+    // split N = N1 * N2, four-step twiddle source, and the persistent grid
+    // with L2 prefetch of the next tile (variant 3)
     const int l1d = def.passes[0].logL;
     for (int l1 = l1d - 1; l1 <= l1d + 1; ++l1)
-      for (int ep : {2, 3}) {
-        if (ep == 2 && logN > 22) continue;
-        fft_plan_options_t o = b;
-        o.split_log2 = l1;
-        o.epilogue = ep;
-        cand.push_back(o);
-      }
+      for (int ep : {2, 3})
+        for (int v : {0, 3}) {
+          if (ep == 2 && logN > 22) continue;
+          fft_plan_options_t o = b;
+          o.split_log2 = l1;
+          o.epilogue = ep;
+          o.variant = v;
+          cand.push_back(o);
+        }
   } else if (dims == 2) {
     for (int v : {1, 2, 3}) {
       fft_plan_options_t o = b;

@@ -41,7 +41,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
         e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
         if (e != cudaSuccess) return e;
       }
-      if (p.variant == 3 && l.specialised && p.batch_is_tiles) {
+      if (p.variant == 3 && l.specialised) {
         int per_sm = 0;
         e = occupancy(l, &per_sm);
         if (e != cudaSuccess) return e;

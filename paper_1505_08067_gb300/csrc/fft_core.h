@@ -38,8 +38,26 @@ struct alignas(8) cf {
 };
 
 GB_HD cf mk(float x, float y) { cf r; r.x = x; r.y = y; return r; }
+
+// Complex add / subtract.  On sm_100 and later one paired-FP32 instruction
+// does both halves (same IEEE round-to-nearest result per component; a - b
+// is b * (-1) + a, whose single rounding equals the subtraction's).
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define GB_PAIRED 1
+__device__ __forceinline__ float2 f2(cf a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ cf fc(float2 a) { cf r; r.x = a.x; r.y = a.y; return r; }
+GB_HD cf cadd(cf a, cf b) { return fc(__fadd2_rn(f2(a), f2(b))); }
+GB_HD cf csub(cf a, cf b) { return fc(__ffma2_rn(f2(b), make_float2(-1.f, -1.f), f2(a))); }
+// a + s * (b.y, b.x) with s = (sx, sy) in {+1, -1}^2: adds a quarter-turn
+// rotation of b without moving b's halves first.
+GB_HD cf cadd_rot(cf a, cf b, float sx, float sy) {
+  return fc(__ffma2_rn(make_float2(b.y, b.x), make_float2(sx, sy), f2(a)));
+}
+#else
 GB_HD cf cadd(cf a, cf b) { return mk(a.x + b.x, a.y + b.y); }
 GB_HD cf csub(cf a, cf b) { return mk(a.x - b.x, a.y - b.y); }
+GB_HD cf cadd_rot(cf a, cf b, float sx, float sy) { return mk(a.x + sx * b.y, a.y + sy * b.x); }
+#endif
 GB_HD cf cmul(cf a, cf b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 GB_HD cf cconj(cf a) { return mk(a.x, -a.y); }
 
@@ -82,11 +100,10 @@ GB_HD void dft_small(cf* v) {
     cf a0 = v[0], a1 = v[S], a2 = v[2 * S], a3 = v[3 * S];
     cf t0 = cadd(a0, a2), t1 = csub(a0, a2);
     cf t2 = cadd(a1, a3), t3 = csub(a1, a3);
-    t3 = mk(t3.y, -t3.x);  // * (-i)
     v[0] = cadd(t0, t2);
     v[2 * S] = csub(t0, t2);
-    v[S] = cadd(t1, t3);
-    v[3 * S] = csub(t1, t3);
+    v[S] = cadd_rot(t1, t3, 1.f, -1.f);      // t1 - i*t3
+    v[3 * S] = cadd_rot(t1, t3, -1.f, 1.f);  // t1 + i*t3
   }
 }
 

@@ -89,6 +89,36 @@ __device__ __forceinline__ void pass_tile(const cf* __restrict__ in, cf* out, co
   __syncthreads();  // shared memory is reused by the next tile
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
+}
+
+// Pull the input of tile `tile` into L2 (persistent grids: a block's next
+// tile streams in while the current one is computed, so its stage-0 loads hit
+// L2 instead of DRAM).  Two tile layouts: G whole contiguous transforms (one
+// 128-byte line per thread and pass of the loop), or G adjacent columns of a
+// strided pass (the first and last line of each row's G elements).
+template <class TR>
+__device__ __forceinline__ void prefetch_tile(const cf* in, const PassDesc& d, int64_t tile,
+                                              int tid) {
+  const int64_t L = int64_t(1) << TR::logL(d);
+  const int64_t outer = tile / d.tiles_inner, inner = tile - outer * d.tiles_inner;
+  const cf* base = in + outer * d.in.o + inner * d.in.t;
+  if (TR::in_e(d) == 1 && TR::in_g(d) == L) {
+    const int64_t left = (d.count_inner - inner * TR::G(d)) * L;  // ragged last tile
+    const int64_t valid = min((int64_t)TR::G(d) * L, left);
+    const char* b = reinterpret_cast<const char*>(base);
+    for (int64_t line = tid; line * 16 < valid; line += blockDim.x) prefetch_l2(b + line * 128);
+  } else if (TR::in_g(d) == 1) {
+    const int64_t gl = min((int64_t)TR::G(d), d.count_inner - inner * TR::G(d)) - 1;
+    for (int64_t a = tid; a < L; a += blockDim.x) {
+      const cf* row = base + a * TR::in_e(d);
+      prefetch_l2(row);
+      prefetch_l2(row + gl);
+    }
+  }
+}
+
 // Stages s = 1 .. nst-1 of one round of a convolution tile.  Round 1 keeps
 // the last stage's results in registers; round 2 stores them (swap undone).
 template <int R, int MAP, class TR, bool ROUND1>
@@ -153,8 +183,11 @@ __global__ void __launch_bounds__(1024)
 stockham_conv(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* sm = reinterpret_cast<cf*>(smem_raw);
-  for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x)
+  for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
+    if (d.l2_prefetch && tile + gridDim.x < d.tiles)
+      prefetch_tile<TR>(in, d, tile + gridDim.x, threadIdx.x);
     conv_tile<R, MAP, TR>(in, out, d, tile, sm, threadIdx.x);
+  }
 }
 
 // Coalesced launch of several same-shape jobs (separate buffers): the job
@@ -187,19 +220,7 @@ stockham_pass(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
     const typename B::Tile tl = B::tile_of(d, tile);
-    if constexpr (TR::kContig) {
-      // Persistent grids: pull this block's next tile into L2 while the
-      // current one is computed (one 128-byte line per thread and pass of
-      // this loop), so its stage-0 loads hit L2 instead of DRAM.
-      if (d.l2_prefetch && tile + gridDim.x < d.tiles) {
-        const int64_t L = int64_t(1) << TR::logL(d);
-        const int64_t tile_elems = (int64_t)TR::G(d) * L;
-        const int64_t valid = min(tile_elems, d.count_inner * L - (tile + gridDim.x) * tile_elems);
-        const char* base = reinterpret_cast<const char*>(in + (tile + gridDim.x) * tile_elems);
-        for (int64_t line = tid; line * 16 < valid; line += blockDim.x)
-          asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(base + line * 128));
-      }
-    }
+    if (d.l2_prefetch && tile + gridDim.x < d.tiles) prefetch_tile<TR>(in, d, tile + gridDim.x, tid);
     cf v[R];
     B::first(v, d, in, out, sm, tl, tid);
     int Ns = 1 << TR::rlog(d, 0);

@@ -408,7 +408,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   // launch shapes and twiddle tables
   int64_t off = 0;
   for (auto& p : s.passes) {
-    if (p.batch_is_tiles && !p.conv) p.variant = o.variant;
+    p.variant = o.variant;  // kernels without a staged / prefetching form ignore it
     const char* err = nullptr;
     if (!fill_launch(p, caps, err)) { fail(FFT_ERR_INVALID_ARG, err); return; }
     if (p.kind != PASS_FFT) continue;

@@ -92,6 +92,14 @@ def test_conv_frames(gb, oracle, shape, per_line):
     _check(gb, oracle, shape, 2, per_line)
 
 
+@pytest.mark.parametrize("shape,batch,per_line", [((8192,), 700, (True, False)),
+                                                  ((4096, 8192), 1, (True, False)),
+                                                  ((1024, 512), 3, (True, True))])
+def test_conv_prefetch_variant(gb, oracle, shape, batch, per_line):
+    """Persistent grid with L2 prefetch of the next tile (variant 3)."""
+    _check(gb, oracle, shape, batch, per_line, variant=3)
+
+
 def test_conv_in_place_and_graph(gb, oracle):
     _check(gb, oracle, (256, 512), 2, (True, False), in_place=True)
     _check(gb, oracle, (1024,), 33, (True, False), graph=True)

@@ -289,6 +289,25 @@ def test_kernel_variants(gb, oracle, variant, logn):
         assert np.max(oracle.rel_l2(y[idx], ref)) <= _tol(n)
 
 
+@pytest.mark.parametrize("shape,batch", [((2 ** 16,), 5), ((2 ** 20,), 2), ((2 ** 22,), 1),
+                                         ((512, 1024), 3), ((4096, 8192), 1)])
+def test_prefetch_variant_strided_passes(gb, oracle, shape, batch):
+    """Variant 3 on two-pass and 2D plans: persistent grids whose strided
+    column tiles prefetch the next tile into L2 (a tile count that is not a
+    multiple of the grid)."""
+    n = int(np.prod(shape))
+    x = synth.uniform(9300 + int(np.log2(n)), batch, n).reshape((batch,) + shape)
+    for d in (-1, 1):
+        y = _run(gb, x, shape, d, variant=3)
+        if len(shape) == 1:
+            idx = np.unique(np.r_[0, batch - 1])
+            ref = oracle.fft_select(x, idx, d)
+            assert np.max(oracle.rel_l2(y[idx], ref)) <= _tol(n)
+        else:
+            ref = oracle.fft2d(x, d)
+            assert np.max(oracle.rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1))) <= _tol(n)
+
+
 @pytest.mark.parametrize("epilogue", [1, 2, 3])
 @pytest.mark.parametrize("logn", [16, 20, 22])
 def test_four_step_twiddle_sources(gb, oracle, epilogue, logn):
