@@ -32,11 +32,12 @@
 
 namespace gbfft {
 
-// Compile-time shape of a staged pass.
-template <int LOGL, uint32_t SCHED, int NST>
+// Compile-time shape of a staged pass; R elements (R/16 radix-16
+// butterflies) per thread.
+template <int LOGL, uint32_t SCHED, int NST, int R_ = 32>
 struct SplitShape {
   static constexpr int kL = 1 << LOGL;
-  static constexpr int kR = 32;                   // two radix-16 butterflies per thread
+  static constexpr int kR = R_;
   static constexpr int kT = kL / kR;              // threads per transform (= per block)
   static constexpr int kHalf = kL / 2;            // exchange buffer holds half a transform
   static constexpr int kHalfSlots = kHalf + (kHalf >> 4) + 1;
@@ -46,6 +47,14 @@ struct SplitShape {
   GB_HDC static constexpr int ns_before(int s) {
     return s == 0 ? 1 : ns_before(s - 1) * radix(s - 1);
   }
+  // A final stage of radix NB = R/16 after a radix-16 one runs in registers:
+  // stage nst-2 has Ns = L/(16 NB) = T, so thread t's butterflies
+  // jb = q*T + t (q < NB) write outputs p + q*L/NB with p = t + i*T (i < 16)
+  // -- exactly the NB inputs of the last stage's butterfly p (Ns = L/NB).
+  // One shared-memory exchange fewer.
+  static constexpr int kNB = R_ / 16;
+  static constexpr bool kFuseLast = NST >= 2 && radix(NST - 1) == kNB && rlog(NST - 2) == 4;
+  static constexpr int kExchanges = kFuseLast ? NST - 2 : NST - 1;
 };
 
 template <class SH, class Mem>
@@ -136,6 +145,30 @@ GB_UNROLL
     }
 GB_UNROLL
     for (int i = 0; i < R; ++i) v[i] = w[i];
+  }
+
+  // ------------ fused last stage (radix NB) + store (SH::kFuseLast) ------
+  // v[q*16 + i] holds output i of butterfly q of stage nst-2, i.e. element
+  // p + q*Ns with p = t + i*T and Ns = L/NB.  The last stage's butterfly p
+  // multiplies input q by w_L^{q p} (row q of the i-major table), takes a
+  // length-NB DFT and writes output q to p + q*Ns.
+  template <bool SWAP>
+  GB_HD static void store_fused(const cf (&v)[R], const PassDesc& d, cf* out, int t) {
+    constexpr int s = SH::kNst - 1;
+    constexpr int NB = SH::kNB;
+    constexpr int Ns = L / NB;
+    const cf* tw = d.tw + d.tw_off[s];
+GB_UNROLL
+    for (int i = 0; i < 16; ++i) {
+      const int p = t + i * T;
+      cf x[NB];
+      x[0] = v[i];
+GB_UNROLL
+      for (int q = 1; q < NB; ++q) x[q] = cmul(v[q * 16 + i], Mem::ldtw(tw + q * Ns + p));
+      dft_radix<NB>(x);
+GB_UNROLL
+      for (int q = 0; q < NB; ++q) Mem::stg(out, p + q * Ns, SWAP ? mk(x[q].y, x[q].x) : x[q]);
+    }
   }
 
   // ------------------------------------------------ last stage to global --

@@ -42,11 +42,12 @@
 
 // Contiguous transforms that run the staged kernel (fft_split.h): whole
 // transform per block, TMA prefetch of the next one, half-size exchanges.
-//   GB_STAGED(log2 L, schedule, stages, blocks per SM)
+//   GB_STAGED(log2 L, schedule, stages, blocks per SM, elements per thread)
+// 2^13 and 2^14 end with a stage of radix R/16, run in registers.
 #define GB_STAGED_SHAPES(GB_STAGED) \
-  GB_STAGED(12, 0x444, 3, 4)        \
-  GB_STAGED(13, 0x1444, 4, 2)       \
-  GB_STAGED(14, 0x2444, 4, 1)
+  GB_STAGED(12, 0x444, 3, 4, 32)    \
+  GB_STAGED(13, 0x1444, 4, 2, 32)   \
+  GB_STAGED(14, 0x2444, 4, 1, 64)
 
 namespace gbfft {
 

@@ -351,12 +351,18 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     cf v[SH::kR];
     if (d.conj_in) B::template first<true>(v, st, tid);
     else B::template first<false>(v, st, tid);
+    static_assert(SH::kExchanges >= 1, "the first exchange issues the next copy");
     split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid);
-    if constexpr (SH::kNst > 2) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid);
-    if constexpr (SH::kNst > 3) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
+    if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid);
+    if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
     cf* o = out + tile * SH::kL;
-    if (d.conj_out) B::template store<true>(v, o, tid);
-    else B::template store<false>(v, o, tid);
+    if constexpr (SH::kFuseLast) {
+      if (d.conj_out) B::template store_fused<true>(v, d, o, tid);
+      else B::template store_fused<false>(v, d, o, tid);
+    } else {
+      if (d.conj_out) B::template store<true>(v, o, tid);
+      else B::template store<false>(v, o, tid);
+    }
   }
 }
 

@@ -14,9 +14,9 @@ const void* resolve_contig_shape(int R, int lmap, int smap, const PassDesc& d) {
 }
 
 bool resolve_staged_shape(const PassDesc& d, StagedLaunch* s) {
-#define GB_STAGED(LOGL, SCHED, NST, MINB)                    \
+#define GB_STAGED(LOGL, SCHED, NST, MINB, RR)                \
   if (staged_shape_matches(d, LOGL, SCHED, NST)) {           \
-    using SH = SplitShape<LOGL, SCHED, NST>;                 \
+    using SH = SplitShape<LOGL, SCHED, NST, RR>;             \
     s->fn = (const void*)staged_fn<SH, MINB>();              \
     s->block = SH::kT;                                       \
     s->smem = split_smem_bytes<SH>();                        \

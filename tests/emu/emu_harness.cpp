@@ -280,20 +280,25 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       }
     };
     exchange(std::integral_constant<int, 0>());
-    if constexpr (SH::kNst > 2) exchange(std::integral_constant<int, 1>());
-    if constexpr (SH::kNst > 3) exchange(std::integral_constant<int, 2>());
+    if constexpr (SH::kExchanges > 1) exchange(std::integral_constant<int, 1>());
+    if constexpr (SH::kExchanges > 2) exchange(std::integral_constant<int, 2>());
     for (int t = 0; t < SH::kT; ++t) {
-      if (d.conj_out) B::template store<true>(reg(t), out + tile * SH::kL, t);
-      else B::template store<false>(reg(t), out + tile * SH::kL, t);
+      if constexpr (SH::kFuseLast) {
+        if (d.conj_out) B::template store_fused<true>(reg(t), d, out + tile * SH::kL, t);
+        else B::template store_fused<false>(reg(t), d, out + tile * SH::kL, t);
+      } else {
+        if (d.conj_out) B::template store<true>(reg(t), out + tile * SH::kL, t);
+        else B::template store<false>(reg(t), out + tile * SH::kL, t);
+      }
     }
   }
   g.staging = nullptr;
 }
 
 bool run_staged(const PassDesc& d, const cf* in, cf* out) {
-#define GB_TRY_STAGED(LOGL, SCHED, NST, MINB)                 \
+#define GB_TRY_STAGED(LOGL, SCHED, NST, MINB, RR)             \
   if (staged_shape_matches(d, LOGL, SCHED, NST)) {            \
-    run_staged_t<SplitShape<LOGL, SCHED, NST>>(d, in, out);   \
+    run_staged_t<SplitShape<LOGL, SCHED, NST, RR>>(d, in, out); \
     return true;                                              \
   }
   GB_STAGED_SHAPES(GB_TRY_STAGED)
