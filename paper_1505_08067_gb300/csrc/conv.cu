@@ -35,4 +35,21 @@ const void* resolve_conv_kernel(int R, int map, const PassDesc& d, bool generic_
   return generic_conv(R, map);
 }
 
+// Staged convolution kernels: one contiguous line per block, the next line
+// copied into shared memory by TMA, the filter applied in registers between
+// the two rounds.
+bool resolve_conv_staged_shape(const PassDesc& d, StagedLaunch* s) {
+#define GB_STAGED(LOGL, SCHED, NST, MINB, RR)                  \
+  if (staged_shape_matches(d, LOGL, SCHED, NST, true)) {       \
+    using SH = SplitShape<LOGL, SCHED, NST, RR>;               \
+    s->fn = (const void*)staged_fn<SH, MINB, true>();          \
+    s->block = SH::kT;                                         \
+    s->smem = split_smem_bytes<SH>();                          \
+    return true;                                               \
+  }
+  GB_STAGED_SHAPES(GB_STAGED)
+#undef GB_STAGED
+  return false;
+}
+
 }  // namespace gbfft

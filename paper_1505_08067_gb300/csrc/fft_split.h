@@ -171,6 +171,56 @@ GB_UNROLL
     }
   }
 
+  // ---------------------------- fast convolution: between the two rounds --
+  // After round 1 (the forward stages; with SH::kFuseLast the last one is
+  // computed here) this thread holds the spectrum at positions t + m*T,
+  // m < R.  Each value is multiplied by h_scale * H[position] and swapped
+  // (re <-> im), and round 2's stage 0 (radix 16), whose butterfly q reads
+  // positions t + (q + i*NB)*T, runs on the registers: no exchange between
+  // the rounds.  `line` selects the line's filter (PassDesc::h_lines).
+  GB_HD static void conv_middle(cf (&v)[R], const PassDesc& d, int64_t line, int t) {
+    constexpr int NB = SH::kNB;
+    static_assert(SH::radix(0) == 16, "round 2 starts with a radix-16 stage");
+    cf y[R];  // y[m]: spectrum at position t + m*T
+    if constexpr (SH::kFuseLast) {
+      constexpr int s = SH::kNst - 1;
+      constexpr int Ns = L / NB;
+      const cf* tw = d.tw + d.tw_off[s];
+GB_UNROLL
+      for (int i = 0; i < 16; ++i) {
+        const int p = t + i * T;
+        cf x[NB];
+        x[0] = v[i];
+GB_UNROLL
+        for (int q = 1; q < NB; ++q) x[q] = cmul(v[q * 16 + i], Mem::ldtw(tw + q * Ns + p));
+        dft_radix<NB>(x);
+GB_UNROLL
+        for (int q = 0; q < NB; ++q) y[i + 16 * q] = x[q];  // position p + q*L/NB
+      }
+    } else {
+      // last stage radix 16, Ns = L/16: output i of butterfly q*T + t is at
+      // t + (q + i*NB)*T
+GB_UNROLL
+      for (int q = 0; q < NB; ++q)
+GB_UNROLL
+        for (int i = 0; i < 16; ++i) y[q + i * NB] = v[q * 16 + i];
+    }
+    const cf* h = d.h;
+    if (d.h_lines > 1) h += ((d.h_first + line) % d.h_lines) * (int64_t)L;
+    const float sc = d.h_scale;
+GB_UNROLL
+    for (int m = 0; m < R; ++m) {
+      const cf z = cmul(y[m], Mem::ldtw(h + t + m * T));
+      y[m] = mk(z.y * sc, z.x * sc);
+    }
+GB_UNROLL
+    for (int q = 0; q < NB; ++q) {
+GB_UNROLL
+      for (int i = 0; i < 16; ++i) v[q * 16 + i] = y[q + i * NB];
+      dft_radix<16>(v + q * 16);
+    }
+  }
+
   // ------------------------------------------------ last stage to global --
   template <bool SWAP>
   GB_HD static void store(const cf (&v)[R], cf* out, int t) {

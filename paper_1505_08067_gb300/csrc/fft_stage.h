@@ -251,6 +251,33 @@ GB_UNROLL
     }
   }
 
+  // When the last stage and stage 0 both have radix R (one butterfly per
+  // thread), the thread's round-1 outputs t + i*L/R are exactly the inputs of
+  // its round-2 stage-0 butterfly: filter, swap and DFT in registers, no
+  // exchange between the rounds.
+  GB_HD static bool conv_in_regs(const PassDesc& d) {
+    return (1 << TR::rlog(d, TR::nst(d) - 1)) == R && (1 << TR::rlog(d, 0)) == R;
+  }
+  GB_HD static void conv_regs(cf (&v)[R], const PassDesc& d, const Tile& tl, int tid) {
+    int g, t;
+    thread_coords(LMAP, tid, TR::T(d), TR::G(d), g, t);
+    const int64_t u = tl.inner * TR::G(d) + g;
+    const cf* hb = d.h;
+    int64_t he = 1;
+    if (d.h_lines > 1) {
+      hb += ((d.h_first + u) % d.h_lines) * TR::in_g(d);
+      he = TR::in_e(d);
+    }
+    const float sc = d.h_scale;
+    const int stride = (1 << TR::logL(d)) / R;
+GB_UNROLL
+    for (int i = 0; i < R; ++i) {
+      const cf x = cmul(v[i], Mem::ldtw(hb + (int64_t)(t + i * stride) * he));
+      v[i] = mk(x.y * sc, x.x * sc);
+    }
+    dft_radix<R>(v);
+  }
+
   // Stage 0 of round 2: the loads of first_r, from shared memory.  Results
   // stay in registers; the caller writes them after a barrier.
   template <int RR>

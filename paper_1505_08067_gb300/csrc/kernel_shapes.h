@@ -66,13 +66,15 @@ GB_HD bool shape_matches(const PassDesc& d, int R, int lmap, int smap, int logL,
 }
 
 // Is `d` a pass the staged kernel of this (log2 L, schedule, stages) runs?
-// One whole contiguous transform per tile, no four-step epilogue.
-GB_HD bool staged_shape_matches(const PassDesc& d, int logL, uint32_t sched, int nst) {
+// One whole contiguous transform per tile, no four-step epilogue; `conv`
+// selects the fast-convolution form.
+GB_HD bool staged_shape_matches(const PassDesc& d, int logL, uint32_t sched, int nst,
+                                bool conv = false) {
   uint32_t s = 0;
   for (int i = 0; i < d.nst && i < 8; ++i) s |= (uint32_t)d.rlog[i] << (4 * i);
   if (d.nst > 8) return false;
   const int64_t L = int64_t(1) << d.logL;
-  return d.G == 1 && d.epi == 0 && d.conv == 0 && d.in.e == 1 && d.out.e == 1 && d.in.t == L && d.out.t == L &&
+  return d.G == 1 && d.epi == 0 && d.conv == (conv ? 1 : 0) && d.in.e == 1 && d.out.e == 1 && d.in.t == L && d.out.t == L &&
          d.logL == logL && s == sched && d.nst == nst;
 }
 

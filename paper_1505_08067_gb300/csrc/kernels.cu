@@ -73,7 +73,7 @@ const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool ge
 
 bool resolve_staged(const PassDesc& d, bool generic_only, StagedLaunch* s) {
   if (generic_only) return false;
-  return resolve_staged_shape(d, s);
+  return d.conv ? resolve_conv_staged_shape(d, s) : resolve_staged_shape(d, s);
 }
 
 cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count) {

@@ -164,10 +164,14 @@ __device__ __forceinline__ void conv_tile(const cf* __restrict__ in, cf* out, co
   cf v[R];
   B::first_nostore(v, d, in, sm, tl, tid);
   conv_stages<R, MAP, TR, true>(v, d, out, sm, tl, tid);
-  __syncthreads();  // every round-1 read of shared memory is done
-  B::conv_mid(v, d, sm, tl, tid);
-  __syncthreads();
-  B::first_smem(v, d, sm, tid);
+  if (B::conv_in_regs(d)) {
+    B::conv_regs(v, d, tl, tid);
+  } else {
+    __syncthreads();  // every round-1 read of shared memory is done
+    B::conv_mid(v, d, sm, tl, tid);
+    __syncthreads();
+    B::first_smem(v, d, sm, tid);
+  }
   if (TR::nst(d) == 1) {
     B::store_first(v, d, out, tl, tid);
   } else {
@@ -320,9 +324,22 @@ __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& 
   __syncthreads();
 }
 
+// The exchanges after stages 0 .. kExchanges-1; the first one starts the
+// copy of `next` into the staging buffer.
+template <class SH>
+__device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
+                                            uint64_t* bar, const cf* next, int tid) {
+  static_assert(SH::kExchanges >= 1, "at least one exchange");
+  split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid);
+  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid);
+  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
+}
+
 // One contiguous transform per block, persistent over tiles; the next
 // transform streams into shared memory by TMA while this one is computed.
-template <class SH, int MINB>
+// CONV: fast convolution of each line (forward stages, filter, forward
+// stages on swapped data; see SplitBody::conv_middle).
+template <class SH, int MINB, bool CONV = false>
 __global__ void __launch_bounds__(SH::kT, MINB)
 stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   extern __shared__ __align__(128) unsigned char smem_staged[];
@@ -351,12 +368,14 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     cf v[SH::kR];
     if (d.conj_in) B::template first<true>(v, st, tid);
     else B::template first<false>(v, st, tid);
-    static_assert(SH::kExchanges >= 1, "the first exchange issues the next copy");
-    split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid);
-    if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid);
-    if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
+    split_round<SH>(v, d, x, st, bar, next, tid);
     cf* o = out + tile * SH::kL;
-    if constexpr (SH::kFuseLast) {
+    if constexpr (CONV) {
+      B::conv_middle(v, d, tile, tid);
+      split_round<SH>(v, d, x, st, bar, nullptr, tid);
+      if constexpr (SH::kFuseLast) B::template store_fused<true>(v, d, o, tid);
+      else B::template store<true>(v, o, tid);
+    } else if constexpr (SH::kFuseLast) {
       if (d.conj_out) B::template store_fused<true>(v, d, o, tid);
       else B::template store_fused<false>(v, d, o, tid);
     } else {
@@ -399,9 +418,9 @@ KernelFn kfn() {
   return stockham_pass<R, LMAP, SMAP, TR>;
 }
 
-template <class SH, int MINB>
+template <class SH, int MINB, bool CONV = false>
 KernelFn staged_fn() {
-  return stockham_staged<SH, MINB>;
+  return stockham_staged<SH, MINB, CONV>;
 }
 
 // Fast-convolution kernels (conv.cu): a compile-time shape if one matches,
@@ -418,5 +437,6 @@ const void* generic_kernel_transposing(int R);  // rows -> columns
 const void* resolve_contig_shape(int R, int lmap, int smap, const PassDesc& d);
 const void* resolve_fourstep_shape(int R, int lmap, int smap, const PassDesc& d);
 bool resolve_staged_shape(const PassDesc& d, StagedLaunch* s);
+bool resolve_conv_staged_shape(const PassDesc& d, StagedLaunch* s);
 
 }  // namespace gbfft

@@ -104,4 +104,5 @@ def run_conv(x: np.ndarray, shape, filters, specialised=True, stats=None, smem_o
                             ctypes.byref(sp))
     if stats is not None:
         stats["special_passes"] = sp.value % 1000
+        stats["staged_passes"] = sp.value // 1000
     return out, int(nerr), msg.value.decode()

@@ -196,9 +196,13 @@ void run_conv_t(const PassDesc& d, const cf* in, cf* out) {
       }
     };
     stages(true);
-    ++g.epoch;
-    for (int t = 0; t < nthr; ++t) B::conv_mid(reg(t), d, smem.data(), tl, t);
-    for (int t = 0; t < nthr; ++t) B::first_smem(reg(t), d, smem.data(), t);
+    if (B::conv_in_regs(d)) {
+      for (int t = 0; t < nthr; ++t) B::conv_regs(reg(t), d, tl, t);
+    } else {
+      ++g.epoch;
+      for (int t = 0; t < nthr; ++t) B::conv_mid(reg(t), d, smem.data(), tl, t);
+      for (int t = 0; t < nthr; ++t) B::first_smem(reg(t), d, smem.data(), t);
+    }
     if (d.nst == 1) {
       for (int t = 0; t < nthr; ++t) B::store_first(reg(t), d, out, tl, t);
     } else {
@@ -219,6 +223,8 @@ void run_conv_maps(int R, const PassDesc& d, const cf* in, cf* out) {
     default: err("bad R", R);
   }
 }
+
+bool run_conv_staged(const PassDesc& d, const cf* in, cf* out);
 
 bool run_conv_special(int R, int map, const PassDesc& d, const cf* in, cf* out) {
 #define GB_TRY(LOGL, SCHED, NST, RR, G, LMAP_, SMAP_, CONTIG, EPI)                          \
@@ -248,7 +254,7 @@ bool run_special(int R, int lmap, int smap, const PassDesc& d, const cf* in, cf*
 
 // Staged kernel (fft_split.h): the TMA copy of a tile into the staging buffer
 // becomes a memcpy; the phase order and barriers follow the kernel.
-template <class SH>
+template <class SH, bool CONV = false>
 void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
   using B = SplitBody<SH, CheckMem>;
   constexpr int R = SH::kR;
@@ -279,9 +285,21 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
         B::template compute<S>(reg(t), d, t);
       }
     };
-    exchange(std::integral_constant<int, 0>());
-    if constexpr (SH::kExchanges > 1) exchange(std::integral_constant<int, 1>());
-    if constexpr (SH::kExchanges > 2) exchange(std::integral_constant<int, 2>());
+    auto round = [&]() {
+      exchange(std::integral_constant<int, 0>());
+      if constexpr (SH::kExchanges > 1) exchange(std::integral_constant<int, 1>());
+      if constexpr (SH::kExchanges > 2) exchange(std::integral_constant<int, 2>());
+    };
+    round();
+    if constexpr (CONV) {
+      for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, tile, t);
+      round();
+      for (int t = 0; t < SH::kT; ++t) {
+        if constexpr (SH::kFuseLast) B::template store_fused<true>(reg(t), d, out + tile * SH::kL, t);
+        else B::template store<true>(reg(t), out + tile * SH::kL, t);
+      }
+      continue;
+    }
     for (int t = 0; t < SH::kT; ++t) {
       if constexpr (SH::kFuseLast) {
         if (d.conj_out) B::template store_fused<true>(reg(t), d, out + tile * SH::kL, t);
@@ -293,6 +311,17 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
     }
   }
   g.staging = nullptr;
+}
+
+bool run_conv_staged(const PassDesc& d, const cf* in, cf* out) {
+#define GB_TRY_STAGED(LOGL, SCHED, NST, MINB, RR)                     \
+  if (staged_shape_matches(d, LOGL, SCHED, NST, true)) {              \
+    run_staged_t<SplitShape<LOGL, SCHED, NST, RR>, true>(d, in, out); \
+    return true;                                                      \
+  }
+  GB_STAGED_SHAPES(GB_TRY_STAGED)
+#undef GB_TRY_STAGED
+  return false;
 }
 
 bool run_staged(const PassDesc& d, const cf* in, cf* out) {
@@ -492,7 +521,10 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
       d.h = reinterpret_cast<const cf*>(filters[p.h_dim]);
       g.h = d.h;
       g.h_len = filter_len[p.h_dim];
-      if (specialised && !s.generic_only && run_conv_special(p.R, p.lmap, d, src, dst)) ++g.special_passes;
+      const bool want_staged = p.variant == 0 || p.variant == 2;
+      if (specialised && !s.generic_only && want_staged && run_conv_staged(d, src, dst))
+        ++g.staged_passes;
+      else if (specialised && !s.generic_only && run_conv_special(p.R, p.lmap, d, src, dst)) ++g.special_passes;
       else if (p.lmap == MAP_ROWS) run_conv_maps<0>(p.R, d, src, dst);
       else run_conv_maps<1>(p.R, d, src, dst);
     } else if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);

@@ -145,7 +145,7 @@ def _check_conv(oracle, shape, batch, per_line=(False, False), seed=3, specialis
     n = int(np.prod(shape))
     x = synth.uniform(seed, batch, n).reshape((batch,) + tuple(shape))
     filters = _conv_filters(oracle, shape, batch, per_line, seed + 10)
-    st = {}
+    st = opts.pop("stats", {})
     y, nerr, msg = emu.run_conv(x, shape, filters, specialised=specialised, stats=st, **opts)
     assert nerr == 0, msg
     if expect_special is not None:
@@ -164,9 +164,16 @@ def test_conv_lines(oracle, logn, per_line):
 
 
 @pytest.mark.parametrize("logn", [12, 13, 14])
-def test_conv_compile_time_shapes(oracle, logn):
-    _check_conv(oracle, (2 ** logn,), 2, expect_special=1)
-    _check_conv(oracle, (2 ** logn,), 2, specialised=False, expect_special=0)
+@pytest.mark.parametrize("per_line", [False, True])
+def test_conv_compile_time_shapes(oracle, logn, per_line):
+    """Lines of 2^12..2^14 run the staged convolution kernel (no exchange
+    between the two rounds); the register kernel (variant 1) and the generic
+    kernel must agree on the same plan."""
+    st = {}
+    _check_conv(oracle, (2 ** logn,), 3, (per_line, False), stats=st)
+    assert st["staged_passes"] == 1 and st["special_passes"] == 0
+    _check_conv(oracle, (2 ** logn,), 3, (per_line, False), expect_special=1, variant=1)
+    _check_conv(oracle, (2 ** logn,), 3, (per_line, False), specialised=False, expect_special=0)
 
 
 @pytest.mark.parametrize("shape", [(2, 2), (8, 16), (16, 8), (64, 32), (4, 8192)])
