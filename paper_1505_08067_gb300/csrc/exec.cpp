@@ -32,6 +32,14 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       cudaError_t e = prepare_launch(l);
       if (e != cudaSuccess) return e;
       if (p.tc_prec) {
+        // persistent grid: the DFT-matrix fragments a block builds once serve
+        // many tiles
+        int per_sm = 0;
+        e = occupancy(l, &per_sm);
+        if (e != cudaSuccess) return e;
+        const int64_t g = (int64_t)std::max(per_sm, 1) * caps.sm_count;
+        l.grid = (int)std::min<int64_t>(g, l.grid);
+        l.persistent_grid = l.grid;
         launches[i] = l;
         continue;
       }

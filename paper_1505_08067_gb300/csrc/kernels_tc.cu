@@ -53,7 +53,9 @@ __device__ __forceinline__ void tc_group(const cf (&x)[8], const uint32_t (&bh)[
 
 // Stage S reads buffer S & 1's predecessor and writes the other one (ping-pong),
 // so a group's outputs go out right after its MMAs; one barrier per stage.
-template <int LOGL, int PREC, int S, bool SI, bool SO>
+// The backward transform's swaps are run-time selects at the first load and
+// the last store (one copy of the tile code).
+template <int LOGL, int PREC, int S>
 __device__ __forceinline__ void tc_stage(const PassDesc& d, const cf* gin, cf* gout, cf* sm,
                                          const uint32_t (&bh)[2][4][2],
                                          const uint32_t (&bl)[2][4][2], int w, int lane,
@@ -65,22 +67,22 @@ __device__ __forceinline__ void tc_stage(const PassDesc& d, const cf* gin, cf* g
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     cf x[8], y[8];
-    B::template gather<S, SI>(x, d, gin, src, w, h, lane, valid);
+    B::template gather<S>(x, d, gin, src, w, h, lane, valid, d.conj_in != 0);
     tc_group<PREC>(x, bh, bl, y);
-    B::template scatter<S, SO>(y, gout, dst, w, h, lane, valid);
+    B::template scatter<S>(y, gout, dst, w, h, lane, valid, d.conj_out != 0);
   }
   __syncthreads();
 }
 
-template <int LOGL, int PREC, bool SI, bool SO>
+template <int LOGL, int PREC>
 __device__ __forceinline__ void tc_tile(const PassDesc& d, const cf* gin, cf* gout, cf* sm,
                                         const uint32_t (&bh)[2][4][2],
                                         const uint32_t (&bl)[2][4][2], int w, int lane,
                                         int valid) {
   constexpr int NST = LOGL / 4;
-  tc_stage<LOGL, PREC, 0, SI, SO>(d, gin, gout, sm, bh, bl, w, lane, valid);
-  if constexpr (NST > 1) tc_stage<LOGL, PREC, 1, SI, SO>(d, gin, gout, sm, bh, bl, w, lane, valid);
-  if constexpr (NST > 2) tc_stage<LOGL, PREC, 2, SI, SO>(d, gin, gout, sm, bh, bl, w, lane, valid);
+  tc_stage<LOGL, PREC, 0>(d, gin, gout, sm, bh, bl, w, lane, valid);
+  if constexpr (NST > 1) tc_stage<LOGL, PREC, 1>(d, gin, gout, sm, bh, bl, w, lane, valid);
+  if constexpr (NST > 2) tc_stage<LOGL, PREC, 2>(d, gin, gout, sm, bh, bl, w, lane, valid);
 }
 
 template <int LOGL, int PREC>
@@ -106,13 +108,7 @@ stockham_tc(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc
     const int valid = rem < TPC ? (int)rem : TPC;
     const cf* gin = in + first * (1 << LOGL);
     cf* gout = out + first * (1 << LOGL);
-    if (d.conj_in) {
-      if (d.conj_out) tc_tile<LOGL, PREC, true, true>(d, gin, gout, sm, bh, bl, w, lane, valid);
-      else tc_tile<LOGL, PREC, true, false>(d, gin, gout, sm, bh, bl, w, lane, valid);
-    } else {
-      if (d.conj_out) tc_tile<LOGL, PREC, false, true>(d, gin, gout, sm, bh, bl, w, lane, valid);
-      else tc_tile<LOGL, PREC, false, false>(d, gin, gout, sm, bh, bl, w, lane, valid);
-    }
+    tc_tile<LOGL, PREC>(d, gin, gout, sm, bh, bl, w, lane, valid);
   }
 }
 

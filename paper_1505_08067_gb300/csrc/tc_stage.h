@@ -140,9 +140,21 @@ GB_HD int tc_point(int lane, int s) {
 
 // Value of the real 32 x 32 B matrix at (k, n): k < 16 re(x_k), else im(x_{k-16});
 // n < 16 re(Y_n), else im(Y_{n-16}); Y_o = sum_i x_i w16^{o i}.
+// cos(2 pi m / 16) for m = 0..15, the constants mul_w16 uses; -sin(2 pi m / 16)
+// is cos16(m + 4).  Branch-free, so the fragments build without divergence.
+GB_HD float cos16(int m) {
+  m &= 15;
+  const int q = m & 7;                         // cos(2 pi (m + 8) / 16) = -cos(2 pi m / 16)
+  const int a = q <= 4 ? q : 8 - q;            // cos is even: |angle| in eighths of a half turn
+  const float mag = a == 0 ? 1.f : a == 1 ? GB_C8 : a == 2 ? GB_H2 : a == 3 ? GB_S8 : 0.f;
+  const bool neg = (q > 4) != (m >= 8);
+  return neg ? -mag : mag;
+}
+
 GB_HD float tc_dft_entry(int k, int n) {
   const int i = k & 15, o = n & 15;
-  const cf w = mul_w16(mk(1.f, 0.f), (i * o) & 15);  // (cos, -sin)(2 pi o i / 16)
+  const int m = (i * o) & 15;
+  const cf w = mk(cos16(m), cos16(m + 4));  // (cos, -sin)(2 pi o i / 16)
   const bool kre = k < 16, nre = n < 16;
   if (kre && nre) return w.x;    //  re(x) cos
   if (!kre && nre) return -w.y;  // -im(x) (-sin)
@@ -204,6 +216,15 @@ GB_HD void tc_outputs(const float (&d)[4][4], cf (&y)[8]) {
 // L = 16^NST.  8 warps; per stage each warp runs 2 MMA groups of 16
 // butterflies (256 butterflies = 4096 / 16 per stage).  Butterfly u of the tile
 // belongs to transform u / (L/16) and is butterfly jb = u mod (L/16) of it.
+//
+// Addressing.  A group is 16 consecutive butterflies u0 .. u0+15 (u0 a
+// multiple of 16).  Every position the group touches -- stage inputs
+// tr*L + jb + i*L/16, stage outputs tr*L + (jb - k)*16 + k + o*Ns, twiddle
+// rows i*Ns + k -- splits into a group base and a per-lane offset with
+// disjoint bits (so base + off = base ^ off), the offset depending only on the
+// lane's fixed (row, point) pairs.  The shared-memory swizzle is linear over
+// GF(2), slot(a ^ b) = slot(a) ^ slot(b), so a lane's slot is
+// slot(base) ^ slot(off): one XOR per element, the offsets computed once.
 template <int LOGL, int PREC, class Mem>
 struct TcBody {
   static constexpr int L = 1 << LOGL;
@@ -211,29 +232,71 @@ struct TcBody {
   static constexpr int BPS = L / 16;    // butterflies per transform and stage
   static constexpr int TPC = 4096 / L;  // transforms per tile
 
-  // Shared-memory slot of tile element e (bijective swizzle of the low four
-  // bits; keeps the fragment-shaped reads and writes near conflict-free).
+  // Shared-memory slot of tile element e: a bijective XOR swizzle of the low
+  // four bits (GF(2)-linear; keeps the fragment-shaped accesses near
+  // conflict-free).
   GB_HD static int slot(int e) { return e ^ (((e >> 4) ^ (e >> 7)) & 15); }
 
+  // Group base and lane offset of input i of the lane's row r (0..15) of the
+  // group starting at butterfly u0, for a stage with Ns = 16^S.
+  GB_HD static void in_pos(int u0, int r, int i, int& base, int& off) {
+    if (BPS == 1) {  // L = 16: one butterfly per transform
+      base = u0 * 16;
+      off = r * 16 + i;
+    } else {
+      const int tr = u0 / BPS, jb0 = u0 - tr * BPS;
+      base = tr * L + jb0;
+      off = r + i * (L / 16);
+    }
+  }
+  // Output o of row r for a stage with Ns (position (jb - k)*16 + k + o*Ns).
+  template <int Ns>
+  GB_HD static void out_pos(int u0, int r, int o, int& base, int& off) {
+    if (BPS == 1) {
+      base = u0 * 16;
+      off = r * 16 + o;
+    } else {
+      const int tr = u0 / BPS, jb0 = u0 - tr * BPS;
+      if (Ns == 1) {
+        base = tr * L + jb0 * 16;
+        off = r * 16 + o;
+      } else {  // Ns >= 16: k = jb0 mod Ns + r
+        const int k0 = jb0 & (Ns - 1);
+        base = tr * L + (jb0 - k0) * 16 + k0;
+        off = r + o * Ns;
+      }
+    }
+  }
+  // First transform of the group and whether all its rows share it.
+  GB_HD static int transform_of(int u0, int r) { return BPS == 1 ? u0 + r : u0 / BPS; }
+
   // Inputs of MMA group h of warp w for stage S: 8 complex values, twiddled.
-  template <int S, bool SWAP>
+  template <int S>
   GB_HD static void gather(cf (&x)[8], const PassDesc& d, const cf* gin, const cf* sm, int w,
-                           int h, int lane, int valid) {
+                           int h, int lane, int valid, bool swap) {
     constexpr int Ns = 1 << (4 * S);
+    const int u0 = w * 32 + h * 16;
+    int base, off0;
+    in_pos(u0, 0, 0, base, off0);
+    const int sbase = slot(base);
+    const cf* tw = nullptr;
+    if (S > 0) {
+      // twiddle row i*Ns + k with k = (jb0 mod Ns) + r (Ns >= 16 divides jb0's block)
+      const int jb0 = BPS == 1 ? 0 : u0 - (u0 / BPS) * BPS;
+      tw = d.tw + d.tw_off[S] + (jb0 & (Ns - 1));
+    }
 GB_UNROLL
     for (int s8 = 0; s8 < 8; ++s8) {
-      const int u = w * 32 + h * 16 + tc_row(lane, s8);
-      const int g = u / BPS, jb = u - g * BPS;
-      const int i = tc_point(lane, s8);
-      const int e = g * L + jb + i * (L / 16);
+      const int r = tc_row(lane, s8), i = tc_point(lane, s8);
+      int b_, off;
+      in_pos(u0, r, i, b_, off);
       cf v;
       if (S == 0) {
-        v = g < valid ? Mem::ldg(gin, e) : mk(0.f, 0.f);
-        if (SWAP) v = mk(v.y, v.x);
+        v = transform_of(u0, r) < valid ? Mem::ldg(gin, base + off) : mk(0.f, 0.f);
+        v = swap ? mk(v.y, v.x) : v;
       } else {
-        v = Mem::lds(sm, slot(e));
-        const int k = jb & (Ns - 1);
-        if (i > 0) v = cmul(v, Mem::ldtw(d.tw + d.tw_off[S] + i * Ns + k));
+        v = Mem::lds(sm, sbase ^ slot(off));
+        if (i > 0) v = cmul(v, Mem::ldtw(tw + i * Ns + r));
       }
       if (PREC == TC_FP16) v = mk(v.x * 0.0625f, v.y * 0.0625f);  // exact 1/16 per stage
       x[s8] = v;
@@ -241,26 +304,29 @@ GB_UNROLL
   }
 
   // Outputs of group h: to shared memory, or to global memory after the last stage.
-  template <int S, bool SWAP>
+  template <int S>
   GB_HD static void scatter(const cf (&y)[8], cf* gout, cf* sm, int w, int h, int lane,
-                            int valid) {
+                            int valid, bool swap) {
     constexpr int Ns = 1 << (4 * S);
+    const int u0 = w * 32 + h * 16;
+    int base, off0;
+    out_pos<Ns>(u0, 0, 0, base, off0);
+    const int sbase = slot(base);
 GB_UNROLL
     for (int s8 = 0; s8 < 8; ++s8) {
-      const int u = w * 32 + h * 16 + tc_row(lane, s8);
-      const int g = u / BPS, jb = u - g * BPS;
-      const int o = tc_point(lane, s8);
+      const int r = tc_row(lane, s8), o = tc_point(lane, s8);
+      int b_, off;
+      out_pos<Ns>(u0, r, o, b_, off);
       cf v = y[s8];
       if (S == NST - 1) {
-        if (g >= valid) continue;
+        if (transform_of(u0, r) >= valid) continue;
         if (PREC == TC_FP16) {  // undo the 1/16 per stage: exact powers of two
           const float sc = (float)(1 << (4 * NST));
           v = mk(v.x * sc, v.y * sc);
         }
-        Mem::stg(gout, g * L + jb + o * Ns, SWAP ? mk(v.y, v.x) : v);
+        Mem::stg(gout, base + off, swap ? mk(v.y, v.x) : v);
       } else {
-        const int k = jb & (Ns - 1);
-        Mem::sts(sm, slot(g * L + (jb - k) * 16 + k + o * Ns), v);
+        Mem::sts(sm, sbase ^ slot(off), v);
       }
     }
   }

@@ -397,10 +397,8 @@ void run_tc_t(const PassDesc& d, const cf* in, cf* out) {
       for (int w = 0; w < 8; ++w)
         for (int h = 0; h < 2; ++h) {
           cf x[32][8], y[32][8];
-          for (int lane = 0; lane < 32; ++lane) {
-            if (d.conj_in) B::template gather<S, true>(x[lane], d, gin, src, w, h, lane, valid);
-            else B::template gather<S, false>(x[lane], d, gin, src, w, h, lane, valid);
-          }
+          for (int lane = 0; lane < 32; ++lane)
+            B::template gather<S>(x[lane], d, gin, src, w, h, lane, valid, d.conj_in != 0);
           float acc[4][32][4] = {};
           for (int kb = 0; kb < 2; ++kb) {
             uint32_t a[32][4], alo[32][4];
@@ -423,8 +421,7 @@ void run_tc_t(const PassDesc& d, const cf* in, cf* out) {
             for (int nb = 0; nb < 4; ++nb)
               for (int q = 0; q < 4; ++q) dl[nb][q] = acc[nb][lane][q];
             tc_outputs(dl, y[lane]);
-            if (d.conj_out) B::template scatter<S, true>(y[lane], gout, dst, w, h, lane, valid);
-            else B::template scatter<S, false>(y[lane], gout, dst, w, h, lane, valid);
+            B::template scatter<S>(y[lane], gout, dst, w, h, lane, valid, d.conj_out != 0);
           }
         }
     };
