@@ -231,9 +231,10 @@ def ours_other(args, rank: int, world: int) -> None:
     from paper_1505_08067_gb300 import gbfft, synth
 
     if args.workload == "tc":
-        items = [((4096,), 32768)]
-        desc = ("batched 1D complex64 FFT N=4096 batch=32768 (2^27 elements, 1 GiB in): FP32 path "
-                "and the tensor-core classes (FP16, BF16, split BF16x3), forward and inverse")
+        items = [((4096,), 2 ** (TOTAL_LOG - 12))]
+        desc = (f"batched 1D complex64 FFT N=4096 batch={2 ** (TOTAL_LOG - 12)} (2^{TOTAL_LOG} "
+                "elements): FP32 path and the tensor-core classes (FP16, BF16, split BF16x3), "
+                "forward and inverse")
     elif args.workload == "multipass":
         items = [((2 ** 20,), 64), ((2 ** 22,), 16), ((2 ** 24,), 4)]
         desc = ("large multi-pass 1D complex64 FFTs: N=2^20 batch 64, N=2^22 batch 16, "
@@ -249,7 +250,7 @@ def ours_other(args, rank: int, world: int) -> None:
     if args.workload == "sar":
         x = torch.from_numpy(synth.sar_frame(31).reshape(-1)).to(dev)
     elif args.workload == "tc":
-        x = torch.from_numpy(synth.buried_tone(4, 32768, 4096)[0].reshape(-1)).to(dev)
+        x = torch.from_numpy(synth.buried_tone(4, E // 4096, 4096)[0].reshape(-1)).to(dev)
     else:
         x = torch.from_numpy(synth.uniform(3, 1, E)[0]).to(dev)
     y = torch.empty_like(x)

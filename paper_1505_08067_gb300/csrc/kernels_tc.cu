@@ -85,8 +85,10 @@ __device__ __forceinline__ void tc_tile(const PassDesc& d, const cf* gin, cf* go
   if constexpr (NST > 2) tc_stage<LOGL, PREC, 2>(d, gin, gout, sm, bh, bl, w, lane, valid);
 }
 
+// Two blocks per SM (at most 128 registers a thread): the stage-0 loads of
+// one block overlap the other's MMAs.
 template <int LOGL, int PREC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 stockham_tc(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   extern __shared__ __align__(16) unsigned char smem_tc[];
   cf* sm = reinterpret_cast<cf*>(smem_tc);  // two buffers of 4096 complex
