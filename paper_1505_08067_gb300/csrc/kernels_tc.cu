@@ -110,6 +110,16 @@ stockham_tc(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc
     const int valid = rem < TPC ? (int)rem : TPC;
     const cf* gin = in + first * (1 << LOGL);
     cf* gout = out + first * (1 << LOGL);
+    // this block's next tile (32 KB) into L2 while this one is computed: its
+    // stage-0 loads then wait for L2, not DRAM
+    if (tile + gridDim.x < d.tiles) {
+      const int64_t nfirst = (tile + gridDim.x) * TPC;
+      const int64_t nrem = d.count_inner - nfirst;
+      const int64_t bytes = (nrem < TPC ? nrem : TPC) * (int64_t)(8 << LOGL);
+      const char* nb = reinterpret_cast<const char*>(in + nfirst * (1 << LOGL));
+      for (int64_t line = threadIdx.x; line * 128 < bytes; line += blockDim.x)
+        asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(nb + line * 128));
+    }
     tc_tile<LOGL, PREC>(d, gin, gout, sm, bh, bl, w, lane, valid);
   }
 }
