@@ -314,7 +314,7 @@ def ours_other(args, rank: int, world: int) -> None:
 
 
 def ours_serve(args, rank: int, world: int) -> None:
-    """Serving (BASELINE configs[4] shape): a Poisson stream of FFT jobs, sizes
+    """Serving: a Poisson stream of FFT jobs, sizes
     log-uniform over N = 2^8..2^22, batch 1..256, forward / inverse 50/50, 80%
     FP32 and 20% tensor-core class (those take N = 256 or 4096, the lengths the
     class covers), admitted under a 64 GB budget.  Offered load: algorithmic
@@ -426,7 +426,8 @@ def ours_serve(args, rank: int, world: int) -> None:
         print(json.dumps({
             "metric": METRIC, "value": flops / wall / 1e9, "unit": "GFLOP/s", "n_gpus": world,
             "higher_is_better": True, "scaling": "weak", "dtype": "f32+tc", "data": "synthetic",
-            "config": {"workload": "serving: Poisson stream of FFT jobs (configs[4] shape)",
+            "config": {"workload": "serving: Poisson stream of FFT jobs, N = 2^8..2^22, "
+                                   "batch 1..256, 64 GB budget",
                        "jobs": njobs, "offered_load_frac_of_hbm": args.load,
                        "offered_jobs_per_s": rate, "streams": args.streams,
                        "budget_bytes": 64 * 10 ** 9, "mean_job_elements": float(elems.mean()),
@@ -542,7 +543,7 @@ def ours_compress(args, rank: int, world: int) -> None:
 
 
 def ours_small(args, rank: int, world: int) -> None:
-    """BASELINE configs[0]: N = 1024, batch 64 (512 KiB), launch-latency bound.
+    """Small batch: N = 1024, batch 64 (512 KiB), launch-latency bound.
     Device time per call of fft_execute (one kernel launch) and of
     fft_execute_graph (the same launch replayed from a CUDA graph), with the
     calls back to back on one stream."""
