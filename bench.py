@@ -261,6 +261,8 @@ def ours_other(args, rank: int, world: int) -> None:
             for d in DIRS:
                 key = (shape, d, prec)
                 opts = {"epilogue": args.epilogue} if args.epilogue else {}
+                if args.variant and prec == 0:
+                    opts["variant"] = args.variant
                 opts["autotune"] = args.autotune if prec == 0 else 0
                 plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, prec,
                                         **opts)

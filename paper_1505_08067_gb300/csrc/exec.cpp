@@ -44,7 +44,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
         continue;
       }
       const bool want_staged = p.variant == 0 || p.variant == 2;
-      l.has_staged = want_staged && resolve_staged(l.d, s.generic_only, &l.staged);
+      l.has_staged = want_staged && resolve_staged(l.d, l.lmap, l.smap, s.generic_only, &l.staged);
       if (l.has_staged) {
         e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
         if (e != cudaSuccess) return e;

@@ -26,21 +26,31 @@
 // butterfly q', its elements i < r'/2 at q'*(r'/2) + i; after round 1 slots
 // [R/2, R) hold i >= r'/2 at R/2 + q'*(r'/2) + (i - r'/2).  The renaming to
 // v[q'*r' + i] is static and costs nothing once unrolled.
+//
+// Column tiles (G > 1): the same body runs G adjacent columns of a strided
+// pass side by side (transform g = thread id mod G), element a of column g at
+// slot a*G + g.  The next tile's rows are copied by one bulk copy per row
+// (G*8 bytes each), so the strided loads leave the per-thread load queue.
 #pragma once
 #include "fft_core.h"
 #include "fft_stage.h"
 
 namespace gbfft {
 
-// Compile-time shape of a staged pass; R elements (R/16 radix-16
-// butterflies) per thread.
-template <int LOGL, uint32_t SCHED, int NST, int R_ = 32>
+// Compile-time shape of a staged pass: R elements (R/16 radix-16
+// butterflies) per thread; G transforms per tile (1: one contiguous
+// transform; > 1: G adjacent columns of a strided pass); EPI the four-step
+// twiddle applied on store (0, 2 full table, 3 computed; column tiles only).
+template <int LOGL, uint32_t SCHED, int NST, int R_ = 32, int G_ = 1, int EPI_ = 0>
 struct SplitShape {
   static constexpr int kL = 1 << LOGL;
   static constexpr int kR = R_;
-  static constexpr int kT = kL / kR;              // threads per transform (= per block)
-  static constexpr int kHalf = kL / 2;            // exchange buffer holds half a transform
-  static constexpr int kHalfSlots = kHalf + (kHalf >> 4) + 1;
+  static constexpr int kG = G_;
+  static constexpr int kEpi = EPI_;
+  static constexpr int kTt = kL / kR;             // threads per transform
+  static constexpr int kT = kTt * kG;             // threads per block
+  static constexpr int kHalf = kL / 2;            // exchange buffer holds half of each transform
+  static constexpr int kHalfSlots = kHalf * kG + ((kHalf * kG) >> 4) + 1;
   static constexpr int kNst = NST;
   GB_HDC static constexpr int rlog(int s) { return (int)((SCHED >> (4 * s)) & 15u); }
   GB_HDC static constexpr int radix(int s) { return 1 << rlog(s); }
@@ -60,24 +70,44 @@ struct SplitShape {
 template <class SH, class Mem>
 struct SplitBody {
   static constexpr int R = SH::kR;
-  static constexpr int T = SH::kT;
+  static constexpr int T = SH::kTt;  // threads per transform
   static constexpr int L = SH::kL;
+  static constexpr int G = SH::kG;
 
-  GB_HD static int hslot(int a) { return a + (a >> 4); }  // a in [0, L/2)
+  // thread -> (transform g, thread t within it); G adjacent lanes share a row
+  GB_HD static void coords(int tid, int& g, int& t) {
+    if (G == 1) { g = 0; t = tid; }
+    else { t = tid / G; g = tid - t * G; }
+  }
+  // Half-buffer slot of element a (rebased into [0, L/2)) of transform g.
+  GB_HD static int hslot(int a, int g) {
+    const int s = a * G + g;
+    return s + (s >> 4);
+  }
+  // Slot of element base + d given the slot of base: for G = 1 the constant
+  // offset of fft_core.h's derivation; for G > 1 constant when d*G is a
+  // multiple of 16, else recomputed.
+  template <int D>
+  GB_HD static int hslot_plus(int sb, int base, int g, int i) {
+    if constexpr (G == 1 || (D * G) % 16 == 0) return sb + pad_off(i * D * G);
+    else return hslot(base + i * D, g);
+  }
 
   // ---------------------------------------------- stage 0 from staging -----
-  // `st` holds the whole transform, unpadded (element a at st[a]).
+  // `st` holds the tile unpadded: element a of transform g at st[a*G + g].
   template <bool SWAP>
-  GB_HD static void first(cf (&v)[R], const cf* st, int t) {
+  GB_HD static void first(cf (&v)[R], const cf* st, int tid) {
     constexpr int RR = SH::radix(0);
     constexpr int NB = R / RR;
     constexpr int stride = L / RR;
+    int g, t;
+    coords(tid, g, t);
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * T + t;
 GB_UNROLL
       for (int i = 0; i < RR; ++i) {
-        cf x = Mem::lds(st, jb + i * stride);
+        cf x = Mem::lds(st, (jb + i * stride) * G + g);
         v[q * RR + i] = SWAP ? mk(x.y, x.x) : x;
       }
       dft_radix<RR>(v + q * RR);
@@ -87,47 +117,54 @@ GB_UNROLL
   // ---------------------------------- exchange after stage S, round H -----
   // Write the butterflies of stage S whose outputs lie in half H.
   template <int S, int H>
-  GB_HD static void write_half(const cf (&v)[R], cf* x, int t) {
+  GB_HD static void write_half(const cf (&v)[R], cf* x, int tid) {
     constexpr int RR = SH::radix(S);
     constexpr int NB = R / RR;
     constexpr int Ns = SH::ns_before(S);
+    int g, t;
+    coords(tid, g, t);
 GB_UNROLL
     for (int q = H * (NB / 2); q < (H + 1) * (NB / 2); ++q) {
       const int jb = q * T + t;
       const int k = jb & (Ns - 1);
       const int base = (jb - k) * RR + k - H * (L / 2);  // rebased into the half buffer
-      const int sb = hslot(base);
+      const int sb = hslot(base, g);
 GB_UNROLL
-      for (int i = 0; i < RR; ++i) Mem::sts(x, sb + pad_off(i * Ns), v[q * RR + i]);
+      for (int i = 0; i < RR; ++i)
+        Mem::sts(x, hslot_plus<Ns>(sb, base, g, i), v[q * RR + i]);
     }
   }
 
   // Read, for stage S+1, this thread's elements that lie in half H into the
   // register slots [H*R/2, (H+1)*R/2).
   template <int S, int H>
-  GB_HD static void read_half(cf (&v)[R], const cf* x, int t) {
+  GB_HD static void read_half(cf (&v)[R], const cf* x, int tid) {
     constexpr int RR = SH::radix(S + 1);
     constexpr int NB = R / RR;
     constexpr int stride = L / RR;
     constexpr int HR = RR / 2;
+    int g, t;
+    coords(tid, g, t);
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * T + t;
-      const int sb = hslot(jb);
+      const int sb = hslot(jb, g);
 GB_UNROLL
       for (int i = 0; i < HR; ++i)
-        v[H * (R / 2) + q * HR + i] = Mem::lds(x, sb + pad_off(i * stride));
+        v[H * (R / 2) + q * HR + i] = Mem::lds(x, sb + pad_off(i * stride * G));
     }
   }
 
   // Stage S+1 after both rounds: undo the slot renaming, twiddle, DFT.
   template <int S>
-  GB_HD static void compute(cf (&v)[R], const PassDesc& d, int t) {
+  GB_HD static void compute(cf (&v)[R], const PassDesc& d, int tid) {
     constexpr int s = S + 1;
     constexpr int RR = SH::radix(s);
     constexpr int NB = R / RR;
     constexpr int HR = RR / 2;
     constexpr int Ns = SH::ns_before(s);
+    int g, t;
+    coords(tid, g, t);
     cf w[R];
 GB_UNROLL
     for (int q = 0; q < NB; ++q)
@@ -147,28 +184,24 @@ GB_UNROLL
     for (int i = 0; i < R; ++i) v[i] = w[i];
   }
 
-  // ------------ fused last stage (radix NB) + store (SH::kFuseLast) ------
-  // v[q*16 + i] holds output i of butterfly q of stage nst-2, i.e. element
-  // p + q*Ns with p = t + i*T and Ns = L/NB.  The last stage's butterfly p
-  // multiplies input q by w_L^{q p} (row q of the i-major table), takes a
-  // length-NB DFT and writes output q to p + q*Ns.
+  // ------------------------------------------------ output of element pos --
+  // Tile output base `o`; element pos of transform g at o + pos (G = 1) or
+  // o + g*out.g + pos*out.e (column tiles), times the four-step twiddle
+  // w_N^{col * pos} of column col = col0 + g when SH::kEpi != 0.
+  // `og` = o for G = 1, else this thread's column o + g*out.g; offsets in
+  // 32 bits (pos * out.e < 2^31 for every frame the planner emits).
   template <bool SWAP>
-  GB_HD static void store_fused(const cf (&v)[R], const PassDesc& d, cf* out, int t) {
-    constexpr int s = SH::kNst - 1;
-    constexpr int NB = SH::kNB;
-    constexpr int Ns = L / NB;
-    const cf* tw = d.tw + d.tw_off[s];
-GB_UNROLL
-    for (int i = 0; i < 16; ++i) {
-      const int p = t + i * T;
-      cf x[NB];
-      x[0] = v[i];
-GB_UNROLL
-      for (int q = 1; q < NB; ++q) x[q] = cmul(v[q * 16 + i], Mem::ldtw(tw + q * Ns + p));
-      dft_radix<NB>(x);
-GB_UNROLL
-      for (int q = 0; q < NB; ++q) Mem::stg(out, p + q * Ns, SWAP ? mk(x[q].y, x[q].x) : x[q]);
+  GB_HD static void put(const PassDesc& d, cf* og, int col, int pos, cf x) {
+    if constexpr (SH::kEpi == 2) {
+      x = cmul(x, Mem::ldtw(d.epi_lo + col + pos * (int)d.count_inner));  // < N <= 2^24
+    } else if constexpr (SH::kEpi == 3) {
+      x = cmul(x, Mem::rotor(col * pos, d.epi_logN));  // < N <= 2^24
     }
+    if constexpr (G == 1) Mem::stg(og, pos, SWAP ? mk(x.y, x.x) : x);
+    else Mem::stg(og, pos * (int)d.out.e, SWAP ? mk(x.y, x.x) : x);
+  }
+  GB_HD static cf* column_out(const PassDesc& d, cf* o, int g) {
+    return G == 1 ? o : o + g * d.out.g;
   }
 
   // ---------------------------- fast convolution: between the two rounds --
@@ -177,10 +210,14 @@ GB_UNROLL
   // m < R.  Each value is multiplied by h_scale * H[position] and swapped
   // (re <-> im), and round 2's stage 0 (radix 16), whose butterfly q reads
   // positions t + (q + i*NB)*T, runs on the registers: no exchange between
-  // the rounds.  `line` selects the line's filter (PassDesc::h_lines).
-  GB_HD static void conv_middle(cf (&v)[R], const PassDesc& d, int64_t line, int t) {
+  // the rounds.  Contiguous lines only; `line` (the tile) selects the filter
+  // (PassDesc::h_lines).
+  GB_HD static void conv_middle(cf (&v)[R], const PassDesc& d, int64_t line, int tid) {
     constexpr int NB = SH::kNB;
     static_assert(SH::radix(0) == 16, "round 2 starts with a radix-16 stage");
+    static_assert(G == 1, "the staged convolution runs contiguous lines");
+    int g, t;
+    coords(tid, g, t);
     cf y[R];  // y[m]: spectrum at position t + m*T
     if constexpr (SH::kFuseLast) {
       constexpr int s = SH::kNst - 1;
@@ -221,30 +258,58 @@ GB_UNROLL
     }
   }
 
+  // ------------ fused last stage (radix NB) + store (SH::kFuseLast) ------
+  // v[q*16 + i] holds output i of butterfly q of stage nst-2, i.e. element
+  // p + q*Ns with p = t + i*T and Ns = L/NB.  The last stage's butterfly p
+  // multiplies input q by w_L^{q p} (row q of the i-major table), takes a
+  // length-NB DFT and writes output q to p + q*Ns.
+  template <bool SWAP>
+  GB_HD static void store_fused(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0,
+                                int tid) {
+    constexpr int s = SH::kNst - 1;
+    constexpr int NB = SH::kNB;
+    constexpr int Ns = L / NB;
+    int g, t;
+    coords(tid, g, t);
+    cf* og = column_out(d, o, g);
+    const cf* tw = d.tw + d.tw_off[s];
+GB_UNROLL
+    for (int i = 0; i < 16; ++i) {
+      const int p = t + i * T;
+      cf x[NB];
+      x[0] = v[i];
+GB_UNROLL
+      for (int q = 1; q < NB; ++q) x[q] = cmul(v[q * 16 + i], Mem::ldtw(tw + q * Ns + p));
+      dft_radix<NB>(x);
+GB_UNROLL
+      for (int q = 0; q < NB; ++q) put<SWAP>(d, og, (int)col0 + g, p + q * Ns, x[q]);
+    }
+  }
+
   // ------------------------------------------------ last stage to global --
   template <bool SWAP>
-  GB_HD static void store(const cf (&v)[R], cf* out, int t) {
+  GB_HD static void store(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0, int tid) {
     constexpr int s = SH::kNst - 1;
     constexpr int RR = SH::radix(s);
     constexpr int NB = R / RR;
     constexpr int Ns = SH::ns_before(s);
+    int g, t;
+    coords(tid, g, t);
+    cf* og = column_out(d, o, g);
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * T + t;
 GB_UNROLL
-      for (int i = 0; i < RR; ++i) {
-        const cf x = v[q * RR + i];
-        Mem::stg(out, jb + i * Ns, SWAP ? mk(x.y, x.x) : x);
-      }
+      for (int i = 0; i < RR; ++i) put<SWAP>(d, og, (int)col0 + g, jb + i * Ns, v[q * RR + i]);
     }
   }
 };
 
-// Shared-memory bytes of a staged pass: staging (whole transform) + half
+// Shared-memory bytes of a staged pass: staging (whole tile) + half
 // exchange buffer + one 8-byte mbarrier.
 template <class SH>
 constexpr int split_smem_bytes() {
-  return SH::kL * 8 + SH::kHalfSlots * 8 + 16;
+  return SH::kL * SH::kG * 8 + SH::kHalfSlots * 8 + 16;
 }
 
 }  // namespace gbfft

@@ -49,6 +49,21 @@
   GB_STAGED(13, 0x1444, 4, 2, 32)   \
   GB_STAGED(14, 0x2444, 4, 1, 64)
 
+// Column tiles of strided passes that run the staged kernel (G adjacent
+// columns per block, rows copied by 16-byte asynchronous copies while the
+// previous tile is computed, half-size exchanges):
+//   GB_STAGED_COLS(log2 L, schedule, stages, R, G, epilogue, conv)
+// four-step first passes (epilogue 2 or 3) and the 2D column pass.  (The
+// azimuth convolution keeps the 1024-thread register kernel, measured faster.)
+#define GB_STAGED_COLS_SHAPES(GB_STAGED_COLS)      \
+  GB_STAGED_COLS(10, 0x244, 3, 32, 16, 2, 0)       \
+  GB_STAGED_COLS(10, 0x244, 3, 32, 16, 3, 0)       \
+  GB_STAGED_COLS(11, 0x344, 3, 32, 8, 2, 0)        \
+  GB_STAGED_COLS(11, 0x344, 3, 32, 8, 3, 0)        \
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 2, 0)        \
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 3, 0)        \
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 0, 0)
+
 namespace gbfft {
 
 // Does pass descriptor `d` (run with R elements per thread and these maps)
@@ -76,6 +91,19 @@ GB_HD bool staged_shape_matches(const PassDesc& d, int logL, uint32_t sched, int
   const int64_t L = int64_t(1) << d.logL;
   return d.G == 1 && d.epi == 0 && d.conv == (conv ? 1 : 0) && d.in.e == 1 && d.out.e == 1 && d.in.t == L && d.out.t == L &&
          d.logL == logL && s == sched && d.nst == nst;
+}
+
+// Is `d` (with these thread maps) a column pass the staged column kernel of
+// this shape runs?  G adjacent columns per tile, columns contiguous, row
+// strides that keep every row copy 16-byte aligned.
+GB_HD bool staged_cols_matches(const PassDesc& d, int lmap, int smap, int logL, uint32_t sched,
+                               int nst, int G, int epi, int conv) {
+  uint32_t s = 0;
+  for (int i = 0; i < d.nst && i < 8; ++i) s |= (uint32_t)d.rlog[i] << (4 * i);
+  if (d.nst > 8) return false;
+  return lmap == MAP_COLS && smap == MAP_COLS && d.G == G && d.logL == logL && s == sched &&
+         d.nst == nst && d.epi == epi && d.conv == conv && d.in.g == 1 && d.out.g == 1 &&
+         d.in.t == G && d.out.t == G && d.in.e % 2 == 0 && d.in.o % 2 == 0 && G % 2 == 0;
 }
 
 }  // namespace gbfft

@@ -41,12 +41,13 @@ struct PassLaunch {
   } staged;
 };
 
-// The staged kernel for a contiguous pass (one transform per block, TMA
-// prefetch of the next); used when the source is 16-byte aligned.
+// The staged kernel for a pass (one contiguous transform or G columns per
+// block, TMA copy of the next tile); used when the source is 16-byte aligned.
 using StagedLaunch = PassLaunch::StagedLaunchData;
 
-// Fills `s` if a staged kernel exists for this pass shape.
-bool resolve_staged(const PassDesc& d, bool generic_only, StagedLaunch* s);
+// Fills `s` if a staged kernel exists for this pass shape (contiguous
+// transforms, or column tiles of a strided pass) and thread maps.
+bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, StagedLaunch* s);
 // Opt-in shared memory and a persistent grid of (blocks per SM) x SMs.
 cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count);
 cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* in, void* out,

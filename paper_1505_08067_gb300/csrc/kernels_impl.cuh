@@ -307,14 +307,52 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 
 constexpr uint32_t kWaitPolls = 1u << 22;  // ~0.5 s of polling before giving up
 
+// Input base of a staged tile: one contiguous transform, or G adjacent
+// columns (tile = (outer, inner) as in PassDesc).
+template <class SH>
+__device__ __forceinline__ const cf* staged_src(const cf* in, const PassDesc& d, int64_t tile) {
+  if constexpr (SH::kG == 1) {
+    return in + tile * SH::kL;
+  } else {
+    const int64_t outer = tile / d.tiles_inner, inner = tile - outer * d.tiles_inner;
+    return in + outer * d.in.o + inner * d.in.t;
+  }
+}
+
+// Column tiles: every thread copies its share of the tile's L rows (G*8
+// bytes each, row a from src + a*e to st + a*G) in 16-byte asynchronous
+// copies, then has the barrier count its arrival once they have landed (the
+// barrier of a column kernel expects one arrival per thread).  Plain per-thread
+// copies: a bulk copy with different addresses in each lane would be issued
+// one lane at a time.
+template <class SH>
+__device__ __forceinline__ void copy_rows(cf* st, const cf* src, int64_t e, uint64_t* bar,
+                                          int tid) {
+  constexpr int CH = SH::kG * 8 / 16;  // 16-byte chunks per row
+  static_assert(CH >= 1 && SH::kG * 8 % 16 == 0, "rows must be whole 16-byte chunks");
+  for (int c = tid; c < SH::kL * CH; c += SH::kT) {
+    const int a = c / CH, j = c - a * CH;
+    const char* g = reinterpret_cast<const char*>(src + a * e) + 16 * j;
+    char* sdst = reinterpret_cast<char*>(st + a * SH::kG) + 16 * j;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(g)
+                 : "memory");
+  }
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
 template <class SH, int S, bool FIRST_EXCHANGE>
 __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
                                                uint64_t* bar, const cf* next_src, int tid) {
   using B = SplitBody<SH, DevMem>;
   B::template write_half<S, 0>(v, x, tid);
   __syncthreads();
-  if (FIRST_EXCHANGE && tid == 0 && next_src)  // staging is free: every thread has read it
-    tma_load(st, next_src, SH::kL * 8, bar);
+  if constexpr (SH::kG == 1) {
+    if (FIRST_EXCHANGE && tid == 0 && next_src)  // staging is free: every thread has read it
+      tma_load(st, next_src, SH::kL * 8, bar);
+  } else {
+    if (FIRST_EXCHANGE && next_src) copy_rows<SH>(st, next_src, d.in.e, bar, tid);
+  }
   B::template read_half<S, 0>(v, x, tid);
   __syncthreads();
   B::template write_half<S, 1>(v, x, tid);
@@ -335,24 +373,33 @@ __device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, 
   if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
 }
 
-// One contiguous transform per block, persistent over tiles; the next
-// transform streams into shared memory by TMA while this one is computed.
-// CONV: fast convolution of each line (forward stages, filter, forward
-// stages on swapped data; see SplitBody::conv_middle).
+// One tile per block (a contiguous transform, or G adjacent columns of a
+// strided pass), persistent over tiles; the next tile streams into shared
+// memory by bulk copies while this one is computed.  CONV: fast convolution
+// of each line (forward stages, filter, forward stages on swapped data; see
+// SplitBody::conv_middle).
 template <class SH, int MINB, bool CONV = false>
 __global__ void __launch_bounds__(SH::kT, MINB)
 stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   extern __shared__ __align__(128) unsigned char smem_staged[];
   cf* st = reinterpret_cast<cf*>(smem_staged);
-  cf* x = st + SH::kL;
+  cf* x = st + SH::kL * SH::kG;
   uint64_t* bar = reinterpret_cast<uint64_t*>(x + SH::kHalfSlots);
   using B = SplitBody<SH, DevMem>;
   const int tid = threadIdx.x;
   const int64_t step = gridDim.x;
   int64_t tile = blockIdx.x;
-  if (tid == 0) mbar_init(bar, 1);
+  // one arrival (the expect_tx of the bulk copy) for a contiguous transform,
+  // one per thread (its row copies) for a column tile
+  if (tid == 0) mbar_init(bar, SH::kG == 1 ? 1 : SH::kT);
   __syncthreads();
-  if (tid == 0 && tile < d.tiles) tma_load(st, in + tile * SH::kL, SH::kL * 8, bar);
+  if (tile < d.tiles) {  // uniform over the block
+    if constexpr (SH::kG == 1) {
+      if (tid == 0) tma_load(st, in + tile * SH::kL, SH::kL * 8, bar);
+    } else {
+      copy_rows<SH>(st, staged_src<SH>(in, d, tile), d.in.e, bar, tid);
+    }
+  }
   uint32_t parity = 0;
   for (; tile < d.tiles; tile += step) {
     const bool ok = mbar_wait(bar, parity, kWaitPolls);
@@ -364,23 +411,32 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
       return;
     }
     parity ^= 1u;
-    const cf* next = tile + step < d.tiles ? in + (tile + step) * SH::kL : nullptr;
+    const cf* next = tile + step < d.tiles ? staged_src<SH>(in, d, tile + step) : nullptr;
     cf v[SH::kR];
     if (d.conj_in) B::template first<true>(v, st, tid);
     else B::template first<false>(v, st, tid);
     split_round<SH>(v, d, x, st, bar, next, tid);
-    cf* o = out + tile * SH::kL;
-    if constexpr (CONV) {
-      B::conv_middle(v, d, tile, tid);
-      split_round<SH>(v, d, x, st, bar, nullptr, tid);
-      if constexpr (SH::kFuseLast) B::template store_fused<true>(v, d, o, tid);
-      else B::template store<true>(v, o, tid);
-    } else if constexpr (SH::kFuseLast) {
-      if (d.conj_out) B::template store_fused<true>(v, d, o, tid);
-      else B::template store_fused<false>(v, d, o, tid);
+    cf* o;
+    int64_t col0;  // G == 1: the line (tile); else the first column of the tile
+    if constexpr (SH::kG == 1) {
+      o = out + tile * SH::kL;
+      col0 = tile;
     } else {
-      if (d.conj_out) B::template store<true>(v, o, tid);
-      else B::template store<false>(v, o, tid);
+      const int64_t outer = tile / d.tiles_inner, inner = tile - outer * d.tiles_inner;
+      o = out + outer * d.out.o + inner * d.out.t;
+      col0 = inner * SH::kG;
+    }
+    if constexpr (CONV) {
+      B::conv_middle(v, d, col0, tid);
+      split_round<SH>(v, d, x, st, bar, nullptr, tid);
+      if constexpr (SH::kFuseLast) B::template store_fused<true>(v, d, o, col0, tid);
+      else B::template store<true>(v, d, o, col0, tid);
+    } else if constexpr (SH::kFuseLast) {
+      if (d.conj_out) B::template store_fused<true>(v, d, o, col0, tid);
+      else B::template store_fused<false>(v, d, o, col0, tid);
+    } else {
+      if (d.conj_out) B::template store<true>(v, d, o, col0, tid);
+      else B::template store<false>(v, d, o, col0, tid);
     }
   }
 }
@@ -438,5 +494,6 @@ const void* resolve_contig_shape(int R, int lmap, int smap, const PassDesc& d);
 const void* resolve_fourstep_shape(int R, int lmap, int smap, const PassDesc& d);
 bool resolve_staged_shape(const PassDesc& d, StagedLaunch* s);
 bool resolve_conv_staged_shape(const PassDesc& d, StagedLaunch* s);
+bool resolve_staged_cols_shape(const PassDesc& d, int lmap, int smap, StagedLaunch* s);
 
 }  // namespace gbfft

@@ -13,4 +13,19 @@ const void* resolve_fourstep_shape(int R, int lmap, int smap, const PassDesc& d)
   return nullptr;
 }
 
+// Staged column tiles (see GB_STAGED_COLS_SHAPES).
+bool resolve_staged_cols_shape(const PassDesc& d, int lmap, int smap, StagedLaunch* s) {
+#define GB_STAGED_COLS(LOGL, SCHED, NST, RR, G, EPI, CONV)                         \
+  if (staged_cols_matches(d, lmap, smap, LOGL, SCHED, NST, G, EPI, CONV)) {         \
+    using SH = SplitShape<LOGL, SCHED, NST, RR, G, EPI>;                           \
+    s->fn = (const void*)staged_fn<SH, 1, false>();                                \
+    s->block = SH::kT;                                                             \
+    s->smem = split_smem_bytes<SH>();                                              \
+    return true;                                                                   \
+  }
+  GB_STAGED_COLS_SHAPES(GB_STAGED_COLS)
+#undef GB_STAGED_COLS
+  return false;
+}
+
 }  // namespace gbfft

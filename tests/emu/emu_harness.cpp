@@ -258,17 +258,31 @@ template <class SH, bool CONV = false>
 void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
   using B = SplitBody<SH, CheckMem>;
   constexpr int R = SH::kR;
-  std::vector<cf> st(SH::kL), x(SH::kHalfSlots);
+  constexpr int TILE = SH::kL * SH::kG;
+  std::vector<cf> st(TILE), x(SH::kHalfSlots);
   std::vector<int64_t> ep(x.size(), -1), wr(x.size(), -1);
   g.slot_epoch = &ep;
   g.slot_write = &wr;
   g.smem_len = SH::kHalfSlots;
   g.staging = st.data();
-  g.staging_len = SH::kL;
+  g.staging_len = TILE;
   std::vector<std::array<cf, R>> V(SH::kT);
   auto reg = [&](int t) -> cf (&)[R] { return *reinterpret_cast<cf(*)[R]>(V[t].data()); };
   for (int64_t tile = 0; tile < d.tiles; ++tile) {
-    for (int a = 0; a < SH::kL; ++a) st[a] = CheckMem::ldg(in, tile * SH::kL + a);
+    // the bulk copies: one contiguous transform, or one G-column segment per row
+    int64_t src, dst, col0;
+    if constexpr (SH::kG == 1) {
+      src = dst = tile * SH::kL;
+      col0 = tile;
+    } else {
+      const int64_t outer = tile / d.tiles_inner, inner = tile - outer * d.tiles_inner;
+      src = outer * d.in.o + inner * d.in.t;
+      dst = outer * d.out.o + inner * d.out.t;
+      col0 = inner * SH::kG;
+    }
+    for (int a = 0; a < SH::kL; ++a)
+      for (int c = 0; c < SH::kG; ++c)
+        st[a * SH::kG + c] = CheckMem::ldg(in, src + (SH::kG == 1 ? a : c + a * d.in.e));
     for (int t = 0; t < SH::kT; ++t) {
       if (d.conj_in) B::template first<true>(reg(t), st.data(), t);
       else B::template first<false>(reg(t), st.data(), t);
@@ -291,26 +305,39 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       if constexpr (SH::kExchanges > 2) exchange(std::integral_constant<int, 2>());
     };
     round();
+    cf* o = out + dst;
     if constexpr (CONV) {
-      for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, tile, t);
+      for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, col0, t);
       round();
       for (int t = 0; t < SH::kT; ++t) {
-        if constexpr (SH::kFuseLast) B::template store_fused<true>(reg(t), d, out + tile * SH::kL, t);
-        else B::template store<true>(reg(t), out + tile * SH::kL, t);
+        if constexpr (SH::kFuseLast) B::template store_fused<true>(reg(t), d, o, col0, t);
+        else B::template store<true>(reg(t), d, o, col0, t);
       }
       continue;
     }
     for (int t = 0; t < SH::kT; ++t) {
       if constexpr (SH::kFuseLast) {
-        if (d.conj_out) B::template store_fused<true>(reg(t), d, out + tile * SH::kL, t);
-        else B::template store_fused<false>(reg(t), d, out + tile * SH::kL, t);
+        if (d.conj_out) B::template store_fused<true>(reg(t), d, o, col0, t);
+        else B::template store_fused<false>(reg(t), d, o, col0, t);
       } else {
-        if (d.conj_out) B::template store<true>(reg(t), out + tile * SH::kL, t);
-        else B::template store<false>(reg(t), out + tile * SH::kL, t);
+        if (d.conj_out) B::template store<true>(reg(t), d, o, col0, t);
+        else B::template store<false>(reg(t), d, o, col0, t);
       }
     }
   }
   g.staging = nullptr;
+}
+
+// Column tiles of strided passes (GB_STAGED_COLS_SHAPES).
+bool run_staged_cols(int lmap, int smap, const PassDesc& d, const cf* in, cf* out) {
+#define GB_STAGED_COLS(LOGL, SCHED, NST, RR, G, EPI, CONV)                                  \
+  if (staged_cols_matches(d, lmap, smap, LOGL, SCHED, NST, G, EPI, CONV)) {                  \
+    run_staged_t<SplitShape<LOGL, SCHED, NST, RR, G, EPI>, CONV != 0>(d, in, out);           \
+    return true;                                                                          \
+  }
+  GB_STAGED_COLS_SHAPES(GB_STAGED_COLS)
+#undef GB_STAGED_COLS
+  return false;
 }
 
 bool run_conv_staged(const PassDesc& d, const cf* in, cf* out) {
@@ -519,13 +546,17 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
       g.h = d.h;
       g.h_len = filter_len[p.h_dim];
       const bool want_staged = p.variant == 0 || p.variant == 2;
-      if (specialised && !s.generic_only && want_staged && run_conv_staged(d, src, dst))
+      if (specialised && !s.generic_only && want_staged && p.lmap == MAP_ROWS &&
+          run_conv_staged(d, src, dst))
         ++g.staged_passes;
       else if (specialised && !s.generic_only && run_conv_special(p.R, p.lmap, d, src, dst)) ++g.special_passes;
       else if (p.lmap == MAP_ROWS) run_conv_maps<0>(p.R, d, src, dst);
       else run_conv_maps<1>(p.R, d, src, dst);
     } else if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);
-    else if (specialised && !s.generic_only && run_staged(d, src, dst)) ++g.staged_passes;
+    else if (specialised && !s.generic_only && (p.variant == 0 || p.variant == 2) &&
+             (p.lmap == MAP_COLS ? run_staged_cols(p.lmap, p.smap, d, src, dst)
+                                 : (p.lmap == MAP_ROWS && p.smap == MAP_ROWS && run_staged(d, src, dst))))
+      ++g.staged_passes;
     else if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
     else if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);
     else if (p.lmap == MAP_COLS && p.smap == MAP_COLS) run_maps<1, 1>(p.R, d, src, dst);

@@ -183,10 +183,44 @@ def test_conv_frames(oracle, shape, per_line):
 
 
 def test_conv_azimuth_shape(oracle):
-    """4096-point columns run the compile-time column shape (4 per tile)."""
-    _check_conv(oracle, (4096, 8), 1, (True, False), expect_special=1)
+    """4096-point columns (4 per tile) run the compile-time register
+    convolution kernel."""
+    st = {}
+    _check_conv(oracle, (4096, 8), 2, (True, False), stats=st, expect_special=1)
+    assert st["staged_passes"] == 0
 
 
 @pytest.mark.parametrize("radix,tile", [(4, 0), (8, 2), (2, 4), (16, 8)])
 def test_conv_forced_radix_and_tile(oracle, radix, tile):
     _check_conv(oracle, (1024,), 7, (True, False), radix=radix, tile=tile)
+
+
+@pytest.mark.parametrize("logn,split,epilogue", [(15, 10, 2), (15, 10, 3), (16, 11, 2), (16, 11, 3),
+                                                 (17, 12, 2), (17, 12, 3)])
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_staged_column_first_pass(oracle, logn, split, epilogue, direction):
+    """Four-step first passes of 1024 / 2048 / 4096 points run the staged
+    column kernel (rows copied in bulk, G = 16 / 8 / 4 columns per tile, the
+    four-step twiddle on store); the register kernel must agree."""
+    n = 2 ** logn
+    x = synth.uniform(40 + logn, 3, n)
+    ref = oracle.fft(x, direction)
+    for variant, staged in ((0, 1), (1, 0)):
+        st = {}
+        y, nerr, msg = emu.run(x, (n,), direction=direction, stats=st, split_log2=split,
+                               epilogue=epilogue, variant=variant)
+        assert nerr == 0, msg
+        assert st["staged_passes"] == staged
+        assert np.max(oracle.rel_l2(y, ref)) <= 1e-6 * logn
+
+
+@pytest.mark.parametrize("shape", [(4096, 8), (4096, 16)])
+def test_staged_column_2d(oracle, shape):
+    st = {}
+    x = synth.uniform(77, 2, shape[0] * shape[1]).reshape(2, *shape)
+    for d in (-1, 1):
+        y, nerr, msg = emu.run(x, shape, direction=d, stats=st)
+        assert nerr == 0, msg
+        assert st["staged_passes"] == 1
+        err = oracle.rel_l2(y.reshape(2, -1), oracle.fft2d(x, d).reshape(2, -1))
+        assert np.max(err) <= 1e-6 * np.log2(x[0].size)
