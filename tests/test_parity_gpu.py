@@ -274,6 +274,33 @@ def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
         assert np.max(oracle.rel_l2(y, oracle.fft(x_np))) <= _tol(n), shift
 
 
+@pytest.mark.parametrize("shape,batch,opts", [((4096, 64), 2, {}), ((2 ** 20,), 2, {"split_log2": 10}),
+                                              ((2 ** 22,), 1, {"split_log2": 11, "epilogue": 3}),
+                                              ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 3})])
+def test_staged_columns_and_unaligned_fallback(gb, oracle, shape, batch, opts):
+    """Column passes (2D, four-step first passes with G = 16 / 8 / 4 columns)
+    run the staged column kernel (variant 2) from a 16-byte-aligned source and
+    the register kernel from an 8-byte-aligned one; both match the oracle."""
+    n = int(np.prod(shape))
+    x_np = synth.uniform(9400 + int(np.log2(n)), batch, n)
+    buf = torch.zeros(batch * n + 1, dtype=torch.complex64, device="cuda")
+    dims = shape if len(shape) > 1 else shape[0]
+    for shift in (0, 1):
+        xin = buf[shift:shift + batch * n]
+        xin.copy_(torch.from_numpy(x_np.reshape(-1)))
+        out = torch.empty(batch * n, dtype=torch.complex64, device="cuda")
+        with gb.Plan(dims, batch, variant=2, **opts) as p:
+            st = torch.cuda.current_stream().cuda_stream
+            gb.fft_execute(p.handle, xin.data_ptr(), out.data_ptr(), st)
+            gb.fft_plan_sync_status(p.handle, st)
+        y = out.cpu().numpy().reshape(batch, n)
+        if len(shape) == 1:
+            ref = oracle.fft_select(x_np, np.arange(batch), -1)
+        else:
+            ref = oracle.fft2d(x_np.reshape((batch,) + shape)).reshape(batch, n)
+        assert np.max(oracle.rel_l2(y, ref)) <= _tol(n), (shape, shift)
+
+
 @pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("logn", [8, 11, 12, 13, 14])
 def test_kernel_variants(gb, oracle, variant, logn):
