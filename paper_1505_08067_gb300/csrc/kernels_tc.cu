@@ -57,12 +57,12 @@ __device__ __forceinline__ void tc_group(const cf (&x)[8], const uint32_t (&bh)[
 // the last store (one copy of the tile code).
 template <int LOGL, int PREC, int S>
 __device__ __forceinline__ void tc_stage(const PassDesc& d, const cf* gin, cf* gout, cf* sm,
-                                         const uint32_t (&bh)[2][4][2],
+                                         const cf* stg, const uint32_t (&bh)[2][4][2],
                                          const uint32_t (&bl)[2][4][2], int w, int lane,
                                          int valid) {
   constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
   using B = TcBody<LOGL, P, DevMem>;
-  const cf* src = sm + ((S + 1) & 1) * 4096;  // written by stage S-1
+  const cf* src = S == 0 ? stg : sm + ((S + 1) & 1) * 4096;  // staging, or stage S-1's output
   cf* dst = sm + (S & 1) * 4096;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -74,27 +74,47 @@ __device__ __forceinline__ void tc_stage(const PassDesc& d, const cf* gin, cf* g
   __syncthreads();
 }
 
-template <int LOGL, int PREC>
-__device__ __forceinline__ void tc_tile(const PassDesc& d, const cf* gin, cf* gout, cf* sm,
-                                        const uint32_t (&bh)[2][4][2],
-                                        const uint32_t (&bl)[2][4][2], int w, int lane,
-                                        int valid) {
-  constexpr int NST = LOGL / 4;
-  tc_stage<LOGL, PREC, 0>(d, gin, gout, sm, bh, bl, w, lane, valid);
-  if constexpr (NST > 1) tc_stage<LOGL, PREC, 1>(d, gin, gout, sm, bh, bl, w, lane, valid);
-  if constexpr (NST > 2) tc_stage<LOGL, PREC, 2>(d, gin, gout, sm, bh, bl, w, lane, valid);
+// Copy the valid transforms of tile `tile` into the staging buffer (one
+// thread): bulk copies of kChunk elements, each to its padded place.
+template <class B>
+__device__ __forceinline__ void tc_stage_in(const cf* in, const PassDesc& d, int64_t tile,
+                                            cf* stg, uint64_t* bar) {
+  constexpr int TPC = 4096 / B::L;
+  const int64_t first = tile * TPC;
+  const int64_t rem = d.count_inner - first;
+  const int nv = rem < TPC ? (int)rem : TPC;
+  const int chunks = nv * B::L / B::kChunk;
+  const uint32_t bytes = (uint32_t)(nv * B::L * 8);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  const cf* src = in + first * B::L;
+  for (int c = 0; c < chunks; ++c)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(stg + c * (B::kChunk + 2))),
+        "l"(src + c * B::kChunk), "r"((uint32_t)(B::kChunk * 8)), "r"(smem_u32(bar))
+        : "memory");
 }
 
-// Two blocks per SM (at most 128 registers a thread): the stage-0 loads of
-// one block overlap the other's MMAs.
+// Two blocks per SM (at most 128 registers a thread).  Persistent: each block
+// builds the DFT-matrix fragments once and copies its next tile into a padded
+// staging buffer (bulk copies, mbarrier with a bounded wait) while the
+// current one is computed; a source that is not 16-byte aligned is read from
+// global memory instead.
 template <int LOGL, int PREC>
 __global__ void __launch_bounds__(256, 2)
 stockham_tc(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
+  constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
+  using B = TcBody<LOGL, P, DevMem>;
   extern __shared__ __align__(16) unsigned char smem_tc[];
   cf* sm = reinterpret_cast<cf*>(smem_tc);  // two buffers of 4096 complex
-  constexpr int P = PREC == TC_BF16X3 ? TC_BF16 : PREC;
+  cf* stg = sm + 8192;                      // staging, B::kStageSlots complex
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stg + B::kStageSlots);
   constexpr int TPC = 4096 >> LOGL;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const bool staged = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
   uint32_t bh[2][4][2], bl[2][4][2];
 #pragma unroll
   for (int kb = 0; kb < 2; ++kb)
@@ -104,23 +124,34 @@ stockham_tc(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc
       if (PREC == TC_BF16X3) tc_b_frag<P>(lane, kb, nb, 1, bl[kb][nb][0], bl[kb][nb][1]);
       else bl[kb][nb][0] = bl[kb][nb][1] = 0;
     }
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (staged && tid == 0 && blockIdx.x < d.tiles) tc_stage_in<B>(in, d, blockIdx.x, stg, bar);
+  uint32_t parity = 0;
   for (int64_t tile = blockIdx.x; tile < d.tiles; tile += gridDim.x) {
     const int64_t first = tile * TPC;
     const int64_t rem = d.count_inner - first;
     const int valid = rem < TPC ? (int)rem : TPC;
     const cf* gin = in + first * (1 << LOGL);
     cf* gout = out + first * (1 << LOGL);
-    // this block's next tile (32 KB) into L2 while this one is computed: its
-    // stage-0 loads then wait for L2, not DRAM
-    if (tile + gridDim.x < d.tiles) {
-      const int64_t nfirst = (tile + gridDim.x) * TPC;
-      const int64_t nrem = d.count_inner - nfirst;
-      const int64_t bytes = (nrem < TPC ? nrem : TPC) * (int64_t)(8 << LOGL);
-      const char* nb = reinterpret_cast<const char*>(in + nfirst * (1 << LOGL));
-      for (int64_t line = threadIdx.x; line * 128 < bytes; line += blockDim.x)
-        asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(nb + line * 128));
+    if (staged) {
+      const bool ok = mbar_wait(bar, parity, kWaitPolls);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicExch(d.status, 1);
+          mbar_wait(bar, parity, kWaitPolls);  // let the copy in flight land before leaving
+        }
+        return;
+      }
+      parity ^= 1u;
     }
-    tc_tile<LOGL, PREC>(d, gin, gout, sm, bh, bl, w, lane, valid);
+    tc_stage<LOGL, PREC, 0>(d, gin, gout, sm, staged ? stg : nullptr, bh, bl, w, lane, valid);
+    // every thread has read the staging buffer: start the next tile's copy
+    if (staged && tid == 0 && tile + gridDim.x < d.tiles)
+      tc_stage_in<B>(in, d, tile + gridDim.x, stg, bar);
+    constexpr int NST = LOGL / 4;
+    if constexpr (NST > 1) tc_stage<LOGL, PREC, 1>(d, gin, gout, sm, stg, bh, bl, w, lane, valid);
+    if constexpr (NST > 2) tc_stage<LOGL, PREC, 2>(d, gin, gout, sm, stg, bh, bl, w, lane, valid);
   }
 }
 

@@ -55,11 +55,15 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
     p.grid = 0;
     return true;
   }
-  if (p.tc_prec) {  // fixed shape: 8 warps, two shared buffers of 4096 complex
+  if (p.tc_prec) {
+    // fixed shape: 8 warps, two shared buffers of 4096 complex, a staging
+    // buffer for the next tile (chunks of 2^8 or 2^4 elements each followed
+    // by a 2-slot gap) and its mbarrier
+    const int chunk_log = p.logL >= 12 ? 8 : 4;
     p.block = 256;
     p.pitch = 0;
-    p.smem_elems = 2 * 4096;
-    p.smem = (size_t)p.smem_elems * 8;
+    p.smem_elems = 2 * 4096 + 4096 + 2 * (4096 >> chunk_log);
+    p.smem = (size_t)p.smem_elems * 8 + 16;
     if (p.smem > (size_t)caps.smem_optin) {
       err = "tensor-core tile does not fit in shared memory";
       return false;

@@ -237,6 +237,16 @@ struct TcBody {
   // conflict-free).
   GB_HD static int slot(int e) { return e ^ (((e >> 4) ^ (e >> 7)) & 15); }
 
+  // Staging buffer (the next tile, copied in by bulk copies of kChunk
+  // elements, each followed by a 2-slot gap): element e at pslot(e).  The gap
+  // shifts the banks of the stage-0 loads, element u0 + r + i*L/16, by 2 per
+  // chunk, which separates the 4 lanes that share r within a half warp.
+  // Additive: pslot(base + off) = pslot(base) + pslot(off) for disjoint bits.
+  static constexpr int kChunkLog = LOGL >= 12 ? 8 : 4;
+  static constexpr int kChunk = 1 << kChunkLog;
+  static constexpr int kStageSlots = 4096 + 2 * (4096 >> kChunkLog);
+  GB_HD static int pslot(int e) { return e + 2 * (e >> kChunkLog); }
+
   // Group base and lane offset of input i of the lane's row r (0..15) of the
   // group starting at butterfly u0, for a stage with Ns = 16^S.
   GB_HD static void in_pos(int u0, int r, int i, int& base, int& off) {
@@ -291,8 +301,11 @@ GB_UNROLL
       int b_, off;
       in_pos(u0, r, i, b_, off);
       cf v;
-      if (S == 0) {
-        v = transform_of(u0, r) < valid ? Mem::ldg(gin, base + off) : mk(0.f, 0.f);
+      if (S == 0) {  // from the staging buffer `sm` (padded), or global memory if null
+        if (transform_of(u0, r) < valid)
+          v = sm ? Mem::lds(sm, pslot(base) + pslot(off)) : Mem::ldg(gin, base + off);
+        else
+          v = mk(0.f, 0.f);
         v = swap ? mk(v.y, v.x) : v;
       } else {
         v = Mem::lds(sm, sbase ^ slot(off));

@@ -89,13 +89,13 @@ struct CheckMem {
     return *p;
   }
   static cf lds(const cf* s, int i) {
-    if (g.smem_base && s != g.smem_base) {  // second TC buffer
-      i += (int)(s - g.smem_base);
-      s = g.smem_base;
-    }
     if (g.staging && s == g.staging) {
       if (i < 0 || i >= g.staging_len) { err("staging load out of bounds", i); return mk(0, 0); }
       return s[i];
+    }
+    if (g.smem_base && s != g.smem_base) {  // second TC buffer
+      i += (int)(s - g.smem_base);
+      s = g.smem_base;
     }
     if (i < 0 || i >= g.smem_len) { err("shared load out of bounds", i); return mk(0, 0); }
     const int64_t want = g.split_epochs ? g.read_epoch : g.epoch;
@@ -409,17 +409,24 @@ void run_tc_t(const PassDesc& d, const cf* in, cf* out) {
         tc_b_frag<P>(lane, kb, nb, 0, bh[lane][kb][nb][0], bh[lane][kb][nb][1]);
         tc_b_frag<P>(lane, kb, nb, 1, bl[lane][kb][nb][0], bl[lane][kb][nb][1]);
       }
+  // the kernel's staging buffer: the tile's valid transforms in chunks of
+  // kChunk elements, each followed by a 2-slot gap (the bulk copies)
+  std::vector<cf> stg(B::kStageSlots);
   int64_t phase = 0;
   for (int64_t tile = 0; tile < d.tiles; ++tile) {
     const int64_t first = tile * TPC;
     const int valid = (int)std::min<int64_t>(TPC, d.count_inner - first);
     const cf* gin = in + first * (1 << LOGL);
     cf* gout = out + first * (1 << LOGL);
+    for (int e = 0; e < valid * (1 << LOGL); ++e)
+      stg[B::pslot(e)] = CheckMem::ldg(in, first * (1 << LOGL) + e);
+    g.staging = stg.data();
+    g.staging_len = B::kStageSlots;
     auto stage = [&](auto S_) {
       constexpr int S = decltype(S_)::value;
       g.read_epoch = phase;
       g.write_epoch = ++phase;
-      const cf* src = sm.data() + ((S + 1) & 1) * 4096;
+      const cf* src = S == 0 ? stg.data() : sm.data() + ((S + 1) & 1) * 4096;
       cf* dst = sm.data() + (S & 1) * 4096;
       for (int w = 0; w < 8; ++w)
         for (int h = 0; h < 2; ++h) {
@@ -457,6 +464,7 @@ void run_tc_t(const PassDesc& d, const cf* in, cf* out) {
     if constexpr (NST > 2) stage(std::integral_constant<int, 2>());
   }
   g.smem_base = nullptr;
+  g.staging = nullptr;
   g.split_epochs = false;
 }
 
