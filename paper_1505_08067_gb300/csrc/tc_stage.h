@@ -232,10 +232,17 @@ struct TcBody {
   static constexpr int BPS = L / 16;    // butterflies per transform and stage
   static constexpr int TPC = 4096 / L;  // transforms per tile
 
-  // Shared-memory slot of tile element e: a bijective XOR swizzle of the low
-  // four bits (GF(2)-linear; keeps the fragment-shaped accesses near
-  // conflict-free).
-  GB_HD static int slot(int e) { return e ^ (((e >> 4) ^ (e >> 7)) & 15); }
+  // Shared-memory slot of tile element e: the low four bits (the bank pair
+  // of an 8-byte access) XORed with a linear function of higher bits, so the
+  // map is bijective and GF(2)-linear.  Within a half warp the fragment-shaped
+  // accesses vary bits {0,1} and {9,10} (stage inputs i*L/16 + r), {1,2} and
+  // {4,5} (stage-0 outputs 16 r + o) or {0,1} and {5,6} (stage-1 outputs
+  // r + 16 o); the function sends bits 9,10 to 2,3, bits 4,5 to 0,3 and
+  // bits 5,6 to 3,2, which makes every one of these patterns conflict-free
+  // (for L = 256 the same three patterns appear).
+  GB_HD static int slot(int e) {
+    return e ^ (((e >> 4) & 5) ^ ((e >> 2) & 8) ^ ((e >> 7) & 12));
+  }
 
   // Staging buffer (the next tile, copied in by bulk copies of kChunk
   // elements, each followed by a 2-slot gap): element e at pslot(e).  The gap
