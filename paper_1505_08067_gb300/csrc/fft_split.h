@@ -41,12 +41,22 @@ namespace gbfft {
 // butterflies) per thread; G transforms per tile (1: one contiguous
 // transform; > 1: G adjacent columns of a strided pass); EPI the four-step
 // twiddle applied on store (0, 2 full table, 3 computed; column tiles only).
-template <int LOGL, uint32_t SCHED, int NST, int R_ = 32, int G_ = 1, int EPI_ = 0>
+//   ROWS_IN: the tile's input is G contiguous rows (the transposing pass of a
+//   four-step plan), staged one row per bulk copy with a pitch of L + kRowPad;
+//   otherwise G adjacent columns staged interleaved (element a of column g at
+//   a*G + g).  The output side is the same for both: G columns.
+template <int LOGL, uint32_t SCHED, int NST, int R_ = 32, int G_ = 1, int EPI_ = 0,
+          bool ROWS_IN = false>
 struct SplitShape {
   static constexpr int kL = 1 << LOGL;
   static constexpr int kR = R_;
   static constexpr int kG = G_;
   static constexpr int kEpi = EPI_;
+  static constexpr bool kRowsIn = ROWS_IN;
+  // row pitch padding of the staged rows: the stage-0 loads of a half warp
+  // (G columns x 16/G threads) then hit distinct bank pairs (2-way for G = 16)
+  static constexpr int kRowPad = ROWS_IN ? (16 / G_ > 2 ? 16 / G_ : 2) : 0;
+  static constexpr int kStageElems = ROWS_IN ? G_ * ((1 << LOGL) + kRowPad) : (1 << LOGL) * G_;
   static constexpr int kTt = kL / kR;             // threads per transform
   static constexpr int kT = kTt * kG;             // threads per block
   static constexpr int kHalf = kL / 2;            // exchange buffer holds half of each transform
@@ -94,7 +104,8 @@ struct SplitBody {
   }
 
   // ---------------------------------------------- stage 0 from staging -----
-  // `st` holds the tile unpadded: element a of transform g at st[a*G + g].
+  // `st` holds the tile: element a of transform g at st[a*G + g] (columns),
+  // or at st[g*(L + kRowPad) + a] (rows).
   template <bool SWAP>
   GB_HD static void first(cf (&v)[R], const cf* st, int tid) {
     constexpr int RR = SH::radix(0);
@@ -107,7 +118,8 @@ GB_UNROLL
       const int jb = q * T + t;
 GB_UNROLL
       for (int i = 0; i < RR; ++i) {
-        cf x = Mem::lds(st, (jb + i * stride) * G + g);
+        const int a = jb + i * stride;
+        cf x = Mem::lds(st, SH::kRowsIn ? g * (L + SH::kRowPad) + a : a * G + g);
         v[q * RR + i] = SWAP ? mk(x.y, x.x) : x;
       }
       dft_radix<RR>(v + q * RR);
@@ -309,7 +321,7 @@ GB_UNROLL
 // exchange buffer + one 8-byte mbarrier.
 template <class SH>
 constexpr int split_smem_bytes() {
-  return SH::kL * SH::kG * 8 + SH::kHalfSlots * 8 + 16;
+  return SH::kStageElems * 8 + SH::kHalfSlots * 8 + 16;
 }
 
 }  // namespace gbfft

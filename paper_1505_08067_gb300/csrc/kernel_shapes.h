@@ -64,6 +64,14 @@
   GB_STAGED_COLS(12, 0x444, 3, 32, 4, 3, 0)        \
   GB_STAGED_COLS(12, 0x444, 3, 32, 4, 0, 0)
 
+// Transposing passes (G contiguous rows in, G columns out: the second pass of
+// a four-step plan) that run the staged kernel:
+//   GB_STAGED_TRANS(log2 L, schedule, stages, R, G)
+#define GB_STAGED_TRANS_SHAPES(GB_STAGED_TRANS) \
+  GB_STAGED_TRANS(10, 0x244, 3, 32, 16)         \
+  GB_STAGED_TRANS(11, 0x344, 3, 32, 8)          \
+  GB_STAGED_TRANS(12, 0x444, 3, 32, 4)
+
 namespace gbfft {
 
 // Does pass descriptor `d` (run with R elements per thread and these maps)
@@ -104,6 +112,19 @@ GB_HD bool staged_cols_matches(const PassDesc& d, int lmap, int smap, int logL, 
   return lmap == MAP_COLS && smap == MAP_COLS && d.G == G && d.logL == logL && s == sched &&
          d.nst == nst && d.epi == epi && d.conv == conv && d.in.g == 1 && d.out.g == 1 &&
          d.in.t == G && d.out.t == G && d.in.e % 2 == 0 && d.in.o % 2 == 0 && G % 2 == 0;
+}
+
+// Is `d` a transposing pass (G contiguous rows of L in, written as G columns)
+// the staged kernel of this shape runs?
+GB_HD bool staged_trans_matches(const PassDesc& d, int lmap, int smap, int logL, uint32_t sched,
+                                int nst, int G) {
+  uint32_t s = 0;
+  for (int i = 0; i < d.nst && i < 8; ++i) s |= (uint32_t)d.rlog[i] << (4 * i);
+  if (d.nst > 8) return false;
+  const int64_t L = int64_t(1) << logL;
+  return lmap == MAP_ROWS && smap == MAP_COLS && d.G == G && d.logL == logL && s == sched &&
+         d.nst == nst && d.epi == 0 && d.conv == 0 && d.in.e == 1 && d.in.g == L &&
+         d.in.t == G * L && d.out.g == 1 && d.out.t == G && d.in.o % 2 == 0 && G % 2 == 0;
 }
 
 }  // namespace gbfft

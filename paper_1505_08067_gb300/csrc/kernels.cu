@@ -74,6 +74,7 @@ const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool ge
 bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, StagedLaunch* s) {
   if (generic_only) return false;
   if (lmap == MAP_COLS) return !d.conv && resolve_staged_cols_shape(d, lmap, smap, s);
+  if (lmap == MAP_ROWS && smap == MAP_COLS) return !d.conv && resolve_staged_trans_shape(d, lmap, smap, s);
   if (lmap != MAP_ROWS || smap != MAP_ROWS) return false;
   return d.conv ? resolve_conv_staged_shape(d, s) : resolve_staged_shape(d, s);
 }

@@ -341,6 +341,23 @@ __device__ __forceinline__ void copy_rows(cf* st, const cf* src, int64_t e, uint
                : "memory");
 }
 
+// Row tiles of a transposing pass: G contiguous rows of L elements, one bulk
+// copy each (one thread), to pitched rows st + g*(L + kRowPad).
+template <class SH>
+__device__ __forceinline__ void stage_rows(cf* st, const cf* src, uint64_t* bar) {
+  const uint32_t b = smem_u32(bar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+               "r"((uint32_t)(SH::kG * SH::kL * 8))
+               : "memory");
+  for (int g = 0; g < SH::kG; ++g)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(st + g * (SH::kL + SH::kRowPad))),
+        "l"(src + g * SH::kL), "r"((uint32_t)(SH::kL * 8)), "r"(b)
+        : "memory");
+}
+
 template <class SH, int S, bool FIRST_EXCHANGE>
 __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
                                                uint64_t* bar, const cf* next_src, int tid) {
@@ -350,6 +367,8 @@ __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& 
   if constexpr (SH::kG == 1) {
     if (FIRST_EXCHANGE && tid == 0 && next_src)  // staging is free: every thread has read it
       tma_load(st, next_src, SH::kL * 8, bar);
+  } else if constexpr (SH::kRowsIn) {
+    if (FIRST_EXCHANGE && tid == 0 && next_src) stage_rows<SH>(st, next_src, bar);
   } else {
     if (FIRST_EXCHANGE && next_src) copy_rows<SH>(st, next_src, d.in.e, bar, tid);
   }
@@ -383,7 +402,7 @@ __global__ void __launch_bounds__(SH::kT, MINB)
 stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   extern __shared__ __align__(128) unsigned char smem_staged[];
   cf* st = reinterpret_cast<cf*>(smem_staged);
-  cf* x = st + SH::kL * SH::kG;
+  cf* x = st + SH::kStageElems;
   uint64_t* bar = reinterpret_cast<uint64_t*>(x + SH::kHalfSlots);
   using B = SplitBody<SH, DevMem>;
   const int tid = threadIdx.x;
@@ -391,11 +410,15 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
   int64_t tile = blockIdx.x;
   // one arrival (the expect_tx of the bulk copy) for a contiguous transform,
   // one per thread (its row copies) for a column tile
-  if (tid == 0) mbar_init(bar, SH::kG == 1 ? 1 : SH::kT);
+  // one arrival (thread 0's expect_tx for bulk copies) for contiguous
+  // transforms and row tiles, one per thread (its row copies) for column tiles
+  if (tid == 0) mbar_init(bar, (SH::kG == 1 || SH::kRowsIn) ? 1 : SH::kT);
   __syncthreads();
   if (tile < d.tiles) {  // uniform over the block
     if constexpr (SH::kG == 1) {
       if (tid == 0) tma_load(st, in + tile * SH::kL, SH::kL * 8, bar);
+    } else if constexpr (SH::kRowsIn) {
+      if (tid == 0) stage_rows<SH>(st, staged_src<SH>(in, d, tile), bar);
     } else {
       copy_rows<SH>(st, staged_src<SH>(in, d, tile), d.in.e, bar, tid);
     }
@@ -495,5 +518,6 @@ const void* resolve_fourstep_shape(int R, int lmap, int smap, const PassDesc& d)
 bool resolve_staged_shape(const PassDesc& d, StagedLaunch* s);
 bool resolve_conv_staged_shape(const PassDesc& d, StagedLaunch* s);
 bool resolve_staged_cols_shape(const PassDesc& d, int lmap, int smap, StagedLaunch* s);
+bool resolve_staged_trans_shape(const PassDesc& d, int lmap, int smap, StagedLaunch* s);
 
 }  // namespace gbfft

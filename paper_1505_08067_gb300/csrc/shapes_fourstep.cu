@@ -28,4 +28,19 @@ bool resolve_staged_cols_shape(const PassDesc& d, int lmap, int smap, StagedLaun
   return false;
 }
 
+// Staged transposing passes (see GB_STAGED_TRANS_SHAPES).
+bool resolve_staged_trans_shape(const PassDesc& d, int lmap, int smap, StagedLaunch* s) {
+#define GB_STAGED_TRANS(LOGL, SCHED, NST, RR, G)                                     \
+  if (staged_trans_matches(d, lmap, smap, LOGL, SCHED, NST, G)) {                    \
+    using SH = SplitShape<LOGL, SCHED, NST, RR, G, 0, true>;                         \
+    s->fn = (const void*)staged_fn<SH, 1, false>();                                  \
+    s->block = SH::kT;                                                               \
+    s->smem = split_smem_bytes<SH>();                                                \
+    return true;                                                                     \
+  }
+  GB_STAGED_TRANS_SHAPES(GB_STAGED_TRANS)
+#undef GB_STAGED_TRANS
+  return false;
+}
+
 }  // namespace gbfft

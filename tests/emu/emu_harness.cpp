@@ -258,7 +258,7 @@ template <class SH, bool CONV = false>
 void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
   using B = SplitBody<SH, CheckMem>;
   constexpr int R = SH::kR;
-  constexpr int TILE = SH::kL * SH::kG;
+  constexpr int TILE = SH::kStageElems;
   std::vector<cf> st(TILE), x(SH::kHalfSlots);
   std::vector<int64_t> ep(x.size(), -1), wr(x.size(), -1);
   g.slot_epoch = &ep;
@@ -281,8 +281,12 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       col0 = inner * SH::kG;
     }
     for (int a = 0; a < SH::kL; ++a)
-      for (int c = 0; c < SH::kG; ++c)
-        st[a * SH::kG + c] = CheckMem::ldg(in, src + (SH::kG == 1 ? a : c + a * d.in.e));
+      for (int c = 0; c < SH::kG; ++c) {
+        if constexpr (SH::kRowsIn)  // one bulk copy per row, pitched
+          st[c * (SH::kL + SH::kRowPad) + a] = CheckMem::ldg(in, src + c * SH::kL + a);
+        else
+          st[a * SH::kG + c] = CheckMem::ldg(in, src + (SH::kG == 1 ? a : c + a * d.in.e));
+      }
     for (int t = 0; t < SH::kT; ++t) {
       if (d.conj_in) B::template first<true>(reg(t), st.data(), t);
       else B::template first<false>(reg(t), st.data(), t);
@@ -326,6 +330,18 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
     }
   }
   g.staging = nullptr;
+}
+
+// Transposing passes (GB_STAGED_TRANS_SHAPES).
+bool run_staged_trans(int lmap, int smap, const PassDesc& d, const cf* in, cf* out) {
+#define GB_STAGED_TRANS(LOGL, SCHED, NST, RR, G)                                  \
+  if (staged_trans_matches(d, lmap, smap, LOGL, SCHED, NST, G)) {                 \
+    run_staged_t<SplitShape<LOGL, SCHED, NST, RR, G, 0, true>>(d, in, out);       \
+    return true;                                                                 \
+  }
+  GB_STAGED_TRANS_SHAPES(GB_STAGED_TRANS)
+#undef GB_STAGED_TRANS
+  return false;
 }
 
 // Column tiles of strided passes (GB_STAGED_COLS_SHAPES).
@@ -563,7 +579,8 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
     } else if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);
     else if (specialised && !s.generic_only && (p.variant == 0 || p.variant == 2) &&
              (p.lmap == MAP_COLS ? run_staged_cols(p.lmap, p.smap, d, src, dst)
-                                 : (p.lmap == MAP_ROWS && p.smap == MAP_ROWS && run_staged(d, src, dst))))
+              : p.smap == MAP_COLS ? run_staged_trans(p.lmap, p.smap, d, src, dst)
+                                   : run_staged(d, src, dst)))
       ++g.staged_passes;
     else if (specialised && !s.generic_only && run_special(p.R, p.lmap, p.smap, d, src, dst)) ++g.special_passes;
     else if (p.lmap == MAP_ROWS && p.smap == MAP_ROWS) run_maps<0, 0>(p.R, d, src, dst);

@@ -196,16 +196,19 @@ def test_conv_forced_radix_and_tile(oracle, radix, tile):
 
 
 @pytest.mark.parametrize("logn,split,epilogue", [(15, 10, 2), (15, 10, 3), (16, 11, 2), (16, 11, 3),
-                                                 (17, 12, 2), (17, 12, 3)])
+                                                 (17, 12, 2), (17, 12, 3), (20, 10, 2), (22, 11, 3),
+                                                 (22, 10, 3)])
 @pytest.mark.parametrize("direction", [-1, 1])
 def test_staged_column_first_pass(oracle, logn, split, epilogue, direction):
     """Four-step first passes of 1024 / 2048 / 4096 points run the staged
-    column kernel (rows copied in bulk, G = 16 / 8 / 4 columns per tile, the
-    four-step twiddle on store); the register kernel must agree."""
+    column kernel (G = 16 / 8 / 4 columns per tile, the four-step twiddle on
+    store); second passes of 1024 / 2048 / 4096 points the staged transposing
+    kernel (G contiguous rows in, G columns out); the register kernels must
+    agree."""
     n = 2 ** logn
     x = synth.uniform(40 + logn, 3, n)
     ref = oracle.fft(x, direction)
-    for variant, staged in ((0, 1), (1, 0)):
+    for variant, staged in ((0, 2 if logn - split in (10, 11, 12) else 1), (1, 0)):
         st = {}
         y, nerr, msg = emu.run(x, (n,), direction=direction, stats=st, split_log2=split,
                                epilogue=epilogue, variant=variant)
