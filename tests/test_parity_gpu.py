@@ -167,7 +167,10 @@ def test_empty_batch_and_errors(gb):
 
 
 def test_execute_host_matches_device(gb, oracle):
-    for shape, batch in (((4096,), 300), ((2 ** 18,), 6), ((64, 128), 3)):
+    # 2^22 x 3 and 2^20 x 40 split into several ~32 MiB chunks, each running
+    # the staged column and transposing passes on a sub-batch
+    for shape, batch in (((4096,), 300), ((2 ** 18,), 6), ((64, 128), 3), ((2 ** 22,), 3),
+                         ((2 ** 20,), 40)):
         n = int(np.prod(shape))
         x = synth.uniform(4700 + n, batch, n).reshape((batch,) + shape)
         host_in = torch.from_numpy(x).pin_memory()
