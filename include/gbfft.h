@@ -190,7 +190,11 @@ GBFFT_API fft_status_t fft_plan_launch_count(fft_plan_t plan, int* launches);
 
 /*
  * JSON description of the plan (passes, radix schedules, tile shapes, grid,
- * shared memory) written to buf (NUL-terminated, truncated to len).  Returns
+ * shared memory; "kernels": per pass the kernel bound to it -- "staged" (the
+ * TMA / cp.async staged kernel, used when the source is 16-byte aligned, else
+ * the compile-time kernel of the shape), "compile_time", "generic",
+ * "tensor_core" or "copy" -- with its persistent-grid size and L2-prefetch
+ * flag) written to buf (NUL-terminated, truncated to len).  Returns
  * FFT_ERR_INVALID_ARG if buf is too small for the whole text.
  */
 GBFFT_API fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len);

@@ -359,7 +359,26 @@ static fft_status_t copy_text(const std::string& t, char* buf, size_t len) {
 
 fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len) {
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
-  return copy_text(describe(plan->spec), buf, len);
+  // the planner's description plus, per pass, the kernel bound to it
+  std::string t = describe(plan->spec);
+  std::string k = ",\"kernels\":[";
+  for (int i = 0; i < plan->spec.passes.size(); ++i) {
+    const PassSpec& p = plan->spec.passes[i];
+    const PassLaunch& l = plan->launches[i];
+    const char* kind = p.kind != PASS_FFT ? "copy"
+                       : p.tc_prec        ? "tensor_core"
+                       : l.has_staged     ? "staged"  // for a 16-byte-aligned source
+                       : l.specialised    ? "compile_time"
+                                          : "generic";
+    char b[160];
+    snprintf(b, sizeof b, "%s{\"kernel\":\"%s\",\"conv\":%d,\"persistent_grid\":%d,"
+             "\"l2_prefetch\":%d}", i ? "," : "", kind, p.conv, l.persistent_grid,
+             (int)l.d.l2_prefetch);
+    k += b;
+  }
+  k += "]";
+  t.insert(t.size() - 1, k);
+  return copy_text(t, buf, len);
 }
 
 fft_status_t fft_plan_dry_run(const int64_t* n, int dims, int64_t batch, int direction,

@@ -396,3 +396,27 @@ def test_graph_execution_matches(gb, oracle, shape, batch):
         p.execute_graph(x, y1)
         torch.cuda.synchronize()
         assert torch.equal(-ref, y1)
+
+
+@pytest.mark.parametrize("shape,batch,kernels", [
+    ((256,), 2 ** 19, ["compile_time"]), ((2048,), 2 ** 16, ["compile_time"]),
+    ((4096,), 2 ** 15, ["staged"]), ((8192,), 2 ** 14, ["staged"]), ((16384,), 2 ** 13, ["staged"]),
+    ((2 ** 20,), 4, ["staged", "staged"]), ((2 ** 22,), 1, ["staged", "staged"]),
+    ((4096, 8192), 1, ["staged", "staged"]), ((512,), 2 ** 18, ["compile_time"]),
+    ((512,), 3, ["generic"])])
+def test_kernel_selection(gb, shape, batch, kernels):
+    """The benchmarked shapes bind the intended kernels (no generic fallback)."""
+    with gb.Plan(shape if len(shape) > 1 else shape[0], batch) as p:
+        got = [k["kernel"] for k in p.describe()["kernels"]]
+    assert got == kernels, got
+
+
+def test_kernel_selection_conv_and_tc(gb):
+    h = torch.ones(8192, dtype=torch.complex64, device="cuda")
+    ha = torch.ones(4096 * 8192, dtype=torch.complex64, device="cuda")
+    with gb.ConvPlan((4096, 8192), 1, [(ha, 8192, 1.0), (h, 1, 1.0)]) as p:
+        ks = p.describe()["kernels"]
+    assert [k["kernel"] for k in ks] == ["staged", "compile_time"] and all(k["conv"] for k in ks)
+    with gb.Plan(4096, 64, -1, gb.FFT_PREC_TC_BF16) as p:
+        ks = p.describe()["kernels"]
+    assert ks[0]["kernel"] == "tensor_core" and ks[0]["persistent_grid"] > 0
