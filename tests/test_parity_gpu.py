@@ -405,7 +405,9 @@ def test_graph_execution_matches(gb, oracle, shape, batch):
     ((4096, 8192), 1, ["staged", "staged"]), ((512,), 2 ** 18, ["compile_time"]),
     ((512,), 3, ["generic"])])
 def test_kernel_selection(gb, shape, batch, kernels):
-    """The benchmarked shapes bind the intended kernels (no generic fallback)."""
+    """The benchmarked shapes bind the intended kernels; a small batch whose
+    tile has no compiled shape (4 transforms of 512 points) runs the generic
+    kernel."""
     with gb.Plan(shape if len(shape) > 1 else shape[0], batch) as p:
         got = [k["kernel"] for k in p.describe()["kernels"]]
     assert got == kernels, got
