@@ -422,3 +422,29 @@ def test_kernel_selection_conv_and_tc(gb):
     with gb.Plan(4096, 64, -1, gb.FFT_PREC_TC_BF16) as p:
         ks = p.describe()["kernels"]
     assert ks[0]["kernel"] == "tensor_core" and ks[0]["persistent_grid"] > 0
+
+
+def test_execute_argument_errors(gb):
+    """Run-time argument checks of the execute entry points: null or
+    misaligned device pointers, null host buffers, a description buffer that
+    is too small.  Each returns FFT_ERR_INVALID_ARG and leaves the plan usable."""
+    x = torch.zeros(2 * 1024, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    hx = torch.zeros(2 * 1024, dtype=torch.complex64).pin_memory()
+    with gb.Plan(1024, 2) as p:
+        for args in ((0, y.data_ptr()), (x.data_ptr(), 0), (x.data_ptr() + 4, y.data_ptr()),
+                     (x.data_ptr(), y.data_ptr() + 2)):
+            for fn in (gb.fft_execute, gb.fft_execute_graph):
+                with pytest.raises(gb.GbfftError) as e:
+                    fn(p.handle, *args)
+                assert e.value.status == gb.FFT_ERR_INVALID_ARG
+        with pytest.raises(gb.GbfftError) as e:
+            gb.fft_execute_host(p.handle, 0, hx.data_ptr(), x.data_ptr(), y.data_ptr())
+        assert e.value.status == gb.FFT_ERR_INVALID_ARG
+        import ctypes
+        buf = ctypes.create_string_buffer(16)
+        st = gb.load().fft_plan_describe(p.handle, buf, len(buf))
+        assert st == gb.FFT_ERR_INVALID_ARG and len(buf.value) == 15
+        p.execute(x, y)                      # still usable
+        gb.fft_plan_sync_status(p.handle)
+        torch.cuda.synchronize()
