@@ -339,7 +339,7 @@ typedef struct {
   uint64_t coalesced_jobs;  /* jobs that shared a coalesced launch */
   uint64_t workspace_allocations;
   size_t peak_bytes_in_flight, budget_bytes;
-  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed jobs */
+  double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed jobs (the most recent 2^20) */
   double wall_s;            /* first submit -> last completion */
   double gflops;            /* 5 N log2 N of completed jobs / wall_s */
 } fft_server_stats_t;

@@ -139,8 +139,10 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
                   (long long)spec.work_elems * 8, cudaGetErrorString(e));
     }
   }
+  // tables on the legacy stream, waited for alone (work of the caller on
+  // non-blocking streams is not waited for)
   e = enqueue_tables(spec, static_cast<cf*>(p->tables), 0);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e == cudaSuccess)
     e = bind_launches(p->spec, p->caps, static_cast<const cf*>(p->tables), p->status, p->launches);
   if (e != cudaSuccess) {

@@ -41,6 +41,7 @@ using namespace gbfft;
 namespace {
 
 constexpr uint32_t kServerMagic = 0x53525646u;
+constexpr size_t kLatencyWindow = size_t(1) << 20;  // latency samples kept for p50 / p99
 
 double now_s() {
   using namespace std::chrono;
@@ -102,7 +103,8 @@ struct fft_server_s {
   std::vector<cudaEvent_t> free_events;
   uint64_t next_id = 1;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, coalesced = 0;
-  std::vector<double> latencies;
+  std::vector<double> latencies;  // the most recent kLatencyWindow completions (a ring)
+  size_t latency_next = 0;
   double first_submit = 0, last_done = 0, flops = 0;
   size_t ws_allocs = 0;
 
@@ -144,9 +146,11 @@ PlanEntry* plan_for(fft_server_t s, const JobKey& k, fft_status_t* st) {
     return nullptr;
   }
   pe->status = reinterpret_cast<int*>(static_cast<char*>(pe->tables) + pe->spec.table_elems * 8);
-  cudaMemset(pe->status, 0, 16);
-  e = enqueue_tables(pe->spec, static_cast<cf*>(pe->tables), 0);
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  // tables on the legacy stream, waited for alone: the server's streams are
+  // non-blocking, so groups already running are not waited for
+  e = cudaMemsetAsync(pe->status, 0, 16, 0);
+  if (e == cudaSuccess) e = enqueue_tables(pe->spec, static_cast<cf*>(pe->tables), 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e == cudaSuccess)
     e = bind_launches(pe->spec, s->caps, static_cast<const cf*>(pe->tables), pe->status,
                       pe->launches);
@@ -317,7 +321,10 @@ void worker_loop(fft_server_t s) {
         if (q == cudaSuccess) {
           rec.status = FFT_OK;
           ++s->completed;
-          s->latencies.push_back((t - rec.t_submit) * 1e3);
+          const double ms = (t - rec.t_submit) * 1e3;
+          if (s->latencies.size() < kLatencyWindow) s->latencies.push_back(ms);
+          else s->latencies[s->latency_next] = ms;
+          s->latency_next = (s->latency_next + 1) % kLatencyWindow;
           s->flops += job_flops(rec.job);
         } else {
           rec.status = FFT_ERR_CUDA;
