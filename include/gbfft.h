@@ -125,7 +125,10 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *                 (w = hi[m >> b] * lo[m mod 2^b]), 2 one table of N entries laid
  *                 out like the first pass's output (coalesced loads, N*8 bytes
  *                 more plan memory), 3 computed in-kernel from the exact FP32
- *                 angle 2m/N with sincospi.
+ *                 angle 2m/N with sincospi, 4 factored: the first pass's last
+ *                 stage writes k1 = jb + i*Ns, and w_N^{n2 k1} is computed as
+ *                 w_N^{n2 jb} * (w_N^{n2 Ns})^i (two sincospi per butterfly,
+ *                 the powers by products; no table).
  *   split_log2    two-pass 1D plans: log2 of the first (column) pass length N1
  *                 (0 = library choice, N1 <= N2).
  */

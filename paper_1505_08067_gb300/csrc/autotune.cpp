@@ -321,7 +321,7 @@ fft_status_t autotune_options(const int64_t* n, int dims, int64_t batch, int dir
     // with L2 prefetch of the next tile (variant 3)
     const int l1d = def.passes[0].logL;
     for (int l1 = l1d - 1; l1 <= l1d + 1; ++l1)
-      for (int ep : {2, 3})
+      for (int ep : {2, 3, 4})
         for (int v : {0, 3}) {
           if (ep == 2 && logN > 22) continue;
           fft_plan_options_t o = b;

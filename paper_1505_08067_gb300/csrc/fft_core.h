@@ -169,6 +169,9 @@ struct PassDesc {
                               //   1 two-level tables hi[m >> lo_bits] * lo[m & (2^lo_bits - 1)]
                               //   2 full table in the output's layout: epi_lo[n2 + k1 * N2]
                               //   3 computed: sincospi of the exact FP32 angle 2 m / N
+                              //   4 factored: the last stage writes k1 = jb + i*Ns, so
+                              //     w = w_N^{n2 jb} * (w_N^{n2 Ns})^i: two sincospi per
+                              //     butterfly and step, powers of the step by products
   int32_t epi_lo_bits;
   int32_t epi_logN;
   int32_t l2_prefetch;        // contiguous passes on a persistent grid: prefetch next tile

@@ -202,6 +202,7 @@ GB_UNROLL
   // w_N^{col * pos} of column col = col0 + g when SH::kEpi != 0.
   // `og` = o for G = 1, else this thread's column o + g*out.g; offsets in
   // 32 bits (pos * out.e < 2^31 for every frame the planner emits).
+  // (kEpi == 4 is applied by the caller, which knows the butterfly structure)
   template <bool SWAP>
   GB_HD static void put(const PassDesc& d, cf* og, int col, int pos, cf x) {
     if constexpr (SH::kEpi == 2) {
@@ -278,6 +279,7 @@ GB_UNROLL
   template <bool SWAP>
   GB_HD static void store_fused(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0,
                                 int tid) {
+    static_assert(SH::kEpi != 4, "the factored twiddle needs the plain last stage");
     constexpr int s = SH::kNst - 1;
     constexpr int NB = SH::kNB;
     constexpr int Ns = L / NB;
@@ -308,11 +310,26 @@ GB_UNROLL
     int g, t;
     coords(tid, g, t);
     cf* og = column_out(d, o, g);
+    const int col = (int)col0 + g;
+    // factored four-step twiddle: w_N^{col (jb + i Ns)} = w_N^{col jb} (w_N^{col Ns})^i
+    cf pw[RR];
+    if constexpr (SH::kEpi == 4) {
+      pw[0] = mk(1.f, 0.f);
+      pw[1] = Mem::rotor(col * (int64_t)Ns, d.epi_logN);  // col*Ns < N
+GB_UNROLL
+      for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
+    }
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * T + t;
+      cf base = mk(1.f, 0.f);
+      if constexpr (SH::kEpi == 4) base = Mem::rotor(col * (int64_t)jb, d.epi_logN);
 GB_UNROLL
-      for (int i = 0; i < RR; ++i) put<SWAP>(d, og, (int)col0 + g, jb + i * Ns, v[q * RR + i]);
+      for (int i = 0; i < RR; ++i) {
+        cf x = v[q * RR + i];
+        if constexpr (SH::kEpi == 4) x = cmul(x, i == 0 ? base : cmul(base, pw[i]));
+        put<SWAP>(d, og, col, jb + i * Ns, x);
+      }
     }
   }
 };

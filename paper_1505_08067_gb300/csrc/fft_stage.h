@@ -194,15 +194,26 @@ GB_UNROLL
     const int epi = TR::kEpi < 0 ? d.epi : TR::kEpi;
     // full-table mode: the twiddle of output (col, a) sits at col + a * columns
     const cf* tfull = d.epi_lo + col;
+    // factored mode: powers of w_N^{col Ns}, each a product of two lower ones
+    cf pw[RR];
+    if (epi == 4) {
+      pw[0] = mk(1.f, 0.f);
+      if (RR > 1) pw[1] = Mem::rotor(col * (int64_t)Ns, d.epi_logN);  // col*Ns < N
+GB_UNROLL
+      for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
+    }
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * TR::T(d) + t;
       cf* p = tb + (int64_t)jb * e;
       const cf* pt = tfull + (int64_t)jb * d.count_inner;
+      const cf base = epi == 4 ? Mem::rotor(col * (int64_t)jb, d.epi_logN) : mk(1.f, 0.f);
 GB_UNROLL
       for (int i = 0; i < RR; ++i) {
         cf x = v[q * RR + i];
-        if (epi == 1) {
+        if (epi == 4) {
+          x = cmul(x, i == 0 ? base : cmul(base, pw[i]));
+        } else if (epi == 1) {
           const int64_t m = col * (int64_t)(jb + i * Ns);
           const cf w = cmul(Mem::ldtw(d.epi_hi + (m >> d.epi_lo_bits)),
                             Mem::ldtw(d.epi_lo + (m & ((int64_t(1) << d.epi_lo_bits) - 1))));

@@ -18,8 +18,9 @@
   GB_SHAPE(13, 0x1444, 4, 16, 1, 0, 0, true, 0)               \
   GB_SHAPE(14, 0x2444, 4, 16, 1, 0, 0, true, 0)
 
-/* four-step N = 2^20, 2^22, 2^24: column pass (twiddle on store, full-table */
-/* or computed) and row pass (transposed store); 2D column pass of 4096 rows */
+/* four-step N = 2^20, 2^22, 2^24: column pass (twiddle on store: full table, */
+/* computed or factored) and row pass (transposed store); 2D column pass of */
+/* 4096 rows */
 #define GB_SHAPES_FOURSTEP(GB_SHAPE)                          \
   GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 2)              \
   GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 3)              \
@@ -30,7 +31,10 @@
   GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 2)               \
   GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 3)               \
   GB_SHAPE(12, 0x444, 3, 16, 4, 0, 1, false, 0)               \
-  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)              \
+  GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 4)             \
+  GB_SHAPE(11, 0x344, 3, 16, 8, 1, 1, false, 4)              \
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 4)
 
 /* fast convolution: range lines of 4096 / 8192 / 16384, azimuth columns */
 /* of 4096 (the 2D frame's column pass) */
@@ -53,7 +57,7 @@
 // columns per block, rows copied by 16-byte asynchronous copies while the
 // previous tile is computed, half-size exchanges):
 //   GB_STAGED_COLS(log2 L, schedule, stages, R, G, epilogue, conv)
-// four-step first passes (epilogue 2 or 3) and the 2D column pass.  (The
+// four-step first passes (epilogue 2, 3 or 4) and the 2D column pass.  (The
 // azimuth convolution keeps the 1024-thread register kernel, measured faster.)
 #define GB_STAGED_COLS_SHAPES(GB_STAGED_COLS)      \
   GB_STAGED_COLS(10, 0x244, 3, 32, 16, 2, 0)       \
@@ -62,7 +66,10 @@
   GB_STAGED_COLS(11, 0x344, 3, 32, 8, 3, 0)        \
   GB_STAGED_COLS(12, 0x444, 3, 32, 4, 2, 0)        \
   GB_STAGED_COLS(12, 0x444, 3, 32, 4, 3, 0)        \
-  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 0, 0)
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 0, 0)        \
+  GB_STAGED_COLS(10, 0x244, 3, 32, 16, 4, 0)       \
+  GB_STAGED_COLS(11, 0x344, 3, 32, 8, 4, 0)        \
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 4, 0)
 
 // Transposing passes (G contiguous rows in, G columns out: the second pass of
 // a four-step plan) that run the staged kernel:

@@ -85,7 +85,7 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
     caps.max_block = v;
   PlanSpec s;
   fft_plan_options_t opt{};
-  opt.epilogue = 3;  // four-step twiddles computed in-kernel: no N-entry table in static memory
+  opt.epilogue = 4;  // four-step twiddles computed in-kernel: no N-entry table in static memory
   make_plan(s, &n, 1, batch, direction, FFT_PREC_FP32, &opt, caps);
   if (s.status != FFT_OK) return set_error(s.status, s.error);
   if (s.work_elems > kWorkElems)

@@ -211,7 +211,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   if (o.radix && (o.radix < 2 || o.radix > 16 || !is_pow2(o.radix)))
     { fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16"); return; }
   if (o.variant < 0 || o.variant > 3) { fail(FFT_ERR_INVALID_ARG, "variant must be 0..3"); return; }
-  if (o.epilogue < 0 || o.epilogue > 3) { fail(FFT_ERR_INVALID_ARG, "epilogue must be 0..3"); return; }
+  if (o.epilogue < 0 || o.epilogue > 4) { fail(FFT_ERR_INVALID_ARG, "epilogue must be 0..4"); return; }
   if (o.tile < 0 || o.tile > 1024 || (o.tile && !is_pow2(o.tile)))
     { fail(FFT_ERR_INVALID_ARG, "tile option must be a power of two <= 1024"); return; }
   s.dims = dims;
@@ -344,9 +344,10 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p1.src = BUF_IN;
       p1.dst = BUF_WORK;
       p1.conj_in = inv;
-      // four-step twiddle source: a full table while it stays L2-sized,
-      // computed in-kernel beyond that
-      p1.epi = o.epilogue ? o.epilogue : (logN <= 20 ? 2 : 3);
+      // four-step twiddle source: factored (a sincospi per butterfly and step,
+      // powers of the step by products; no table), measured fastest at
+      // N = 2^20..2^24; the autotuner also tries the tables and sincospi
+      p1.epi = o.epilogue ? o.epilogue : 4;
       p1.epi_logN = logN;
       p1.epi_lo_bits = (logN + 1) / 2;
       // pass 2: row FFTs of length N2 over N1 rows, transposed store

@@ -82,7 +82,7 @@ def test_planner_limits(logn, batch):
     if logn > 14:
         assert d["workspace_bytes"] == 8 * batch * 2 ** logn
         p1, p2 = passes
-        assert p1["L"] * p2["L"] == 2 ** logn and p1["epi"] in (2, 3) and p2["smap"] == "cols"
+        assert p1["L"] * p2["L"] == 2 ** logn and p1["epi"] == 4 and p2["smap"] == "cols"
 
 
 def test_sar_frame_plan():

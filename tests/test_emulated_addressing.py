@@ -85,7 +85,7 @@ def test_largest_four_step_slice(oracle):
     _check(oracle, (2 ** 20,), 1)
 
 
-@pytest.mark.parametrize("epilogue", [1, 2, 3])
+@pytest.mark.parametrize("epilogue", [1, 2, 3, 4])
 @pytest.mark.parametrize("logn", [15, 20])
 def test_four_step_twiddle_sources(oracle, epilogue, logn):
     """Two-level tables, the full table and the in-kernel rotor give the same
@@ -197,7 +197,8 @@ def test_conv_forced_radix_and_tile(oracle, radix, tile):
 
 @pytest.mark.parametrize("logn,split,epilogue", [(15, 10, 2), (15, 10, 3), (16, 11, 2), (16, 11, 3),
                                                  (17, 12, 2), (17, 12, 3), (20, 10, 2), (22, 11, 3),
-                                                 (22, 10, 3)])
+                                                 (22, 10, 3), (15, 10, 4), (16, 11, 4), (17, 12, 4),
+                                                 (22, 11, 4)])
 @pytest.mark.parametrize("direction", [-1, 1])
 def test_staged_column_first_pass(oracle, logn, split, epilogue, direction):
     """Four-step first passes of 1024 / 2048 / 4096 points run the staged

@@ -279,7 +279,9 @@ def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
 
 @pytest.mark.parametrize("shape,batch,opts", [((4096, 64), 2, {}), ((2 ** 20,), 2, {"split_log2": 10}),
                                               ((2 ** 22,), 1, {"split_log2": 11, "epilogue": 3}),
-                                              ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 3})])
+                                              ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 3}),
+                                              ((2 ** 22,), 1, {"split_log2": 11, "epilogue": 4}),
+                                              ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 4})])
 def test_staged_columns_and_unaligned_fallback(gb, oracle, shape, batch, opts):
     """Column passes (2D, four-step first passes with G = 16 / 8 / 4 columns)
     run the staged column kernel (variant 2) from a 16-byte-aligned source and
@@ -338,11 +340,12 @@ def test_prefetch_variant_strided_passes(gb, oracle, shape, batch):
             assert np.max(oracle.rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1))) <= _tol(n)
 
 
-@pytest.mark.parametrize("epilogue", [1, 2, 3])
+@pytest.mark.parametrize("epilogue", [1, 2, 3, 4])
 @pytest.mark.parametrize("logn", [16, 20, 22])
 def test_four_step_twiddle_sources(gb, oracle, epilogue, logn):
-    """The three sources of the four-step twiddle w_N^{n2 k1} (two small tables,
-    one full table, sincospi of the exact angle) agree with the oracle."""
+    """The four sources of the four-step twiddle w_N^{n2 k1} (two small tables,
+    one full table, sincospi of the exact angle, factored into a per-butterfly
+    base and powers of a step) agree with the oracle."""
     n = 2 ** logn
     batch = max(1, 2 ** 22 // n)
     x = synth.uniform(9300 + logn, batch, n)
