@@ -75,6 +75,11 @@ struct SplitShape {
   static constexpr int kNB = R_ / 16;
   static constexpr bool kFuseLast = NST >= 2 && radix(NST - 1) == kNB && rlog(NST - 2) == 4;
   static constexpr int kExchanges = kFuseLast ? NST - 2 : NST - 1;
+  // Stage twiddles as powers of one loaded root (SplitBody::compute) where a
+  // block fills most of an SM (column tiles, 2^13 and 2^14): fewer loads whose
+  // latency few warps cannot hide.  The contiguous 2^12 shape runs four
+  // blocks per SM and is faster with one table load per twiddle (measured).
+  static constexpr bool kPowTw = G_ > 1 || LOGL >= 13;
 };
 
 template <class SH, class Mem>
@@ -188,8 +193,17 @@ GB_UNROLL
       const int jb = q * T + t;
       const int k = jb & (Ns - 1);
       const cf* tw = d.tw + d.tw_off[s] + k;
+      // kPowTw: one table load of w_{RR*Ns}^k per butterfly, its powers by
+      // products (at most four roundings)
+      cf pw[RR];
+      if (SH::kPowTw) {
+        pw[1] = Mem::ldtw(tw + Ns);
 GB_UNROLL
-      for (int i = 1; i < RR; ++i) w[q * RR + i] = cmul(w[q * RR + i], Mem::ldtw(tw + i * Ns));
+        for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
+      }
+GB_UNROLL
+      for (int i = 1; i < RR; ++i)
+        w[q * RR + i] = cmul(w[q * RR + i], SH::kPowTw ? pw[i] : Mem::ldtw(tw + i * Ns));
       dft_radix<RR>(w + q * RR);
     }
 GB_UNROLL
@@ -290,10 +304,16 @@ GB_UNROLL
 GB_UNROLL
     for (int i = 0; i < 16; ++i) {
       const int p = t + i * T;
-      cf x[NB];
+      cf x[NB], pw[NB];
       x[0] = v[i];
+      if (SH::kPowTw && NB > 2) {  // w_L^{q p} = (w_L^p)^q
+        pw[1] = Mem::ldtw(tw + Ns + p);
 GB_UNROLL
-      for (int q = 1; q < NB; ++q) x[q] = cmul(v[q * 16 + i], Mem::ldtw(tw + q * Ns + p));
+        for (int q = 2; q < NB; ++q) pw[q] = cmul(pw[q / 2], pw[q - q / 2]);
+      }
+GB_UNROLL
+      for (int q = 1; q < NB; ++q)
+        x[q] = cmul(v[q * 16 + i], SH::kPowTw && NB > 2 ? pw[q] : Mem::ldtw(tw + q * Ns + p));
       dft_radix<NB>(x);
 GB_UNROLL
       for (int q = 0; q < NB; ++q) put<SWAP>(d, og, (int)col0 + g, p + q * Ns, x[q]);
