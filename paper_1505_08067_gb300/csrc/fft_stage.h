@@ -134,10 +134,11 @@ GB_UNROLL
   }
 
   // --------------------------------------------- shared -> registers -----
-  // POW: instead of one table load per twiddle, load w = w_{Ns*r}^k once and
-  // form w^i as products of lower powers (at most four roundings): fewer
-  // memory instructions for passes bound by the load queue.
-  template <int RR, bool SWAP, bool STORE = true, bool POW = false>
+  // Twiddles: one table load of w = w_{Ns*r}^k per butterfly, w^i formed as
+  // products of lower powers (at most four roundings) instead of r-1 table
+  // loads: the passes were bound by the load queue (2^9..2^12: 92-95% of
+  // the HBM copy bandwidth with table loads, 99-102% with powers).
+  template <int RR, bool SWAP, bool STORE = true>
   GB_HD static void read_r(cf (&v)[R], const PassDesc& d, int s, int Ns, cf* out,
                            const cf* sm, const Tile& tl, int tid) {
     constexpr int NB = R / RR;
@@ -153,16 +154,14 @@ GB_UNROLL
       // twiddles w_{Ns*r}^{i*k}, stored i-major: consecutive k are adjacent
       const cf* w = d.tw + d.tw_off[s] + k;
       cf pw[RR];
-      if (POW) {
-        pw[1] = Mem::ldtw(w + Ns);
+      pw[1] = Mem::ldtw(w + Ns);
 GB_UNROLL
-        for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
-      }
+      for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
       const int sb = slot(d, g, jb);
 GB_UNROLL
       for (int i = 0; i < RR; ++i) {
         cf x = Mem::lds(sm, slot_plus(d, g, jb, sb, i * stride));
-        if (i > 0) x = cmul(x, POW ? pw[i] : Mem::ldtw(w + i * Ns));
+        if (i > 0) x = cmul(x, pw[i]);
         v[q * RR + i] = x;
       }
       dft_radix<RR>(v + q * RR);
@@ -354,10 +353,10 @@ GB_UNROLL
   GB_HD static void read_nostore(cf (&v)[R], const PassDesc& d, int s, int Ns, const cf* sm,
                                  const Tile& tl, int tid) {
     switch (TR::rlog(d, s)) {
-      case 1: if (R >= 2) read_r<(R >= 2 ? 2 : R), false, false, true>(v, d, s, Ns, nullptr, sm, tl, tid); break;
-      case 2: if (R >= 4) read_r<(R >= 4 ? 4 : R), false, false, true>(v, d, s, Ns, nullptr, sm, tl, tid); break;
-      case 3: if (R >= 8) read_r<(R >= 8 ? 8 : R), false, false, true>(v, d, s, Ns, nullptr, sm, tl, tid); break;
-      case 4: if (R >= 16) read_r<(R >= 16 ? 16 : R), false, false, true>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 1: if (R >= 2) read_r<(R >= 2 ? 2 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 2: if (R >= 4) read_r<(R >= 4 ? 4 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 3: if (R >= 8) read_r<(R >= 8 ? 8 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
+      case 4: if (R >= 16) read_r<(R >= 16 ? 16 : R), false, false>(v, d, s, Ns, nullptr, sm, tl, tid); break;
       default: break;
     }
   }
@@ -387,14 +386,14 @@ GB_UNROLL
     }
   }
 
-  template <bool SWAP, bool POW = false>
+  template <bool SWAP>
   GB_HD static void read_s(cf (&v)[R], const PassDesc& d, int s, int Ns, cf* out,
                            const cf* sm, const Tile& tl, int tid) {
     switch (TR::rlog(d, s)) {
-      case 1: if (R >= 2) read_r<(R >= 2 ? 2 : R), SWAP, true, POW>(v, d, s, Ns, out, sm, tl, tid); break;
-      case 2: if (R >= 4) read_r<(R >= 4 ? 4 : R), SWAP, true, POW>(v, d, s, Ns, out, sm, tl, tid); break;
-      case 3: if (R >= 8) read_r<(R >= 8 ? 8 : R), SWAP, true, POW>(v, d, s, Ns, out, sm, tl, tid); break;
-      case 4: if (R >= 16) read_r<(R >= 16 ? 16 : R), SWAP, true, POW>(v, d, s, Ns, out, sm, tl, tid); break;
+      case 1: if (R >= 2) read_r<(R >= 2 ? 2 : R), SWAP>(v, d, s, Ns, out, sm, tl, tid); break;
+      case 2: if (R >= 4) read_r<(R >= 4 ? 4 : R), SWAP>(v, d, s, Ns, out, sm, tl, tid); break;
+      case 3: if (R >= 8) read_r<(R >= 8 ? 8 : R), SWAP>(v, d, s, Ns, out, sm, tl, tid); break;
+      case 4: if (R >= 16) read_r<(R >= 16 ? 16 : R), SWAP>(v, d, s, Ns, out, sm, tl, tid); break;
       default: break;
     }
   }

@@ -132,7 +132,7 @@ __device__ __forceinline__ void conv_stages(cf (&v)[R], const PassDesc& d, cf* o
     for (int s = 1; s < TR::kMaxStages; ++s) {
       __syncthreads();
       if (ROUND1) B::read_nostore(v, d, s, Ns, sm, tl, tid);
-      else B::template read_s<true, true>(v, d, s, Ns, out, sm, tl, tid);
+      else B::template read_s<true>(v, d, s, Ns, out, sm, tl, tid);
       if (s < TR::kMaxStages - 1) {
         __syncthreads();
         B::write(v, d, s, Ns, sm, tid);
@@ -144,7 +144,7 @@ __device__ __forceinline__ void conv_stages(cf (&v)[R], const PassDesc& d, cf* o
     for (int s = 1; s < d.nst; ++s) {
       __syncthreads();
       if (ROUND1) B::read_nostore(v, d, s, Ns, sm, tl, tid);
-      else B::template read_s<true, true>(v, d, s, Ns, out, sm, tl, tid);
+      else B::template read_s<true>(v, d, s, Ns, out, sm, tl, tid);
       if (s < d.nst - 1) {
         __syncthreads();
         B::write(v, d, s, Ns, sm, tid);

@@ -186,7 +186,7 @@ void run_conv_t(const PassDesc& d, const cf* in, cf* out) {
       for (int s = 1; s < d.nst; ++s) {
         for (int t = 0; t < nthr; ++t) {
           if (round1) B::read_nostore(reg(t), d, s, Ns, smem.data(), tl, t);
-          else B::template read_s<true, true>(reg(t), d, s, Ns, out, smem.data(), tl, t);
+          else B::template read_s<true>(reg(t), d, s, Ns, out, smem.data(), tl, t);
         }
         if (s < d.nst - 1) {
           ++g.epoch;
