@@ -80,6 +80,9 @@ struct SplitShape {
   // latency few warps cannot hide.  The contiguous 2^12 shape runs four
   // blocks per SM and is faster with one table load per twiddle (measured).
   static constexpr bool kPowTw = G_ > 1 || LOGL >= 13;
+  // Load the fused last stage's roots during the last exchange (radix-2
+  // last stage: measured faster) or inside the store loop (radix 4).
+  static constexpr bool kPrefetchFused = kPowTw && kFuseLast && kNB == 2;
 };
 
 template <class SH, class Mem>
@@ -172,9 +175,26 @@ GB_UNROLL
     }
   }
 
-  // Stage S+1 after both rounds: undo the slot renaming, twiddle, DFT.
+  // Twiddle roots w_{RR*Ns}^k of this thread's butterflies in stage S+1
+  // (SH::kPowTw), loaded before the exchange that precedes the stage so that
+  // the exchange hides their latency.
   template <int S>
-  GB_HD static void compute(cf (&v)[R], const PassDesc& d, int tid) {
+  GB_HD static void roots(cf (&r)[R / SH::radix(S + 1)], const PassDesc& d, int tid) {
+    constexpr int s = S + 1;
+    constexpr int NB = R / SH::radix(s);
+    constexpr int Ns = SH::ns_before(s);
+    int g, t;
+    coords(tid, g, t);
+GB_UNROLL
+    for (int q = 0; q < NB; ++q)
+      r[q] = Mem::ldtw(d.tw + d.tw_off[s] + ((q * T + t) & (Ns - 1)) + Ns);
+  }
+
+  // Stage S+1 after both rounds: undo the slot renaming, twiddle, DFT.
+  // `r`: the roots<S>() of this thread (used when SH::kPowTw).
+  template <int S>
+  GB_HD static void compute(cf (&v)[R], const PassDesc& d, int tid,
+                            const cf (&r)[R / SH::radix(S + 1)]) {
     constexpr int s = S + 1;
     constexpr int RR = SH::radix(s);
     constexpr int NB = R / RR;
@@ -193,11 +213,11 @@ GB_UNROLL
       const int jb = q * T + t;
       const int k = jb & (Ns - 1);
       const cf* tw = d.tw + d.tw_off[s] + k;
-      // kPowTw: one table load of w_{RR*Ns}^k per butterfly, its powers by
-      // products (at most four roundings)
+      // kPowTw: one table load of w_{RR*Ns}^k per butterfly (r[q]), its
+      // powers by products (at most four roundings)
       cf pw[RR];
       if (SH::kPowTw) {
-        pw[1] = Mem::ldtw(tw + Ns);
+        pw[1] = r[q];
 GB_UNROLL
         for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
       }
@@ -290,9 +310,20 @@ GB_UNROLL
   // p + q*Ns with p = t + i*T and Ns = L/NB.  The last stage's butterfly p
   // multiplies input q by w_L^{q p} (row q of the i-major table), takes a
   // length-NB DFT and writes output q to p + q*Ns.
+  // Roots w_L^p of the fused last stage's butterflies p = t + i*T (i < 16),
+  // loaded before the last exchange like roots<S>() (SH::kPrefetchFused).
+  GB_HD static void fused_roots(cf (&fr)[16], const PassDesc& d, int tid) {
+    constexpr int Ns = L / SH::kNB;
+    int g, t;
+    coords(tid, g, t);
+    const cf* tw = d.tw + d.tw_off[SH::kNst - 1] + Ns + t;
+GB_UNROLL
+    for (int i = 0; i < 16; ++i) fr[i] = Mem::ldtw(tw + i * T);
+  }
+
   template <bool SWAP>
   GB_HD static void store_fused(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0,
-                                int tid) {
+                                int tid, const cf (&fr)[16]) {
     static_assert(SH::kEpi != 4, "the factored twiddle needs the plain last stage");
     constexpr int s = SH::kNst - 1;
     constexpr int NB = SH::kNB;
@@ -306,14 +337,14 @@ GB_UNROLL
       const int p = t + i * T;
       cf x[NB], pw[NB];
       x[0] = v[i];
-      if (SH::kPowTw && NB > 2) {  // w_L^{q p} = (w_L^p)^q
-        pw[1] = Mem::ldtw(tw + Ns + p);
+      if (SH::kPowTw) {  // w_L^{q p} = (w_L^p)^q
+        pw[1] = SH::kPrefetchFused ? fr[i] : Mem::ldtw(tw + Ns + p);
 GB_UNROLL
         for (int q = 2; q < NB; ++q) pw[q] = cmul(pw[q / 2], pw[q - q / 2]);
       }
 GB_UNROLL
       for (int q = 1; q < NB; ++q)
-        x[q] = cmul(v[q * 16 + i], SH::kPowTw && NB > 2 ? pw[q] : Mem::ldtw(tw + q * Ns + p));
+        x[q] = cmul(v[q * 16 + i], SH::kPowTw ? pw[q] : Mem::ldtw(tw + q * Ns + p));
       dft_radix<NB>(x);
 GB_UNROLL
       for (int q = 0; q < NB; ++q) put<SWAP>(d, og, (int)col0 + g, p + q * Ns, x[q]);

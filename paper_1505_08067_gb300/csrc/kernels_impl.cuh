@@ -360,8 +360,12 @@ __device__ __forceinline__ void stage_rows(cf* st, const cf* src, uint64_t* bar)
 
 template <class SH, int S, bool FIRST_EXCHANGE>
 __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
-                                               uint64_t* bar, const cf* next_src, int tid) {
+                                               uint64_t* bar, const cf* next_src, int tid,
+                                               cf (&fr)[16]) {
   using B = SplitBody<SH, DevMem>;
+  cf r[SH::kR / SH::radix(S + 1)];
+  if constexpr (SH::kPowTw) B::template roots<S>(r, d, tid);
+  if constexpr (SH::kPrefetchFused && S == SH::kExchanges - 1) B::fused_roots(fr, d, tid);
   B::template write_half<S, 0>(v, x, tid);
   __syncthreads();
   if constexpr (SH::kG == 1) {
@@ -377,19 +381,21 @@ __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& 
   B::template write_half<S, 1>(v, x, tid);
   __syncthreads();
   B::template read_half<S, 1>(v, x, tid);
-  B::template compute<S>(v, d, tid);
+  B::template compute<S>(v, d, tid, r);
   __syncthreads();
 }
 
 // The exchanges after stages 0 .. kExchanges-1; the first one starts the
-// copy of `next` into the staging buffer.
+// copy of `next` into the staging buffer, the last one loads the fused last
+// stage's twiddle roots `fr` (SplitBody::fused_roots).
 template <class SH>
 __device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
-                                            uint64_t* bar, const cf* next, int tid) {
+                                            uint64_t* bar, const cf* next, int tid,
+                                            cf (&fr)[16]) {
   static_assert(SH::kExchanges >= 1, "at least one exchange");
-  split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid);
-  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid);
-  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid);
+  split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid, fr);
+  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid, fr);
+  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid, fr);
 }
 
 // One tile per block (a contiguous transform, or G adjacent columns of a
@@ -435,10 +441,10 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     }
     parity ^= 1u;
     const cf* next = tile + step < d.tiles ? staged_src<SH>(in, d, tile + step) : nullptr;
-    cf v[SH::kR];
+    cf v[SH::kR], fr[16];
     if (d.conj_in) B::template first<true>(v, st, tid);
     else B::template first<false>(v, st, tid);
-    split_round<SH>(v, d, x, st, bar, next, tid);
+    split_round<SH>(v, d, x, st, bar, next, tid, fr);
     cf* o;
     int64_t col0;  // G == 1: the line (tile); else the first column of the tile
     if constexpr (SH::kG == 1) {
@@ -451,12 +457,15 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     }
     if constexpr (CONV) {
       B::conv_middle(v, d, col0, tid);
-      split_round<SH>(v, d, x, st, bar, nullptr, tid);
-      if constexpr (SH::kFuseLast) B::template store_fused<true>(v, d, o, col0, tid);
-      else B::template store<true>(v, d, o, col0, tid);
+      split_round<SH>(v, d, x, st, bar, nullptr, tid, fr);
+      if constexpr (SH::kFuseLast) {
+          B::template store_fused<true>(v, d, o, col0, tid, fr);
+      } else {
+        B::template store<true>(v, d, o, col0, tid);
+      }
     } else if constexpr (SH::kFuseLast) {
-      if (d.conj_out) B::template store_fused<true>(v, d, o, col0, tid);
-      else B::template store_fused<false>(v, d, o, col0, tid);
+      if (d.conj_out) B::template store_fused<true>(v, d, o, col0, tid, fr);
+      else B::template store_fused<false>(v, d, o, col0, tid, fr);
     } else {
       if (d.conj_out) B::template store<true>(v, d, o, col0, tid);
       else B::template store<false>(v, d, o, col0, tid);

@@ -300,7 +300,9 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       for (int t = 0; t < SH::kT; ++t) B::template write_half<S, 1>(reg(t), x.data(), t);
       for (int t = 0; t < SH::kT; ++t) {
         B::template read_half<S, 1>(reg(t), x.data(), t);
-        B::template compute<S>(reg(t), d, t);
+        cf r[SH::kR / SH::radix(S + 1)];
+        if constexpr (SH::kPowTw) B::template roots<S>(r, d, t);
+        B::template compute<S>(reg(t), d, t, r);
       }
     };
     auto round = [&]() {
@@ -314,15 +316,15 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, col0, t);
       round();
       for (int t = 0; t < SH::kT; ++t) {
-        if constexpr (SH::kFuseLast) B::template store_fused<true>(reg(t), d, o, col0, t);
+        if constexpr (SH::kFuseLast) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true>(reg(t), d, o, col0, t, fr); }
         else B::template store<true>(reg(t), d, o, col0, t);
       }
       continue;
     }
     for (int t = 0; t < SH::kT; ++t) {
       if constexpr (SH::kFuseLast) {
-        if (d.conj_out) B::template store_fused<true>(reg(t), d, o, col0, t);
-        else B::template store_fused<false>(reg(t), d, o, col0, t);
+        if (d.conj_out) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true>(reg(t), d, o, col0, t, fr); }
+        else { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<false>(reg(t), d, o, col0, t, fr); }
       } else {
         if (d.conj_out) B::template store<true>(reg(t), d, o, col0, t);
         else B::template store<false>(reg(t), d, o, col0, t);
