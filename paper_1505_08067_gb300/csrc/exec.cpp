@@ -43,8 +43,9 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
         launches[i] = l;
         continue;
       }
-      const bool want_staged = p.variant == 0 || p.variant == 2;
+      const bool want_staged = p.variant == 0 || p.variant == 2 || p.variant == 4;
       l.has_staged = want_staged && resolve_staged(l.d, l.lmap, l.smap, s.generic_only, &l.staged);
+      l.staged.tmap = l.staged.cols && p.variant != 4;
       if (l.has_staged) {
         e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
         if (e != cudaSuccess) return e;

@@ -189,7 +189,40 @@ struct PassDesc {
   float h_scale;
   int64_t h_lines, h_first;
   const cf* h;
+  // Column tiles of the staged kernel: when tmap_in_ok, the tile's input is
+  // copied by tensor-map (TMA) box loads.  tmap_in is a CUtensorMap encoded
+  // at launch over `in` viewed as rows of in.e complex64 elements (dims
+  // {in.e, rows}, box {G, min(L, 256)}); tile coordinates from
+  // tma_cols_coords.
+  int32_t tmap_in_ok;
+  alignas(64) unsigned char tmap_in[128];
 };
+
+// Can the column tiles of `d` be copied by tensor-map boxes over the input
+// viewed as rows of in.e elements?  Every tile offset outer*in.o + inner*in.t
+// must split into a row y and a column x with x + G <= in.e (in.o a multiple
+// of in.e, the inner tiles within one row), and x must be even (in.e and G
+// even) so that each box starts on a 16-byte boundary.  `rows`: the rows the
+// map spans.
+GB_HD bool cols_map_rows(const PassDesc& d, int64_t& rows) {
+  const int64_t e = d.in.e, L = int64_t(1) << d.logL;
+  if (d.G < 2 || d.G % 2 || d.in.g != 1 || d.in.t != d.G || e < d.G || e % 2 || d.in.o % e ||
+      d.tiles_inner < 1 || d.tiles_inner * d.G > e || d.tiles < 1 || d.tiles % d.tiles_inner ||
+      (L > 256 && L % 256))
+    return false;
+  rows = (d.tiles / d.tiles_inner - 1) * (d.in.o / e) + L;
+  return rows <= (int64_t(1) << 31);
+}
+
+// Tensor-map coordinates of column tile `tile`'s first element: its offset
+// outer*in.o + inner*in.t written as y*in.e + x (x the column, y the row).
+GB_HD void tma_cols_coords(const PassDesc& d, int64_t tile, int32_t& x, int32_t& y) {
+  const int64_t outer = tile / d.tiles_inner, inner = tile - outer * d.tiles_inner;
+  const int64_t off = outer * d.in.o + inner * d.in.t;
+  const int64_t row = off / d.in.e;
+  y = (int32_t)row;
+  x = (int32_t)(off - row * d.in.e);
+}
 
 GB_HD void thread_coords(int map, int tid, int T, int G, int& g, int& t) {
   if (map == MAP_ROWS) { g = tid / T; t = tid - g * T; }

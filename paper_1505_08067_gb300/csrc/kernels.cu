@@ -13,7 +13,12 @@
 //  twiddle_gen                   FP64 roots of unity rounded once to FP32
 //      (the precomputed twiddle table of Sec. 2.1).
 //  copy_kernel                   length-1 transforms (the DFT is the identity).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "kernels_impl.cuh"
 
@@ -73,7 +78,10 @@ const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool ge
 
 bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, StagedLaunch* s) {
   if (generic_only) return false;
-  if (lmap == MAP_COLS) return !d.conv && resolve_staged_cols_shape(d, lmap, smap, s);
+  if (lmap == MAP_COLS) {
+    s->cols = true;
+    return !d.conv && resolve_staged_cols_shape(d, lmap, smap, s);
+  }
   if (lmap == MAP_ROWS && smap == MAP_COLS) return !d.conv && resolve_staged_trans_shape(d, lmap, smap, s);
   if (lmap != MAP_ROWS || smap != MAP_ROWS) return false;
   return d.conv ? resolve_conv_staged_shape(d, s) : resolve_staged_shape(d, s);
@@ -93,10 +101,59 @@ cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count) {
   return cudaSuccess;
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map for the column tiles of pass `d` over `in`: `in` viewed as rows
+// of in.e complex64 elements, boxes of G columns x min(L, 256) rows.  False
+// (copy rows per thread instead) when the layout does not allow it
+// (cols_map_rows), `in` is not 16-byte aligned, or the encoder refuses.
+bool encode_cols_map(PassDesc& d, const void* in) {
+  const int64_t e = d.in.e, L = int64_t(1) << d.logL;
+  int64_t rows = 0;
+  if (!cols_map_rows(d, rows) || ((uintptr_t)in & 15)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  static_assert(sizeof(CUtensorMap) == sizeof(d.tmap_in), "tensor map size");
+  const cuuint64_t dims[2] = {(cuuint64_t)e, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)e * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)d.G, (cuuint32_t)(L < 256 ? L : 256)};
+  const cuuint32_t elem_strides[2] = {1, 1};
+  CUtensorMap m;
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(in), dims, strides, box,
+          elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  memcpy(d.tmap_in, &m, sizeof(m));
+  d.tmap_in_ok = 1;
+  return true;
+}
+
 cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* in, void* out,
                           cudaStream_t st) {
   KernelFn k = reinterpret_cast<KernelFn>(const_cast<void*>(s.fn));
   if (!k || s.grid < 1) return cudaErrorInvalidValue;
+  if (s.cols && s.tmap) {
+    PassDesc dm = d;
+    if (encode_cols_map(dm, in)) {
+      k<<<s.grid, s.block, s.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), dm);
+      return cudaGetLastError();
+    }
+  }
   k<<<s.grid, s.block, s.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), d);
   return cudaGetLastError();
 }

@@ -38,6 +38,8 @@ struct PassLaunch {
     int grid = 0, block = 0;
     int max_grid = 0;  // resident blocks per SM x SMs (persistent grid)
     size_t smem = 0;
+    bool cols = false;  // column tiles of a strided pass
+    bool tmap = false;  // column tiles: copy the input by tensor-map boxes when possible
   } staged;
 };
 
@@ -52,6 +54,9 @@ bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, St
 cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count);
 cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* in, void* out,
                           cudaStream_t st);
+// Encodes d.tmap_in for column tiles over `in` and sets d.tmap_in_ok; false
+// if the pass's layout or the driver does not allow it.
+bool encode_cols_map(PassDesc& d, const void* in);
 
 // Kernel for this pass shape: a compile-time specialisation when one matches,
 // else the generic kernel for (R, maps).

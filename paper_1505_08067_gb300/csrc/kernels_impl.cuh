@@ -358,23 +358,50 @@ __device__ __forceinline__ void stage_rows(cf* st, const cf* src, uint64_t* bar)
         : "memory");
 }
 
+// Column tiles, tensor-map form: one thread copies the tile's L rows of G
+// elements as boxes of min(L, 256) rows (d.tmap_in), landing in the same
+// interleaved layout as copy_rows (element a of column g at a*G + g); the
+// barrier expects this thread's one arrival with the tile's bytes.
+template <class SH>
+__device__ __forceinline__ void tma_cols(cf* st, const PassDesc& d, int64_t tile, uint64_t* bar) {
+  constexpr int BR = SH::kL < 256 ? SH::kL : 256;
+  static_assert(SH::kL % BR == 0 && SH::kG * 8 % 16 == 0, "whole boxes of 16-byte rows");
+  int32_t x, y;
+  tma_cols_coords(d, tile, x, y);
+  const uint32_t b = smem_u32(bar);
+  const uint64_t map = reinterpret_cast<uint64_t>(&d.tmap_in[0]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+               "r"((uint32_t)(SH::kL * SH::kG * 8))
+               : "memory");
+  for (int j = 0; j < SH::kL / BR; ++j)
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(st + j * BR * SH::kG)),
+        "l"(map), "r"(x), "r"(y + j * BR), "r"(b)
+        : "memory");
+}
+
 template <class SH, int S, bool FIRST_EXCHANGE>
 __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
-                                               uint64_t* bar, const cf* next_src, int tid,
-                                               cf (&fr)[16]) {
+                                               uint64_t* bar, const cf* in, int64_t next,
+                                               int tid, cf (&fr)[16]) {
   using B = SplitBody<SH, DevMem>;
   cf r[SH::kR / SH::radix(S + 1)];
   if constexpr (SH::kPowTw) B::template roots<S>(r, d, tid);
   if constexpr (SH::kPrefetchFused && S == SH::kExchanges - 1) B::fused_roots(fr, d, tid);
   B::template write_half<S, 0>(v, x, tid);
   __syncthreads();
-  if constexpr (SH::kG == 1) {
-    if (FIRST_EXCHANGE && tid == 0 && next_src)  // staging is free: every thread has read it
-      tma_load(st, next_src, SH::kL * 8, bar);
-  } else if constexpr (SH::kRowsIn) {
-    if (FIRST_EXCHANGE && tid == 0 && next_src) stage_rows<SH>(st, next_src, bar);
-  } else {
-    if (FIRST_EXCHANGE && next_src) copy_rows<SH>(st, next_src, d.in.e, bar, tid);
+  if (FIRST_EXCHANGE && next >= 0) {  // staging is free: every thread has read it
+    if constexpr (SH::kG == 1) {
+      if (tid == 0) tma_load(st, staged_src<SH>(in, d, next), SH::kL * 8, bar);
+    } else if constexpr (SH::kRowsIn) {
+      if (tid == 0) stage_rows<SH>(st, staged_src<SH>(in, d, next), bar);
+    } else if (d.tmap_in_ok) {
+      if (tid == 0) tma_cols<SH>(st, d, next, bar);
+    } else {
+      copy_rows<SH>(st, staged_src<SH>(in, d, next), d.in.e, bar, tid);
+    }
   }
   B::template read_half<S, 0>(v, x, tid);
   __syncthreads();
@@ -386,16 +413,16 @@ __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& 
 }
 
 // The exchanges after stages 0 .. kExchanges-1; the first one starts the
-// copy of `next` into the staging buffer, the last one loads the fused last
-// stage's twiddle roots `fr` (SplitBody::fused_roots).
+// copy of tile `next` (if >= 0) into the staging buffer, the last one loads
+// the fused last stage's twiddle roots `fr` (SplitBody::fused_roots).
 template <class SH>
 __device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
-                                            uint64_t* bar, const cf* next, int tid,
+                                            uint64_t* bar, const cf* in, int64_t next, int tid,
                                             cf (&fr)[16]) {
   static_assert(SH::kExchanges >= 1, "at least one exchange");
-  split_exchange<SH, 0, true>(v, d, x, st, bar, next, tid, fr);
-  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, nullptr, tid, fr);
-  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, nullptr, tid, fr);
+  split_exchange<SH, 0, true>(v, d, x, st, bar, in, next, tid, fr);
+  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, in, -1, tid, fr);
+  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, in, -1, tid, fr);
 }
 
 // One tile per block (a contiguous transform, or G adjacent columns of a
@@ -414,17 +441,19 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
   const int tid = threadIdx.x;
   const int64_t step = gridDim.x;
   int64_t tile = blockIdx.x;
-  // one arrival (the expect_tx of the bulk copy) for a contiguous transform,
-  // one per thread (its row copies) for a column tile
-  // one arrival (thread 0's expect_tx for bulk copies) for contiguous
-  // transforms and row tiles, one per thread (its row copies) for column tiles
-  if (tid == 0) mbar_init(bar, (SH::kG == 1 || SH::kRowsIn) ? 1 : SH::kT);
+  // one arrival (thread 0's expect_tx for bulk or tensor-map copies) for
+  // contiguous transforms, row tiles and column tiles with a tensor map; one
+  // per thread (its row copies) for other column tiles
+  const bool one_arrival = SH::kG == 1 || SH::kRowsIn || d.tmap_in_ok;
+  if (tid == 0) mbar_init(bar, one_arrival ? 1 : SH::kT);
   __syncthreads();
   if (tile < d.tiles) {  // uniform over the block
     if constexpr (SH::kG == 1) {
       if (tid == 0) tma_load(st, in + tile * SH::kL, SH::kL * 8, bar);
     } else if constexpr (SH::kRowsIn) {
       if (tid == 0) stage_rows<SH>(st, staged_src<SH>(in, d, tile), bar);
+    } else if (d.tmap_in_ok) {
+      if (tid == 0) tma_cols<SH>(st, d, tile, bar);
     } else {
       copy_rows<SH>(st, staged_src<SH>(in, d, tile), d.in.e, bar, tid);
     }
@@ -440,11 +469,11 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
       return;
     }
     parity ^= 1u;
-    const cf* next = tile + step < d.tiles ? staged_src<SH>(in, d, tile + step) : nullptr;
+    const int64_t next = tile + step < d.tiles ? tile + step : -1;
     cf v[SH::kR], fr[16];
     if (d.conj_in) B::template first<true>(v, st, tid);
     else B::template first<false>(v, st, tid);
-    split_round<SH>(v, d, x, st, bar, next, tid, fr);
+    split_round<SH>(v, d, x, st, bar, in, next, tid, fr);
     cf* o;
     int64_t col0;  // G == 1: the line (tile); else the first column of the tile
     if constexpr (SH::kG == 1) {
@@ -457,7 +486,7 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     }
     if constexpr (CONV) {
       B::conv_middle(v, d, col0, tid);
-      split_round<SH>(v, d, x, st, bar, nullptr, tid, fr);
+      split_round<SH>(v, d, x, st, bar, in, -1, tid, fr);
       if constexpr (SH::kFuseLast) {
           B::template store_fused<true>(v, d, o, col0, tid, fr);
       } else {

@@ -210,7 +210,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   }
   if (o.radix && (o.radix < 2 || o.radix > 16 || !is_pow2(o.radix)))
     { fail(FFT_ERR_INVALID_ARG, "radix option must be 2, 4, 8 or 16"); return; }
-  if (o.variant < 0 || o.variant > 3) { fail(FFT_ERR_INVALID_ARG, "variant must be 0..3"); return; }
+  if (o.variant < 0 || o.variant > 4) { fail(FFT_ERR_INVALID_ARG, "variant must be 0..4"); return; }
   if (o.epilogue < 0 || o.epilogue > 4) { fail(FFT_ERR_INVALID_ARG, "epilogue must be 0..4"); return; }
   if (o.tile < 0 || o.tile > 1024 || (o.tile && !is_pow2(o.tile)))
     { fail(FFT_ERR_INVALID_ARG, "tile option must be a power of two <= 1024"); return; }

@@ -280,12 +280,26 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       dst = outer * d.out.o + inner * d.out.t;
       col0 = inner * SH::kG;
     }
+    // column tiles the GPU copies by tensor-map boxes: element (y + a, x + c)
+    // of the map, which must lie inside its {in.e, rows} extent (TMA would
+    // fill zeros outside it) and be the element the row copy reads
+    int64_t map_rows = 0;
+    const bool use_map = SH::kG > 1 && !SH::kRowsIn && cols_map_rows(d, map_rows);
+    int32_t mx = 0, my = 0;
+    if (use_map) tma_cols_coords(d, tile, mx, my);
     for (int a = 0; a < SH::kL; ++a)
       for (int c = 0; c < SH::kG; ++c) {
-        if constexpr (SH::kRowsIn)  // one bulk copy per row, pitched
+        if constexpr (SH::kRowsIn) {  // one bulk copy per row, pitched
           st[c * (SH::kL + SH::kRowPad) + a] = CheckMem::ldg(in, src + c * SH::kL + a);
-        else
+        } else if (use_map) {
+          const int64_t row = (int64_t)my + a, col = (int64_t)mx + c;
+          if (row >= map_rows || col >= d.in.e || mx % 2 ||
+              row * d.in.e + col != src + c + a * d.in.e)
+            err("tensor-map box outside the map or off the row copy", row * d.in.e + col);
+          st[a * SH::kG + c] = CheckMem::ldg(in, row * d.in.e + col);
+        } else {
           st[a * SH::kG + c] = CheckMem::ldg(in, src + (SH::kG == 1 ? a : c + a * d.in.e));
+        }
       }
     for (int t = 0; t < SH::kT; ++t) {
       if (d.conj_in) B::template first<true>(reg(t), st.data(), t);

@@ -282,10 +282,12 @@ def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
                                               ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 3}),
                                               ((2 ** 22,), 1, {"split_log2": 11, "epilogue": 4}),
                                               ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 4})])
-def test_staged_columns_and_unaligned_fallback(gb, oracle, shape, batch, opts):
+@pytest.mark.parametrize("variant", [2, 4])
+def test_staged_columns_and_unaligned_fallback(gb, oracle, shape, batch, opts, variant):
     """Column passes (2D, four-step first passes with G = 16 / 8 / 4 columns)
-    run the staged column kernel (variant 2) from a 16-byte-aligned source and
-    the register kernel from an 8-byte-aligned one; both match the oracle."""
+    run the staged column kernel from a 16-byte-aligned source (variant 2:
+    tiles copied by tensor-map boxes; 4: by per-thread 16-byte row copies) and
+    the register kernel from an 8-byte-aligned one; all match the oracle."""
     n = int(np.prod(shape))
     x_np = synth.uniform(9400 + int(np.log2(n)), batch, n)
     buf = torch.zeros(batch * n + 1, dtype=torch.complex64, device="cuda")
@@ -294,7 +296,7 @@ def test_staged_columns_and_unaligned_fallback(gb, oracle, shape, batch, opts):
         xin = buf[shift:shift + batch * n]
         xin.copy_(torch.from_numpy(x_np.reshape(-1)))
         out = torch.empty(batch * n, dtype=torch.complex64, device="cuda")
-        with gb.Plan(dims, batch, variant=2, **opts) as p:
+        with gb.Plan(dims, batch, variant=variant, **opts) as p:
             st = torch.cuda.current_stream().cuda_stream
             gb.fft_execute(p.handle, xin.data_ptr(), out.data_ptr(), st)
             gb.fft_plan_sync_status(p.handle, st)
