@@ -355,7 +355,8 @@ def ours_serve(args, rank: int, world: int) -> None:
         xin[off:off + chunk.numel()].copy_(chunk)
     ring_elems = 6 << 30                                               # 48 GiB of outputs
     yout = torch.empty(ring_elems, dtype=torch.complex64, device=dev)
-    srv = gbfft.fft_server_create(memory_budget_bytes=64 * 10 ** 9, streams=args.streams)
+    srv = gbfft.fft_server_create(memory_budget_bytes=64 * 10 ** 9, streams=args.streams,
+                                  strict_order=int(args.strict_order))
     # warm the plans of every key outside the measured stream
     keys = sorted(set(zip(logn.tolist(), dirs.tolist(), prec.tolist())))
     for lg, d, p in keys:
@@ -435,6 +436,7 @@ def ours_serve(args, rank: int, world: int) -> None:
                        "jobs": njobs, "offered_load_frac_of_hbm": args.load,
                        "offered_jobs_per_s": rate, "streams": args.streams,
                        "budget_bytes": 64 * 10 ** 9, "mean_job_elements": float(elems.mean()),
+                       "admission": "strict arrival order" if args.strict_order else "backfilling",
                        "tc_share": float((prec > 0).mean())},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max())},
@@ -442,9 +444,10 @@ def ours_serve(args, rank: int, world: int) -> None:
             "submit_s": t_sub, "wall_s": wall,
             "achieved_alg_gbs": float(alg_bytes.sum() / wall / 1e9),
             "server": {k: stats[k] - base_stats.get(k, 0) if k in ("launches", "groups",
-                       "coalesced_jobs", "completed") else stats[k]
+                       "coalesced_jobs", "completed", "backfilled_jobs") else stats[k]
                        for k in ("launches", "groups", "coalesced_jobs", "completed",
-                                 "peak_bytes_in_flight", "workspace_allocations")}}))
+                                 "backfilled_jobs", "peak_bytes_in_flight",
+                                 "workspace_allocations")}}))
 
 
 def ours_compress(args, rank: int, world: int) -> None:
@@ -740,6 +743,8 @@ def main() -> None:
     ap.add_argument("--load", type=float, default=0.5,
                     help="serve workload: offered algorithmic bytes/s as a fraction of HBM")
     ap.add_argument("--streams", type=int, default=4, help="serve workload: server streams")
+    ap.add_argument("--strict-order", action="store_true",
+                    help="serve workload: admit strictly in arrival order (no backfilling)")
     ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve", "small",
                                            "sar_compress"],
                     default="sweep",

@@ -306,9 +306,13 @@ GBFFT_API fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int directi
  * running (input + output + workspace) fit the memory budget, coalesces every
  * waiting job of the same shape, direction and precision into one launch (for
  * batched 1D single-pass FP32 shapes: one kernel over all their buffers),
- * spreads launches over several streams so they overlap, and keeps plans and
- * twiddle tables resident per shape.  Jobs that arrive while others run are
- * admitted as soon as memory frees up.
+ * spreads launches over several streams so they overlap (each on the stream
+ * whose queued work is estimated to end first), and keeps plans and twiddle
+ * tables resident per shape.  Jobs that arrive while others run are admitted
+ * as soon as memory frees up.  When the oldest waiting job does not fit, later
+ * jobs that fit may start first if, by an estimate of run times from the bytes
+ * each job moves, they cannot delay it (backfilling; strict_order turns this
+ * off).
  */
 typedef struct fft_server_s* fft_server_t;
 
@@ -318,7 +322,8 @@ typedef struct {
   int max_group;              /* most jobs coalesced into one group, default 256 */
   int max_running;            /* most groups on the GPU at once, default 4 x streams */
   int fail_workspace_alloc;   /* testing: workspace allocations fail (host-side fault) */
-  int reserved[7];
+  int strict_order;           /* 1: admit strictly in arrival order (no backfilling) */
+  int reserved[6];
 } fft_server_options_t;
 
 typedef struct {
@@ -347,6 +352,7 @@ typedef struct {
   double p50_ms, p99_ms, mean_ms, max_ms; /* latency of completed jobs (the most recent 2^20) */
   double wall_s;            /* first submit -> last completion */
   double gflops;            /* 5 N log2 N of completed jobs / wall_s */
+  uint64_t backfilled_jobs; /* jobs admitted ahead of an older waiting job */
 } fft_server_stats_t;
 
 /* Start a server on the current device (options may be NULL). */

@@ -5,10 +5,11 @@
 //   1. polls the completion events of running groups, marks their jobs done
 //      (latency = completion seen - submit) and frees their bytes;
 //   2. asks the scheduler (scheduler.h) for groups that fit the memory budget
-//      and launches each on the next of several streams: jobs of one
-//      contiguous single-pass FP32 shape in one coalesced kernel launch (job
-//      table in the kernel parameters), other jobs as their plan's passes, one
-//      after the other, on the group's stream;
+//      (backfilling by estimated run times unless strict order is asked for)
+//      and launches each on the stream whose queued work is estimated to end
+//      first: jobs of one contiguous single-pass FP32 shape in one coalesced
+//      kernel launch (job table in the kernel parameters), other jobs as their
+//      plan's passes, one after the other, on the group's stream;
 //   3. sleeps briefly when nothing changed.
 // Plans (twiddle tables) stay resident per job key; multi-pass workspaces come
 // from a pool and are reused.  Groups on different streams overlap on the
@@ -41,6 +42,10 @@ using namespace gbfft;
 namespace {
 
 constexpr uint32_t kServerMagic = 0x53525646u;
+// Run-time estimate of a job for the scheduler: its algorithmic bytes (16 per
+// element per pass) at an effective rate, plus a launch overhead.
+constexpr double kEstBytesPerS = 3.0e12;
+constexpr double kEstLaunchS = 6e-6;
 constexpr size_t kLatencyWindow = size_t(1) << 20;  // latency samples kept for p50 / p99
 
 double now_s() {
@@ -94,7 +99,7 @@ struct fft_server_s {
   bool stop = false;
   bool paused = false;  // admissions held (fft_server_pause)
   std::vector<cudaStream_t> streams;
-  int next_stream = 0;
+  std::vector<double> stream_free;  // estimated time each stream's queued work ends
   std::map<JobKey, PlanEntry*, KeyLess> plans;
   std::unordered_map<uint64_t, JobRec> jobs;
   std::vector<Running> running;
@@ -108,8 +113,8 @@ struct fft_server_s {
   double first_submit = 0, last_done = 0, flops = 0;
   size_t ws_allocs = 0;
 
-  fft_server_s(size_t budget, int max_group, size_t group_bytes)
-      : sched(budget, max_group, group_bytes) {}
+  fft_server_s(size_t budget, int max_group, size_t group_bytes, bool backfill)
+      : sched(budget, max_group, group_bytes, backfill) {}
 };
 
 namespace {
@@ -239,8 +244,11 @@ bool launch_group(fft_server_t s, Running& r) {
     fail_all(pst);
     return false;
   }
-  cudaStream_t st = s->streams[s->next_stream];
-  s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+  size_t si = 0;  // the stream whose queued work is estimated to end first
+  for (size_t i = 1; i < s->streams.size(); ++i)
+    if (s->stream_free[i] < s->stream_free[si]) si = i;
+  cudaStream_t st = s->streams[si];
+  s->stream_free[si] = std::max(s->stream_free[si], t) + g.cost;
   cudaError_t e = cudaSuccess;
   if (pe->groupable && g.jobs.size() > 1) {
     // one coalesced launch per kMaxGroup jobs
@@ -342,7 +350,8 @@ void worker_loop(fft_server_t s) {
     if (progress) s->cv_done.notify_all();
     // 2. launches
     SchedGroup g;
-    while (!s->paused && (int)s->running.size() < s->opt.max_running && s->sched.next(g)) {
+    while (!s->paused && (int)s->running.size() < s->opt.max_running &&
+           s->sched.next(g, now_s())) {
       Running r;
       r.group = g;
       if (launch_group(s, r)) {
@@ -391,7 +400,7 @@ fft_status_t fft_server_create(fft_server_t* server, const fft_server_options_t*
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
     return set_error(FFT_ERR_CUDA, "cudaGetDeviceProperties");
   fft_server_t s = new (std::nothrow) fft_server_s(o.memory_budget_bytes, o.max_group,
-                                                    o.memory_budget_bytes);
+                                                    o.memory_budget_bytes, o.strict_order == 0);
   if (!s) return set_error(FFT_ERR_OUT_OF_MEMORY, "host allocation of the server failed");
   s->opt = o;
   s->device = dev;
@@ -406,6 +415,7 @@ fft_status_t fft_server_create(fft_server_t* server, const fft_server_options_t*
       return set_error(FFT_ERR_CUDA, "stream creation");
     }
     s->streams.push_back(st);
+    s->stream_free.push_back(0.0);
   }
   s->worker = std::thread(worker_loop, s);
   *server = s;
@@ -439,6 +449,7 @@ fft_status_t fft_server_submit(fft_server_t s, const fft_job_t* job, uint64_t* t
   sj.groupable = probe.passes.size() == 1 && probe.passes[0].batch_is_tiles &&
                  probe.passes[0].tc_prec == 0 && job->dims == 1;
   sj.t_submit = now_s();
+  sj.cost = (double)e * 16.0 * (double)probe.passes.size() / kEstBytesPerS + kEstLaunchS;
   if (!s->sched.submit(sj))
     return set_error(FFT_ERR_OUT_OF_MEMORY, "job needs more bytes than the server's budget");
   JobRec rec;
@@ -505,6 +516,7 @@ fft_status_t fft_server_stats(fft_server_t s, fft_server_stats_t* out) {
   out->peak_bytes_in_flight = s->sched.peak_in_flight();
   out->budget_bytes = s->sched.budget();
   out->workspace_allocations = s->ws_allocs;
+  out->backfilled_jobs = s->sched.backfilled();
   std::vector<double> l = s->latencies;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());

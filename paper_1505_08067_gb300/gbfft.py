@@ -57,7 +57,8 @@ class fft_filter_t(ctypes.Structure):
 class fft_server_options_t(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int),
                 ("max_group", ctypes.c_int), ("max_running", ctypes.c_int),
-                ("fail_workspace_alloc", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("fail_workspace_alloc", ctypes.c_int), ("strict_order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class fft_job_t(ctypes.Structure):
@@ -79,7 +80,8 @@ class fft_server_stats_t(ctypes.Structure):
                 ("peak_bytes_in_flight", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("wall_s", ctypes.c_double), ("gflops", ctypes.c_double)]
+                ("wall_s", ctypes.c_double), ("gflops", ctypes.c_double),
+                ("backfilled_jobs", ctypes.c_uint64)]
 
 
 _lib = None
@@ -439,9 +441,10 @@ class ConvPlan(Plan):
 # ----------------------------------------------------------------- serving --
 
 def fft_server_create(memory_budget_bytes: int = 0, streams: int = 0, max_group: int = 0,
-                      max_running: int = 0, fail_workspace_alloc: int = 0) -> int:
+                      max_running: int = 0, fail_workspace_alloc: int = 0,
+                      strict_order: int = 0) -> int:
     o = fft_server_options_t(memory_budget_bytes, streams, max_group, max_running,
-                             fail_workspace_alloc)
+                             fail_workspace_alloc, strict_order)
     h = _vp()
     _check(load().fft_server_create(ctypes.byref(h), ctypes.byref(o)))
     return h.value

@@ -26,7 +26,7 @@ def load():
     return _lib
 
 
-def simulate(key, nbytes, arrive, dur, groupable, budget, max_group=256):
+def simulate(key, nbytes, arrive, dur, groupable, budget, max_group=256, backfill=False):
     n = len(key)
     a = lambda v, t: np.ascontiguousarray(np.asarray(v), dtype=t)
     key, arrive, dur, grp = a(key, np.int32), a(arrive, np.int32), a(dur, np.int32), a(groupable, np.int32)
@@ -35,7 +35,8 @@ def simulate(key, nbytes, arrive, dur, groupable, budget, max_group=256):
     peak = ctypes.c_uint64()
     p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     steps = load().sched_simulate(n, p(key), p(nbytes), p(arrive), p(dur), p(grp),
-                                  ctypes.c_uint64(budget), max_group, p(launch), p(gid), p(done),
+                                  ctypes.c_uint64(budget), max_group, int(backfill), p(launch),
+                                  p(gid), p(done),
                                   ctypes.byref(peak), p(rej))
     return dict(steps=steps, launch=launch, group=gid, done=done, rejected=rej.astype(bool),
                 peak=peak.value)

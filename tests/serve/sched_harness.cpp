@@ -1,8 +1,9 @@
 // Test infrastructure: drives the serving scheduler (csrc/scheduler.h) with a
 // simulated device in discrete time steps.  Jobs arrive at given steps and run
-// for given numbers of steps once launched; a group runs as long as its
-// longest job.  Reports when each job launched, which group it joined, the
-// peak bytes in flight and which jobs were rejected.
+// for given numbers of steps once launched (the scheduler's cost estimate is
+// that exact duration); a group runs its jobs one after another.  Reports
+// when each job launched, which group it joined, when it finished, the peak
+// bytes in flight and which jobs were rejected.
 #include <stdint.h>
 
 #include <vector>
@@ -13,9 +14,9 @@ using namespace gbfft;
 
 extern "C" int sched_simulate(int n, const int* key, const uint64_t* bytes, const int* arrive,
                               const int* dur, const int* groupable, uint64_t budget, int max_group,
-                              int* launch_step, int* group_id, int* done_step,
+                              int backfill, int* launch_step, int* group_id, int* done_step,
                               uint64_t* peak_in_flight, int* rejected) {
-  Scheduler s(budget, max_group, budget);
+  Scheduler s(budget, max_group, budget, backfill != 0);
   struct Run {
     SchedGroup g;
     int end;
@@ -49,6 +50,7 @@ extern "C" int sched_simulate(int n, const int* key, const uint64_t* bytes, cons
       j.key.n0 = key[next_job];
       j.bytes = (size_t)bytes[next_job];
       j.groupable = groupable[next_job] != 0;
+      j.cost = dur[next_job];
       if (!s.submit(j)) {
         rejected[next_job] = 1;
         ++finished;
@@ -57,12 +59,12 @@ extern "C" int sched_simulate(int n, const int* key, const uint64_t* bytes, cons
     }
     // launches
     SchedGroup g;
-    while (s.next(g)) {
+    while (s.next(g, step)) {
       int end = step;
       for (auto& j : g.jobs) {
         launch_step[j.id] = step;
         group_id[j.id] = gid;
-        end = end > step + dur[j.id] ? end : step + dur[j.id];
+        end += dur[j.id];
       }
       if (s.in_flight() > budget) return -1;  // accounting broke the budget
       running.push_back(Run{g, end});

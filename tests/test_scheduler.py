@@ -1,8 +1,9 @@
 """Serving policy (csrc/scheduler.h) on a simulated device, CPU only:
-admission never exceeds the memory budget, the oldest waiting job always goes
-first, only same-key jobs share a launch, jobs that arrive while others run
-are admitted as memory frees up, and jobs larger than the budget are
-rejected."""
+admission never exceeds the memory budget, in strict arrival order the oldest
+waiting job always goes first, only same-key jobs share a launch, jobs that
+arrive while others run are admitted as memory frees up, jobs larger than the
+budget are rejected, and backfilled jobs never delay the waiting head when
+the run-time estimates are exact."""
 import numpy as np
 
 from serve import sched
@@ -70,3 +71,41 @@ def test_too_large_is_rejected():
     r = sched.simulate([0, 0], [16 << 30, 1 << 20], [0, 0], [1, 1], [1, 1], 8 << 30)
     assert r["rejected"].tolist() == [True, False]
     assert r["done"][1] >= 0
+
+
+def test_backfill_never_delays_the_head():
+    """Backfilling with exact run-time estimates.  Job 0 (5 GB, 100 steps) runs;
+    job 1 (7 GB) waits for it: its reservation is step 100 with 3 GB left over
+    next to it.  Job 2 (4 GB, 200 steps) fits now but would still hold 4 GB at
+    step 100, more than the 3 GB left over: it waits.  Job 3 (4 GB, 50 steps)
+    ends before step 100: it starts at once.  Job 4 (2 GB, 500 steps) fits in
+    the 3 GB next to job 1: it starts as soon as job 3's bytes free up.  Job 1
+    still starts at step 100, exactly as in strict arrival order."""
+    G = 1 << 30
+    key = [0, 1, 2, 3, 4]
+    nbytes = [5 * G, 7 * G, 4 * G, 4 * G, 2 * G]
+    arrive = [0, 1, 2, 3, 4]
+    dur = [100, 10, 200, 50, 500]
+    grp = [0] * 5
+    fifo = sched.simulate(key, nbytes, arrive, dur, grp, 10 * G, backfill=False)
+    bf = sched.simulate(key, nbytes, arrive, dur, grp, 10 * G, backfill=True)
+    assert fifo["launch"].tolist() == [0, 100, 110, 110, 110]
+    assert bf["launch"].tolist() == [0, 100, 110, 3, 53]
+    assert bf["peak"] <= 10 * G and fifo["peak"] <= 10 * G
+
+
+def test_backfill_random_streams():
+    """Random streams under a tight budget: with backfilling every job still
+    completes, the budget holds, only same-key jobs share a launch, and the
+    mean wait for a launch is no longer than in strict arrival order."""
+    for seed in (11, 12, 13, 14):
+        key, nbytes, arrive, dur, grp = _random_stream(seed)
+        budget = 2 << 30
+        fifo = sched.simulate(key, nbytes, arrive, dur, grp, budget, backfill=False)
+        bf = sched.simulate(key, nbytes, arrive, dur, grp, budget, backfill=True)
+        assert bf["steps"] > 0 and bf["peak"] <= budget
+        assert (bf["done"] >= 0).all() and (bf["launch"] >= arrive).all()
+        for g in np.unique(bf["group"]):
+            members = np.where(bf["group"] == g)[0]
+            assert len(set(key[members])) == 1
+        assert np.mean(bf["launch"] - arrive) <= np.mean(fifo["launch"] - arrive)

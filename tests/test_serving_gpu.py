@@ -96,3 +96,44 @@ def test_budget_rejection_and_fault_injection(gb):
             gb.fft_server_submit(srv, 12, 1, -1, 0, x.data_ptr(), y.data_ptr())
     finally:
         gb.fft_server_destroy(srv)
+
+
+@pytest.mark.parametrize("strict", [0, 1])
+def test_backfill_small_job_passes_a_blocked_head(gb, oracle, strict):
+    """Two two-pass jobs that do not fit the budget together and a small job
+    behind them, admitted as one held burst: the second large job waits for
+    the first one's memory.  With backfilling the small job starts at once
+    (its estimated run time ends long before the first job frees its bytes);
+    in strict arrival order it waits behind the second job.  Every result
+    matches the same job run alone."""
+    specs = [(2 ** 20, 16), (2 ** 20, 16), (1024, 8)]
+    bufs = []
+    for k, (n, b) in enumerate(specs):
+        x = torch.from_numpy(synth.uniform(13000 + k, b, n)).cuda()
+        bufs.append((x, torch.full_like(x, float("nan"))))
+    torch.cuda.synchronize()
+    srv = gb.fft_server_create(memory_budget_bytes=600 << 20, streams=4, strict_order=strict)
+    try:
+        gb.fft_server_pause(srv, True)
+        tickets = [gb.fft_server_submit(srv, n, b, -1, 0, x.data_ptr(), y.data_ptr())
+                   for (n, b), (x, y) in zip(specs, bufs)]
+        gb.fft_server_pause(srv, False)
+        results = [gb.fft_server_wait(srv, t, 60.0) for t in tickets]
+        stats = gb.fft_server_stats(srv)
+    finally:
+        gb.fft_server_destroy(srv)
+    assert all(r["status"] == 0 for r in results)
+    assert stats["peak_bytes_in_flight"] <= 600 << 20
+    if strict:
+        assert stats["backfilled_jobs"] == 0
+        assert results[2]["queue_ms"] >= results[1]["queue_ms"]
+    else:
+        assert stats["backfilled_jobs"] >= 1
+        assert results[2]["queue_ms"] < results[1]["queue_ms"]
+    torch.cuda.synchronize()
+    for (n, b), (x, y) in zip(specs, bufs):
+        with gb.Plan(n, b, -1) as p:
+            alone = p.execute(x)
+            torch.cuda.synchronize()
+        assert np.max(oracle.rel_l2(y.cpu().numpy().reshape(b, n),
+                                    alone.cpu().numpy().reshape(b, n))) <= TOL[0](n)
