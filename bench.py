@@ -250,7 +250,9 @@ def ours_other(args, rank: int, world: int) -> None:
     if args.workload == "sar":
         x = torch.from_numpy(synth.sar_frame(31).reshape(-1)).to(dev)
     elif args.workload == "tc":
-        x = torch.from_numpy(synth.buried_tone(4, E // 4096, 4096)[0].reshape(-1)).to(dev)
+        xt, tone_bins = synth.buried_tone(4, E // 4096, 4096)
+        x = torch.from_numpy(xt.reshape(-1)).to(dev)
+        del xt
     else:
         x = torch.from_numpy(synth.uniform(3, 1, E)[0]).to(dev)
     y = torch.empty_like(x)
@@ -302,19 +304,50 @@ def ours_other(args, rank: int, world: int) -> None:
             "passes": passes, "gbs": round(16.0 * passes * e / (t * 1e-3) / 1e9, 1),
             "frac": round(16.0 * passes * e / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
             "tuned": _tuned(plans[key])}
+    accuracy = _tc_accuracy(gbfft, x, tone_bins) if args.workload == "tc" else None
     if rank == 0:
         tot_bytes = sum(16.0 * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
-        print(json.dumps({
+        line = {
             "metric": METRIC, "value": world * flops * args.steps / (ms * 1e-3) / 1e9,
             "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "dtype": "f32", "data": "synthetic", "config": {"workload": desc},
+            "dtype": "f32+tc" if args.workload == "tc" else "f32", "data": "synthetic",
+            "config": {"workload": desc},
             "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
                          "achieved": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9, 1),
                          "frac": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
-            "per_item": per}))
+            "per_item": per}
+        if accuracy:
+            line["accuracy_vs_fp32"] = accuracy
+        print(json.dumps(line))
     for p in plans.values():
         p.close()
+
+
+def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: float = 1e-3):
+    """Error of each tensor-core class on the first `count` transforms of the
+    tone-bearing input, against this library's FP32 path (itself 2-5e-7 from the
+    FP64 oracle in the parity tests): max and mean relative L2 per transform, and
+    the error at each transform's tone bin relative to the tone's exact
+    contribution n * amplitude."""
+    import numpy as np
+    import torch
+
+    xs = x[:count * n]
+    outs = {}
+    for prec, name in ((0, "fp32"), (1, "tc_fp16"), (2, "tc_bf16"), (3, "tc_bf16x3")):
+        with gbfft.Plan(n, count, -1, prec) as p:
+            outs[name] = p.execute(xs).cpu().numpy().reshape(count, n).astype(np.complex128)
+            torch.cuda.synchronize()
+    ref = outs.pop("fp32")
+    k0 = np.asarray(bins[:count])
+    acc = {}
+    for name, y in outs.items():
+        rel = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        tone = np.abs(y[np.arange(count), k0] - ref[np.arange(count), k0]) / (n * amplitude)
+        acc[name] = {"rel_l2_max": float(rel.max()), "rel_l2_mean": float(rel.mean()),
+                     "tone_err_max": float(tone.max()), "transforms": count}
+    return acc
 
 
 def ours_serve(args, rank: int, world: int) -> None:

@@ -11,8 +11,10 @@
 //      kernel launch (job table in the kernel parameters), other jobs as their
 //      plan's passes, one after the other, on the group's stream;
 //   3. sleeps briefly when nothing changed.
-// Plans (twiddle tables) stay resident per job key; multi-pass workspaces come
-// from a pool and are reused.  Groups on different streams overlap on the
+// Plans (twiddle tables) stay resident per job key; multi-pass workspaces are
+// stream-ordered allocations from the server's own memory pool (allocated on
+// the group's stream before its passes, freed on it after them: no device-wide
+// synchronisation, memory reused once the freeing stream has passed it).  Groups on different streams overlap on the
 // device.  Everything a running group holds counts against the budget.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -82,7 +84,6 @@ struct JobRec {
 struct Running {
   SchedGroup group;
   cudaEvent_t done = nullptr;
-  std::vector<std::pair<void*, size_t>> workspaces;
 };
 
 }  // namespace
@@ -103,8 +104,7 @@ struct fft_server_s {
   std::map<JobKey, PlanEntry*, KeyLess> plans;
   std::unordered_map<uint64_t, JobRec> jobs;
   std::vector<Running> running;
-  std::multimap<size_t, void*> ws_pool;  // free workspaces by size class
-  size_t pool_bytes = 0;
+  cudaMemPool_t ws_pool = nullptr;  // stream-ordered workspace allocations
   std::vector<cudaEvent_t> free_events;
   uint64_t next_id = 1;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, coalesced = 0;
@@ -174,55 +174,25 @@ PlanEntry* plan_for(fft_server_t s, const JobKey& k, fft_status_t* st) {
   return pe;
 }
 
-// Workspaces come in power-of-two size classes (at most 2x the request, and the
-// budget accounts for the class size).  Freed workspaces stay pooled up to
-// kPoolCap bytes; beyond that they are released.  If an allocation fails, the
-// pool is released and the allocation retried once.
-constexpr size_t kPoolCap = (size_t)16 << 30;
-
+// Workspaces come in power-of-two size classes (at most 2x the request; the
+// budget accounts for the class size), allocated in stream order from the
+// server's pool, which keeps its memory (release threshold: never) so that
+// steady-state allocations map no new pages.
 size_t ws_class(size_t bytes) {
   size_t c = 1 << 20;
   while (c < bytes) c <<= 1;
   return c;
 }
 
-void ws_flush(fft_server_t s) {
-  for (auto& kv : s->ws_pool) cudaFree(kv.second);
-  s->ws_pool.clear();
-  s->pool_bytes = 0;
-}
-
-void* ws_get(fft_server_t s, size_t bytes) {
-  const size_t c = ws_class(bytes);
-  auto it = s->ws_pool.find(c);
-  if (it != s->ws_pool.end()) {
-    void* p = it->second;
-    s->ws_pool.erase(it);
-    s->pool_bytes -= c;
-    return p;
-  }
+void* ws_get(fft_server_t s, size_t bytes, cudaStream_t st) {
   if (s->opt.fail_workspace_alloc) return nullptr;  // host-side fault injection
   void* p = nullptr;
-  if (cudaMalloc(&p, c) != cudaSuccess) {
+  if (cudaMallocFromPoolAsync(&p, ws_class(bytes), s->ws_pool, st) != cudaSuccess) {
     cudaGetLastError();
-    ws_flush(s);
-    if (cudaMalloc(&p, c) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
+    return nullptr;
   }
   ++s->ws_allocs;
   return p;
-}
-
-void ws_put(fft_server_t s, void* p, size_t bytes) {
-  const size_t c = ws_class(bytes);
-  if (s->pool_bytes + c > kPoolCap) {
-    cudaFree(p);
-    return;
-  }
-  s->ws_pool.emplace(c, p);
-  s->pool_bytes += c;
 }
 
 // Launch one admitted group on a stream.  Returns false if it could not.
@@ -278,14 +248,14 @@ bool launch_group(fft_server_t s, Running& r) {
       void* ws = nullptr;
       const size_t wsb = (size_t)pe->work_per_entry * 8 * (size_t)rec.job.batch;
       if (wsb) {
-        ws = ws_get(s, wsb);
+        ws = ws_get(s, wsb, st);
         if (!ws) {
           e = cudaErrorMemoryAllocation;
           break;
         }
-        r.workspaces.emplace_back(ws, wsb);
       }
       e = enqueue_passes(pe->spec, pe->launches, rec.job.in, rec.job.out, ws, 0, rec.job.batch, st);
+      if (ws) cudaFreeAsync(ws, st);  // after the passes, in stream order
       ++s->launches;
       if (e != cudaSuccess) break;
     }
@@ -293,8 +263,6 @@ bool launch_group(fft_server_t s, Running& r) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     fail_all(e == cudaErrorMemoryAllocation ? FFT_ERR_OUT_OF_MEMORY : FFT_ERR_CUDA);
-    for (auto& w : r.workspaces) ws_put(s, w.first, w.second);
-    r.workspaces.clear();
     return false;
   }
   if (s->free_events.empty()) {
@@ -342,7 +310,6 @@ void worker_loop(fft_server_t s) {
       if (q != cudaSuccess) cudaGetLastError();
       s->last_done = t;
       s->sched.finished(r.group);
-      for (auto& w : r.workspaces) ws_put(s, w.first, w.second);
       s->free_events.push_back(r.done);
       s->running.erase(s->running.begin() + i);
       progress = true;
@@ -417,6 +384,18 @@ fft_status_t fft_server_create(fft_server_t* server, const fft_server_options_t*
     s->streams.push_back(st);
     s->stream_free.push_back(0.0);
   }
+  cudaMemPoolProps pp{};
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = dev;
+  if (cudaMemPoolCreate(&s->ws_pool, &pp) != cudaSuccess) {
+    cudaGetLastError();
+    for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+    delete s;
+    return set_error(FFT_ERR_CUDA, "workspace memory pool creation");
+  }
+  uint64_t keep = ~uint64_t(0);
+  cudaMemPoolSetAttribute(s->ws_pool, cudaMemPoolAttrReleaseThreshold, &keep);
   s->worker = std::thread(worker_loop, s);
   *server = s;
   return FFT_OK;
@@ -554,11 +533,9 @@ fft_status_t fft_server_destroy(fft_server_t s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
-  for (Running& r : s->running) {
-    for (auto& w : r.workspaces) cudaFree(w.first);
+  for (Running& r : s->running)
     if (r.done) cudaEventDestroy(r.done);
-  }
-  ws_flush(s);
+  if (s->ws_pool) cudaMemPoolDestroy(s->ws_pool);
   for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
   for (auto& kv : s->plans) {
     cudaFree(kv.second->tables);
