@@ -119,9 +119,10 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *                 kernel on a persistent grid that prefetches its next tile
  *                 into L2 (every pass with a compile-time shape: contiguous
  *                 tiles, and the strided column tiles of two-pass and 2D
- *                 plans), 4 as 2 but the column tiles of strided passes copy
- *                 their rows with per-thread 16-byte copies instead of
- *                 tensor-map (TMA) boxes.
+ *                 plans), 4 as 2 but without tensor maps: the column tiles
+ *                 of strided passes copy their rows with per-thread 16-byte
+ *                 copies instead of tensor-map (TMA) boxes and write their
+ *                 output with register stores only.
  *   epilogue      how a two-pass 1D plan finds the twiddle w_N^{n2 k1} applied
  *                 between its passes: 0 library choice, 1 two small tables
  *                 (w = hi[m >> b] * lo[m mod 2^b]), 2 one table of N entries laid

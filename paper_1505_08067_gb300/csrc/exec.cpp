@@ -45,7 +45,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       }
       const bool want_staged = p.variant == 0 || p.variant == 2 || p.variant == 4;
       l.has_staged = want_staged && resolve_staged(l.d, l.lmap, l.smap, s.generic_only, &l.staged);
-      l.staged.tmap = l.staged.cols && p.variant != 4;
+      l.staged.tmap = p.variant != 4;
       if (l.has_staged) {
         e = prepare_staged(l.staged, l.d.tiles, caps.sm_count);
         if (e != cudaSuccess) return e;

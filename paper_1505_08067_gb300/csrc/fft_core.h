@@ -190,38 +190,49 @@ struct PassDesc {
   int64_t h_lines, h_first;
   const cf* h;
   // Column tiles of the staged kernel: when tmap_in_ok, the tile's input is
-  // copied by tensor-map (TMA) box loads.  tmap_in is a CUtensorMap encoded
-  // at launch over `in` viewed as rows of in.e complex64 elements (dims
-  // {in.e, rows}, box {G, min(L, 256)}); tile coordinates from
-  // tma_cols_coords.
-  int32_t tmap_in_ok;
+  // copied by tensor-map (TMA) box loads; when tmap_out_ok, its output (G
+  // columns) is written by tensor-map box stores.  tmap_in / tmap_out are
+  // CUtensorMaps encoded at launch over `in` / `out` viewed as rows of in.e /
+  // out.e complex64 elements (dims {e, rows}, box {G, min(rows of a copy,
+  // 256)}); tile coordinates from tma_tile_coords.
+  int32_t tmap_in_ok, tmap_out_ok;
   alignas(64) unsigned char tmap_in[128];
+  alignas(64) unsigned char tmap_out[128];
 };
 
-// Can the column tiles of `d` be copied by tensor-map boxes over the input
-// viewed as rows of in.e elements?  Every tile offset outer*in.o + inner*in.t
-// must split into a row y and a column x with x + G <= in.e (in.o a multiple
-// of in.e, the inner tiles within one row), and x must be even (in.e and G
-// even) so that each box starts on a 16-byte boundary.  `rows`: the rows the
-// map spans.
-GB_HD bool cols_map_rows(const PassDesc& d, int64_t& rows) {
-  const int64_t e = d.in.e, L = int64_t(1) << d.logL;
-  if (d.G < 2 || d.G % 2 || d.in.g != 1 || d.in.t != d.G || e < d.G || e % 2 || d.in.o % e ||
+// Can the column tiles of `d` (G adjacent columns of L rows) be moved by
+// tensor-map boxes over the buffer with strides `st` (d.in or d.out) viewed
+// as rows of st.e elements?  Every tile offset outer*st.o + inner*st.t must
+// split into a row y and a column x with x + G <= st.e (st.o a multiple of
+// st.e, the inner tiles within one row), and x must be even (st.e and G
+// even) so that each box starts on a 16-byte boundary.  `rows`: the rows
+// the map spans.
+GB_HD bool cols_map_rows(const PassDesc& d, const Strides& st, int64_t& rows) {
+  const int64_t e = st.e, L = int64_t(1) << d.logL;
+  if (d.G < 2 || d.G % 2 || st.g != 1 || st.t != d.G || e < d.G || e % 2 || st.o % e ||
       d.tiles_inner < 1 || d.tiles_inner * d.G > e || d.tiles < 1 || d.tiles % d.tiles_inner ||
-      (L > 256 && L % 256))
+      (L > 512 && L % 512))
     return false;
-  rows = (d.tiles / d.tiles_inner - 1) * (d.in.o / e) + L;
+  rows = (d.tiles / d.tiles_inner - 1) * (st.o / e) + L;
   return rows <= (int64_t(1) << 31);
 }
 
-// Tensor-map coordinates of column tile `tile`'s first element: its offset
-// outer*in.o + inner*in.t written as y*in.e + x (x the column, y the row).
-GB_HD void tma_cols_coords(const PassDesc& d, int64_t tile, int32_t& x, int32_t& y) {
+// Column tiles whose output goes half through tensor-map box stores: only
+// 32-byte row segments (G = 4).  With 64- or 128-byte segments the register
+// stores are already efficient and the extra pass through shared memory
+// measured slower.
+GB_HD bool cols_store_map(const PassDesc& d) { return d.G * 8 <= 32; }
+
+// Tensor-map coordinates of column tile `tile`'s first element in the buffer
+// with strides `st`: its offset outer*st.o + inner*st.t written as y*st.e + x
+// (x the column, y the row).
+GB_HD void tma_tile_coords(const PassDesc& d, const Strides& st, int64_t tile, int32_t& x,
+                           int32_t& y) {
   const int64_t outer = tile / d.tiles_inner, inner = tile - outer * d.tiles_inner;
-  const int64_t off = outer * d.in.o + inner * d.in.t;
-  const int64_t row = off / d.in.e;
+  const int64_t off = outer * st.o + inner * st.t;
+  const int64_t row = off / st.e;
   y = (int32_t)row;
-  x = (int32_t)(off - row * d.in.e);
+  x = (int32_t)(off - row * st.e);
 }
 
 GB_HD void thread_coords(int map, int tid, int T, int G, int& g, int& t) {

@@ -238,14 +238,19 @@ GB_UNROLL
   // 32 bits (pos * out.e < 2^31 for every frame the planner emits).
   // (kEpi == 4 is applied by the caller, which knows the butterfly structure)
   template <bool SWAP>
-  GB_HD static void put(const PassDesc& d, cf* og, int col, int pos, cf x) {
+  GB_HD static cf out_value(const PassDesc& d, int col, int pos, cf x) {
     if constexpr (SH::kEpi == 2) {
       x = cmul(x, Mem::ldtw(d.epi_lo + col + pos * (int)d.count_inner));  // < N <= 2^24
     } else if constexpr (SH::kEpi == 3) {
       x = cmul(x, Mem::rotor(col * pos, d.epi_logN));  // < N <= 2^24
     }
-    if constexpr (G == 1) Mem::stg(og, pos, SWAP ? mk(x.y, x.x) : x);
-    else Mem::stg(og, pos * (int)d.out.e, SWAP ? mk(x.y, x.x) : x);
+    return SWAP ? mk(x.y, x.x) : x;
+  }
+  template <bool SWAP>
+  GB_HD static void put(const PassDesc& d, cf* og, int col, int pos, cf x) {
+    x = out_value<SWAP>(d, col, pos, x);
+    if constexpr (G == 1) Mem::stg(og, pos, x);
+    else Mem::stg(og, pos * (int)d.out.e, x);
   }
   GB_HD static cf* column_out(const PassDesc& d, cf* o, int g) {
     return G == 1 ? o : o + g * d.out.g;
@@ -352,15 +357,18 @@ GB_UNROLL
   }
 
   // ------------------------------------------------ last stage to global --
-  template <bool SWAP>
-  GB_HD static void store(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0, int tid) {
+  // Outputs i in [I0, I1) of each of this thread's last-stage butterflies
+  // (positions jb + i*Ns), passed as emit(g, pos, value) with the four-step
+  // twiddle and the swap applied.
+  template <bool SWAP, int I0, int I1, class Emit>
+  GB_HD static void store_range(const cf (&v)[R], const PassDesc& d, int64_t col0, int tid,
+                                Emit emit) {
     constexpr int s = SH::kNst - 1;
     constexpr int RR = SH::radix(s);
     constexpr int NB = R / RR;
     constexpr int Ns = SH::ns_before(s);
     int g, t;
     coords(tid, g, t);
-    cf* og = column_out(d, o, g);
     const int col = (int)col0 + g;
     // factored four-step twiddle: w_N^{col (jb + i Ns)} = w_N^{col jb} (w_N^{col Ns})^i
     cf pw[RR];
@@ -376,12 +384,52 @@ GB_UNROLL
       cf base = mk(1.f, 0.f);
       if constexpr (SH::kEpi == 4) base = Mem::rotor(col * (int64_t)jb, d.epi_logN);
 GB_UNROLL
-      for (int i = 0; i < RR; ++i) {
+      for (int i = I0; i < I1; ++i) {
         cf x = v[q * RR + i];
         if constexpr (SH::kEpi == 4) x = cmul(x, i == 0 ? base : cmul(base, pw[i]));
-        put<SWAP>(d, og, col, jb + i * Ns, x);
+        emit(g, jb + i * Ns, out_value<SWAP>(d, col, jb + i * Ns, x));
       }
     }
+  }
+
+  template <bool SWAP>
+  GB_HD static void store(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0, int tid) {
+    constexpr int RR = SH::radix(SH::kNst - 1);
+    int g, t;
+    coords(tid, g, t);
+    cf* og = column_out(d, o, g);
+    store_range<SWAP, 0, RR>(v, d, col0, tid, [&](int, int pos, cf x) {
+      if constexpr (G == 1) Mem::stg(og, pos, x);
+      else Mem::stg(og, pos * (int)d.out.e, x);
+    });
+  }
+
+  // Column tiles, half H of the output rows, [H*L/2, (H+1)*L/2): outputs i
+  // in [H*RR/2, (H+1)*RR/2) of every butterfly, since the last stage writes
+  // jb + i*Ns with jb < Ns = L/RR.  store_half_smem puts them in xs in the
+  // layout of a tensor-map box, row a of column g at (a - H*L/2)*G + g (a
+  // warp's lanes -- adjacent columns, then adjacent rows -- write consecutive
+  // slots: no bank conflicts); store_half writes them to global memory.
+  template <bool SWAP, int H>
+  GB_HD static void store_half_smem(const cf (&v)[R], const PassDesc& d, cf* xs, int64_t col0,
+                                    int tid) {
+    static_assert(G > 1, "column tiles only");
+    constexpr int RR = SH::radix(SH::kNst - 1);
+    store_range<SWAP, H * RR / 2, (H + 1) * RR / 2>(v, d, col0, tid, [&](int g, int pos, cf x) {
+      Mem::sts(xs, (pos - H * (L / 2)) * G + g, x);
+    });
+  }
+  template <bool SWAP, int H>
+  GB_HD static void store_half(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0,
+                               int tid) {
+    static_assert(G > 1, "column tiles only");
+    constexpr int RR = SH::radix(SH::kNst - 1);
+    int g, t;
+    coords(tid, g, t);
+    cf* og = column_out(d, o, g);
+    store_range<SWAP, H * RR / 2, (H + 1) * RR / 2>(v, d, col0, tid, [&](int, int pos, cf x) {
+      Mem::stg(og, pos * (int)d.out.e, x);
+    });
   }
 };
 

@@ -79,10 +79,13 @@ const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool ge
 bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, StagedLaunch* s) {
   if (generic_only) return false;
   if (lmap == MAP_COLS) {
-    s->cols = true;
+    s->map_in = s->map_out = true;
     return !d.conv && resolve_staged_cols_shape(d, lmap, smap, s);
   }
-  if (lmap == MAP_ROWS && smap == MAP_COLS) return !d.conv && resolve_staged_trans_shape(d, lmap, smap, s);
+  if (lmap == MAP_ROWS && smap == MAP_COLS) {
+    s->map_out = true;
+    return !d.conv && resolve_staged_trans_shape(d, lmap, smap, s);
+  }
   if (lmap != MAP_ROWS || smap != MAP_ROWS) return false;
   return d.conv ? resolve_conv_staged_shape(d, s) : resolve_staged_shape(d, s);
 }
@@ -118,38 +121,46 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map for the column tiles of pass `d` over `in`: `in` viewed as rows
-// of in.e complex64 elements, boxes of G columns x min(L, 256) rows.  False
-// (copy rows per thread instead) when the layout does not allow it
-// (cols_map_rows), `in` is not 16-byte aligned, or the encoder refuses.
-bool encode_cols_map(PassDesc& d, const void* in) {
-  const int64_t e = d.in.e, L = int64_t(1) << d.logL;
+// Tensor map for the column tiles of pass `d` over buffer `p` with strides
+// `st` (d.in or d.out): rows of st.e complex64 elements, boxes of G columns x
+// `box_rows` rows.  False when the layout does not allow it (cols_map_rows),
+// `p` is not 16-byte aligned, or the encoder refuses.
+static bool encode_cols_map(const PassDesc& d, const Strides& st, const void* p, int box_rows,
+                            unsigned char (&map)[128]) {
   int64_t rows = 0;
-  if (!cols_map_rows(d, rows) || ((uintptr_t)in & 15)) return false;
+  if (!cols_map_rows(d, st, rows) || ((uintptr_t)p & 15)) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  static_assert(sizeof(CUtensorMap) == sizeof(d.tmap_in), "tensor map size");
-  const cuuint64_t dims[2] = {(cuuint64_t)e, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)e * 8};
-  const cuuint32_t box[2] = {(cuuint32_t)d.G, (cuuint32_t)(L < 256 ? L : 256)};
+  static_assert(sizeof(CUtensorMap) == sizeof(map), "tensor map size");
+  const cuuint64_t dims[2] = {(cuuint64_t)st.e, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)st.e * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)d.G, (cuuint32_t)box_rows};
   const cuuint32_t elem_strides[2] = {1, 1};
   CUtensorMap m;
-  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(in), dims, strides, box,
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(p), dims, strides, box,
           elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
-  memcpy(d.tmap_in, &m, sizeof(m));
-  d.tmap_in_ok = 1;
+  memcpy(map, &m, sizeof(m));
   return true;
+}
+
+bool encode_cols_maps(PassDesc& d, bool map_in, bool map_out, const void* in, void* out) {
+  const int L = 1 << d.logL;
+  d.tmap_in_ok = map_in && encode_cols_map(d, d.in, in, L < 256 ? L : 256, d.tmap_in);
+  d.tmap_out_ok =
+      map_out && encode_cols_map(d, d.out, out, L / 2 < 256 ? L / 2 : 256, d.tmap_out);
+  return d.tmap_in_ok || d.tmap_out_ok;
 }
 
 cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* in, void* out,
                           cudaStream_t st) {
   KernelFn k = reinterpret_cast<KernelFn>(const_cast<void*>(s.fn));
   if (!k || s.grid < 1) return cudaErrorInvalidValue;
-  if (s.cols && s.tmap) {
+  if (s.tmap && (s.map_in || s.map_out)) {
     PassDesc dm = d;
-    if (encode_cols_map(dm, in)) {
+    const bool mo = s.map_out && cols_store_map(d);
+    if (encode_cols_maps(dm, s.map_in, mo, in, out)) {
       k<<<s.grid, s.block, s.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), dm);
       return cudaGetLastError();
     }

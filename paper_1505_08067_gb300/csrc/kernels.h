@@ -38,8 +38,9 @@ struct PassLaunch {
     int grid = 0, block = 0;
     int max_grid = 0;  // resident blocks per SM x SMs (persistent grid)
     size_t smem = 0;
-    bool cols = false;  // column tiles of a strided pass
-    bool tmap = false;  // column tiles: copy the input by tensor-map boxes when possible
+    bool map_in = false;   // input in column tiles (tensor-map box loads possible)
+    bool map_out = false;  // output in column tiles (tensor-map box stores possible)
+    bool tmap = false;     // use tensor maps where the layout allows
   } staged;
 };
 
@@ -54,9 +55,10 @@ bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, St
 cudaError_t prepare_staged(StagedLaunch& s, int64_t tiles, int sm_count);
 cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* in, void* out,
                           cudaStream_t st);
-// Encodes d.tmap_in for column tiles over `in` and sets d.tmap_in_ok; false
-// if the pass's layout or the driver does not allow it.
-bool encode_cols_map(PassDesc& d, const void* in);
+// Encodes d.tmap_in (map_in) and d.tmap_out (map_out) for column tiles over
+// `in` / `out` and sets d.tmap_*_ok; false if neither could be encoded (the
+// pass's layout or the driver does not allow it).
+bool encode_cols_maps(PassDesc& d, bool map_in, bool map_out, const void* in, void* out);
 
 // Kernel for this pass shape: a compile-time specialisation when one matches,
 // else the generic kernel for (R, maps).

@@ -367,7 +367,7 @@ __device__ __forceinline__ void tma_cols(cf* st, const PassDesc& d, int64_t tile
   constexpr int BR = SH::kL < 256 ? SH::kL : 256;
   static_assert(SH::kL % BR == 0 && SH::kG * 8 % 16 == 0, "whole boxes of 16-byte rows");
   int32_t x, y;
-  tma_cols_coords(d, tile, x, y);
+  tma_tile_coords(d, d.in, tile, x, y);
   const uint32_t b = smem_u32(bar);
   const uint64_t map = reinterpret_cast<uint64_t>(&d.tmap_in[0]);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -380,6 +380,41 @@ __device__ __forceinline__ void tma_cols(cf* st, const PassDesc& d, int64_t tile
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(st + j * BR * SH::kG)),
         "l"(map), "r"(x), "r"(y + j * BR), "r"(b)
         : "memory");
+}
+
+// Column tiles, tensor-map store of rows [0, L/2) of tile `tile` from xs (box
+// layout, SplitBody::store_half_smem) as boxes of min(L/2, 256) rows
+// (d.tmap_out).  Called by one thread after a barrier that follows every
+// thread's writes and proxy fence.  Does not wait: the caller's thread 0
+// waits for the copies to have read xs (cp.async.bulk.wait_group.read)
+// before the barrier that precedes the next write to xs.
+template <class SH>
+__device__ __forceinline__ void tma_store_half0(const cf* xs, const PassDesc& d, int64_t tile) {
+  constexpr int HL = SH::kL / 2, BR = HL < 256 ? HL : 256;
+  static_assert(HL % BR == 0 && SH::kG * 8 % 16 == 0, "whole boxes of 16-byte rows");
+  int32_t x, y;
+  tma_tile_coords(d, d.out, tile, x, y);
+  const uint64_t map = reinterpret_cast<uint64_t>(&d.tmap_out[0]);
+  for (int j = 0; j < HL / BR; ++j)
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::
+                     "l"(map), "r"(x), "r"(y + j * BR), "r"(smem_u32(xs + j * BR * SH::kG))
+                 : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Column-tile output: the first half of the rows through the exchange buffer
+// x and tensor-map box stores (asynchronous), the second half by register
+// stores while those copies run -- half the strided store instructions, and
+// no wait for the copies (x is next written one tile later).
+template <class SH, bool SWAP>
+__device__ __forceinline__ void store_cols_tma(const cf (&v)[SH::kR], const PassDesc& d, cf* x,
+                                               cf* o, int64_t tile, int64_t col0, int tid) {
+  using B = SplitBody<SH, DevMem>;
+  B::template store_half_smem<SWAP, 0>(v, d, x, col0, tid);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) tma_store_half0<SH>(x, d, tile);
+  B::template store_half<SWAP, 1>(v, d, o, col0, tid);
 }
 
 template <class SH, int S, bool FIRST_EXCHANGE>
@@ -460,11 +495,15 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
   }
   uint32_t parity = 0;
   for (; tile < d.tiles; tile += step) {
+    // the previous tile's tensor-map stores must have read x before this
+    // tile's exchanges write it (the barrier below orders the rest)
+    if (SH::kG > 1 && tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     const bool ok = mbar_wait(bar, parity, kWaitPolls);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(d.status, 1);
         mbar_wait(bar, parity, kWaitPolls);  // let the copy in flight land before leaving
+        if constexpr (SH::kG > 1) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
       }
       return;
     }
@@ -495,11 +534,18 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     } else if constexpr (SH::kFuseLast) {
       if (d.conj_out) B::template store_fused<true>(v, d, o, col0, tid, fr);
       else B::template store_fused<false>(v, d, o, col0, tid, fr);
+    } else if (SH::kG > 1 && d.tmap_out_ok) {
+      if constexpr (SH::kG > 1) {
+        if (d.conj_out) store_cols_tma<SH, true>(v, d, x, o, tile, col0, tid);
+        else store_cols_tma<SH, false>(v, d, x, o, tile, col0, tid);
+      }
     } else {
       if (d.conj_out) B::template store<true>(v, d, o, col0, tid);
       else B::template store<false>(v, d, o, col0, tid);
     }
   }
+  // tensor-map stores: the last ones have read shared memory; let them land
+  if (SH::kG > 1 && tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 

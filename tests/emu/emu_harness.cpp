@@ -284,9 +284,9 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
     // of the map, which must lie inside its {in.e, rows} extent (TMA would
     // fill zeros outside it) and be the element the row copy reads
     int64_t map_rows = 0;
-    const bool use_map = SH::kG > 1 && !SH::kRowsIn && cols_map_rows(d, map_rows);
+    const bool use_map = SH::kG > 1 && !SH::kRowsIn && cols_map_rows(d, d.in, map_rows);
     int32_t mx = 0, my = 0;
-    if (use_map) tma_cols_coords(d, tile, mx, my);
+    if (use_map) tma_tile_coords(d, d.in, tile, mx, my);
     for (int a = 0; a < SH::kL; ++a)
       for (int c = 0; c < SH::kG; ++c) {
         if constexpr (SH::kRowsIn) {  // one bulk copy per row, pitched
@@ -334,6 +334,38 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
         else B::template store<true>(reg(t), d, o, col0, t);
       }
       continue;
+    }
+    // column tiles the GPU writes half by tensor-map box stores: rows
+    // [0, L/2) go to the exchange buffer in the box layout (every slot
+    // written once), then box element (a, c) to row y + a, column x + c of the
+    // output map, which must be the element the register store writes; rows
+    // [L/2, L) by register stores
+    int64_t out_rows = 0;
+    if constexpr (SH::kG > 1 && !SH::kFuseLast) {
+      if (cols_store_map(d) && cols_map_rows(d, d.out, out_rows)) {
+        int32_t ox = 0, oy = 0;
+        tma_tile_coords(d, d.out, tile, ox, oy);
+        ++g.epoch;
+        for (int t = 0; t < SH::kT; ++t) {
+          if (d.conj_out) B::template store_half_smem<true, 0>(reg(t), d, x.data(), col0, t);
+          else B::template store_half_smem<false, 0>(reg(t), d, x.data(), col0, t);
+        }
+        for (int a = 0; a < SH::kL / 2; ++a)
+          for (int c = 0; c < SH::kG; ++c) {
+            const int slot = a * SH::kG + c;
+            if (wr[slot] != g.epoch) err("box-store slot not written in this half", slot);
+            const int64_t row = (int64_t)oy + a, col = (int64_t)ox + c;
+            if (row >= out_rows || col >= d.out.e || ox % 2 ||
+                row * d.out.e + col != dst + c + a * d.out.e)
+              err("tensor-map box store outside the map or off the column", row * d.out.e + col);
+            CheckMem::stg(out, row * d.out.e + col, x[slot]);
+          }
+        for (int t = 0; t < SH::kT; ++t) {
+          if (d.conj_out) B::template store_half<true, 1>(reg(t), d, o, col0, t);
+          else B::template store_half<false, 1>(reg(t), d, o, col0, t);
+        }
+        continue;
+      }
     }
     for (int t = 0; t < SH::kT; ++t) {
       if constexpr (SH::kFuseLast) {
