@@ -83,6 +83,14 @@ struct SplitShape {
   // Load the fused last stage's roots during the last exchange (radix-2
   // last stage: measured faster) or inside the store loop (radix 4).
   static constexpr bool kPrefetchFused = kPowTw && kFuseLast && kNB == 2;
+  // The roots depend on the thread and the stage only, not on the tile: a
+  // kernel with registers to spare loads them once, before its first tile,
+  // and keeps them -- those of the exchanged stages for column tiles and
+  // 2^14 (the 2^13 shape, two blocks per SM at up to 128 registers, measured
+  // 1% slower holding them), those of the fused last stage (16 per thread)
+  // only for 2^14 (one 256-thread block per SM, up to 255 registers).
+  static constexpr bool kHoldRoots = kPowTw && (G_ > 1 || LOGL == 14);
+  static constexpr bool kHoldFused = kPowTw && kFuseLast && G_ == 1 && LOGL == 14;
 };
 
 template <class SH, class Mem>
@@ -175,9 +183,24 @@ GB_UNROLL
     }
   }
 
+  // This thread's twiddle roots: for the stage after exchange S (S <
+  // kExchanges) and for the fused last stage.
+  template <int S>
+  static constexpr int nb_after() { return S < SH::kExchanges ? R / SH::radix(S + 1) : 1; }
+  struct Roots {
+    cf r0[nb_after<0>()], r1[nb_after<1>()], r2[nb_after<2>()];
+    cf fr[16];
+  };
+  template <int S>
+  GB_HD static auto roots_of(Roots& x) -> cf (&)[nb_after<S>()] {
+    if constexpr (S == 0) return x.r0;
+    else if constexpr (S == 1) return x.r1;
+    else return x.r2;
+  }
+
   // Twiddle roots w_{RR*Ns}^k of this thread's butterflies in stage S+1
   // (SH::kPowTw), loaded before the exchange that precedes the stage so that
-  // the exchange hides their latency.
+  // the exchange hides their latency (or once per kernel, SH::kHoldRoots).
   template <int S>
   GB_HD static void roots(cf (&r)[R / SH::radix(S + 1)], const PassDesc& d, int tid) {
     constexpr int s = S + 1;
@@ -326,7 +349,8 @@ GB_UNROLL
     for (int i = 0; i < 16; ++i) fr[i] = Mem::ldtw(tw + i * T);
   }
 
-  template <bool SWAP>
+  // FR_READY: fr holds the roots (fused_roots ran); else each is loaded here.
+  template <bool SWAP, bool FR_READY = SH::kPrefetchFused>
   GB_HD static void store_fused(const cf (&v)[R], const PassDesc& d, cf* o, int64_t col0,
                                 int tid, const cf (&fr)[16]) {
     static_assert(SH::kEpi != 4, "the factored twiddle needs the plain last stage");
@@ -343,7 +367,7 @@ GB_UNROLL
       cf x[NB], pw[NB];
       x[0] = v[i];
       if (SH::kPowTw) {  // w_L^{q p} = (w_L^p)^q
-        pw[1] = SH::kPrefetchFused ? fr[i] : Mem::ldtw(tw + Ns + p);
+        pw[1] = FR_READY ? fr[i] : Mem::ldtw(tw + Ns + p);
 GB_UNROLL
         for (int q = 2; q < NB; ++q) pw[q] = cmul(pw[q / 2], pw[q - q / 2]);
       }

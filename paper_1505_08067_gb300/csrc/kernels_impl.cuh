@@ -417,14 +417,16 @@ __device__ __forceinline__ void store_cols_tma(const cf (&v)[SH::kR], const Pass
   B::template store_half<SWAP, 1>(v, d, o, col0, tid);
 }
 
-template <class SH, int S, bool FIRST_EXCHANGE>
+// HOLD: the exchanged stages' roots in `rt` were loaded before the first tile.
+template <class SH, int S, bool FIRST_EXCHANGE, bool HOLD>
 __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
                                                uint64_t* bar, const cf* in, int64_t next,
-                                               int tid, cf (&fr)[16]) {
+                                               int tid,
+                                               typename SplitBody<SH, DevMem>::Roots& rt) {
   using B = SplitBody<SH, DevMem>;
-  cf r[SH::kR / SH::radix(S + 1)];
-  if constexpr (SH::kPowTw) B::template roots<S>(r, d, tid);
-  if constexpr (SH::kPrefetchFused && S == SH::kExchanges - 1) B::fused_roots(fr, d, tid);
+  auto& r = B::template roots_of<S>(rt);
+  if constexpr (SH::kPowTw && !HOLD) B::template roots<S>(r, d, tid);
+  if constexpr (SH::kPrefetchFused && S == SH::kExchanges - 1) B::fused_roots(rt.fr, d, tid);
   B::template write_half<S, 0>(v, x, tid);
   __syncthreads();
   if (FIRST_EXCHANGE && next >= 0) {  // staging is free: every thread has read it
@@ -448,16 +450,19 @@ __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& 
 }
 
 // The exchanges after stages 0 .. kExchanges-1; the first one starts the
-// copy of tile `next` (if >= 0) into the staging buffer, the last one loads
-// the fused last stage's twiddle roots `fr` (SplitBody::fused_roots).
-template <class SH>
+// copy of tile `next` (if >= 0) into the staging buffer; unless HOLD, each
+// loads the twiddle roots of the stage after it into `rt`; the last one loads
+// those of a fused radix-2 last stage (SplitShape::kPrefetchFused).
+template <class SH, bool HOLD>
 __device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
                                             uint64_t* bar, const cf* in, int64_t next, int tid,
-                                            cf (&fr)[16]) {
+                                            typename SplitBody<SH, DevMem>::Roots& rt) {
   static_assert(SH::kExchanges >= 1, "at least one exchange");
-  split_exchange<SH, 0, true>(v, d, x, st, bar, in, next, tid, fr);
-  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, false>(v, d, x, st, bar, in, -1, tid, fr);
-  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, false>(v, d, x, st, bar, in, -1, tid, fr);
+  split_exchange<SH, 0, true, HOLD>(v, d, x, st, bar, in, next, tid, rt);
+  if constexpr (SH::kExchanges > 1)
+    split_exchange<SH, 1, false, HOLD>(v, d, x, st, bar, in, -1, tid, rt);
+  if constexpr (SH::kExchanges > 2)
+    split_exchange<SH, 2, false, HOLD>(v, d, x, st, bar, in, -1, tid, rt);
 }
 
 // One tile per block (a contiguous transform, or G adjacent columns of a
@@ -493,6 +498,17 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
       copy_rows<SH>(st, staged_src<SH>(in, d, tile), d.in.e, bar, tid);
     }
   }
+  // twiddle roots: loaded once here (kHold, kHoldFused) or per tile
+  constexpr bool kHold = SH::kHoldRoots && !CONV;
+  constexpr bool kHoldFused = SH::kHoldFused && !CONV;
+  typename B::Roots rt;
+  if constexpr (kHold) {
+    B::template roots<0>(rt.r0, d, tid);
+    if constexpr (SH::kExchanges > 1) B::template roots<1>(rt.r1, d, tid);
+    if constexpr (SH::kExchanges > 2) B::template roots<2>(rt.r2, d, tid);
+  }
+  if constexpr (kHoldFused) B::fused_roots(rt.fr, d, tid);
+  constexpr bool kFrReady = SH::kPrefetchFused || kHoldFused;
   uint32_t parity = 0;
   for (; tile < d.tiles; tile += step) {
     // the previous tile's tensor-map stores must have read x before this
@@ -509,10 +525,10 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     }
     parity ^= 1u;
     const int64_t next = tile + step < d.tiles ? tile + step : -1;
-    cf v[SH::kR], fr[16];
+    cf v[SH::kR];
     if (d.conj_in) B::template first<true>(v, st, tid);
     else B::template first<false>(v, st, tid);
-    split_round<SH>(v, d, x, st, bar, in, next, tid, fr);
+    split_round<SH, kHold>(v, d, x, st, bar, in, next, tid, rt);
     cf* o;
     int64_t col0;  // G == 1: the line (tile); else the first column of the tile
     if constexpr (SH::kG == 1) {
@@ -525,15 +541,12 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     }
     if constexpr (CONV) {
       B::conv_middle(v, d, col0, tid);
-      split_round<SH>(v, d, x, st, bar, in, -1, tid, fr);
-      if constexpr (SH::kFuseLast) {
-          B::template store_fused<true>(v, d, o, col0, tid, fr);
-      } else {
-        B::template store<true>(v, d, o, col0, tid);
-      }
+      split_round<SH, kHold>(v, d, x, st, bar, in, -1, tid, rt);
+      if constexpr (SH::kFuseLast) B::template store_fused<true, kFrReady>(v, d, o, col0, tid, rt.fr);
+      else B::template store<true>(v, d, o, col0, tid);
     } else if constexpr (SH::kFuseLast) {
-      if (d.conj_out) B::template store_fused<true>(v, d, o, col0, tid, fr);
-      else B::template store_fused<false>(v, d, o, col0, tid, fr);
+      if (d.conj_out) B::template store_fused<true, kFrReady>(v, d, o, col0, tid, rt.fr);
+      else B::template store_fused<false, kFrReady>(v, d, o, col0, tid, rt.fr);
     } else if (SH::kG > 1 && d.tmap_out_ok) {
       if constexpr (SH::kG > 1) {
         if (d.conj_out) store_cols_tma<SH, true>(v, d, x, o, tile, col0, tid);

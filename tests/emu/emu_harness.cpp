@@ -330,7 +330,7 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
       for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, col0, t);
       round();
       for (int t = 0; t < SH::kT; ++t) {
-        if constexpr (SH::kFuseLast) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true>(reg(t), d, o, col0, t, fr); }
+        if constexpr (SH::kFuseLast) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true, true>(reg(t), d, o, col0, t, fr); }
         else B::template store<true>(reg(t), d, o, col0, t);
       }
       continue;
@@ -369,8 +369,8 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
     }
     for (int t = 0; t < SH::kT; ++t) {
       if constexpr (SH::kFuseLast) {
-        if (d.conj_out) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true>(reg(t), d, o, col0, t, fr); }
-        else { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<false>(reg(t), d, o, col0, t, fr); }
+        if (d.conj_out) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true, true>(reg(t), d, o, col0, t, fr); }
+        else { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<false, true>(reg(t), d, o, col0, t, fr); }
       } else {
         if (d.conj_out) B::template store<true>(reg(t), d, o, col0, t);
         else B::template store<false>(reg(t), d, o, col0, t);
