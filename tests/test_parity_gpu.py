@@ -134,6 +134,22 @@ def test_tones_closed_form(gb, oracle):
         _compare(oracle, y, x, (n,))
 
 
+@pytest.mark.parametrize("n", [512, 8192, 2 ** 14, 2 ** 22])
+def test_multi_tone_closed_form(gb, oracle, n):
+    """Four unit tones per transform: the spectrum is N at each tone bin and
+    zero elsewhere (closed form of the DFT of a sum of exponentials)."""
+    batch = 3
+    x = synth.tones(4600 + n, batch, n, 4)
+    bins = synth.tone_bins(4600 + n, batch, n, 4)
+    y = _run(gb, x, (n,))
+    expect = np.zeros((batch, n), dtype=np.complex128)
+    for b in range(batch):
+        expect[b, bins[b]] = n
+    err = np.linalg.norm(y - expect, axis=1) / np.linalg.norm(expect, axis=1)
+    assert np.max(err) <= _tol(n), float(np.max(err))
+    _compare(oracle, y, x, (n,))
+
+
 def test_impulse_and_roundtrip(gb, oracle):
     n = 4096
     x = np.zeros((2, n), np.complex64)
