@@ -104,7 +104,7 @@ def test_tiles_ragged_batch(gb, oracle, tile):
     _compare(oracle, _run(gb, x, (256,), tile=tile), x, (256,))
 
 
-@pytest.mark.parametrize("shape", [(2 ** 12,), (2 ** 18,), (64, 32)])
+@pytest.mark.parametrize("shape", [(2 ** 12,), (2 ** 18,), (64, 32), (4096, 64), (1024, 256)])
 def test_in_place(gb, oracle, shape):
     n = int(np.prod(shape))
     x = synth.uniform(4300, 3, n).reshape((3,) + shape)
