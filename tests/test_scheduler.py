@@ -109,3 +109,21 @@ def test_backfill_random_streams():
             members = np.where(bf["group"] == g)[0]
             assert len(set(key[members])) == 1
         assert np.mean(bf["launch"] - arrive) <= np.mean(fifo["launch"] - arrive)
+
+
+def test_backfilled_group_coalesces_same_key_jobs():
+    """A blocked head does not stop later same-key small jobs from starting
+    together in one backfilled group, and the group as a whole obeys the
+    reservation: job 1 (7 GB) waits for job 0 (5 GB, 100 steps); jobs 2-4
+    (1 GB, 10 steps each, same key, groupable) run back to back in one group
+    that ends at step 32 < 100; the head still starts at step 100."""
+    G = 1 << 30
+    key = [0, 1, 2, 2, 2]
+    nbytes = [5 * G, 7 * G, G, G, G]
+    arrive = [0, 1, 2, 2, 2]
+    dur = [100, 10, 10, 10, 10]
+    grp = [0, 0, 1, 1, 1]
+    r = sched.simulate(key, nbytes, arrive, dur, grp, 10 * G, backfill=True)
+    assert r["launch"].tolist() == [0, 100, 2, 2, 2]
+    assert len(set(r["group"][2:].tolist())) == 1          # one coalesced group
+    assert r["done"][2] == 32 and r["peak"] <= 10 * G
