@@ -13,9 +13,10 @@
 //   3. sleeps briefly when nothing changed.
 // Plans (twiddle tables) stay resident per job key; multi-pass workspaces are
 // stream-ordered allocations from the server's own memory pool (allocated on
-// the group's stream before its passes, freed on it after them: no device-wide
-// synchronisation, memory reused once the freeing stream has passed it).  Groups on different streams overlap on the
-// device.  Everything a running group holds counts against the budget.
+// the group's stream before its passes, freed on it after them: no
+// device-wide synchronisation, memory reused once the freeing stream has
+// passed it).  Groups on different streams overlap on the device.
+// Everything a running group holds counts against the budget.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
