@@ -265,6 +265,8 @@ def ours_other(args, rank: int, world: int) -> None:
                 opts = {"epilogue": args.epilogue} if args.epilogue else {}
                 if args.variant and prec == 0:
                     opts["variant"] = args.variant
+                if args.tile and prec == 0:
+                    opts["tile"] = args.tile
                 opts["autotune"] = args.autotune if prec == 0 else 0
                 plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, prec,
                                         **opts)
@@ -785,6 +787,8 @@ def main() -> None:
                          "the large-transform configs, reported as separate lines")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--only", type=int, default=0, help="run only N = 2^ONLY (profiling)")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="multipass / sar workloads: transforms per tile (0: library choice)")
     ap.add_argument("--variant", type=int, default=0,
                     help="contiguous-pass kernel variant (0 library choice, 1 register, "
                          "2 TMA-staged, 3 L2 prefetch)")

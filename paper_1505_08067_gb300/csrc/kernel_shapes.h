@@ -69,7 +69,13 @@
   GB_STAGED_COLS(12, 0x444, 3, 32, 4, 0, 0)        \
   GB_STAGED_COLS(10, 0x244, 3, 32, 16, 4, 0)       \
   GB_STAGED_COLS(11, 0x344, 3, 32, 8, 4, 0)        \
-  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 4, 0)
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 4, 0)       \
+  GB_STAGED_COLS(10, 0x244, 3, 32, 8, 2, 0)       \
+  GB_STAGED_COLS(10, 0x244, 3, 32, 8, 3, 0)       \
+  GB_STAGED_COLS(10, 0x244, 3, 32, 8, 4, 0)       \
+  GB_STAGED_COLS(11, 0x344, 3, 32, 4, 2, 0)       \
+  GB_STAGED_COLS(11, 0x344, 3, 32, 4, 3, 0)       \
+  GB_STAGED_COLS(11, 0x344, 3, 32, 4, 4, 0)
 
 // Transposing passes (G contiguous rows in, G columns out: the second pass of
 // a four-step plan) that run the staged kernel:
@@ -77,7 +83,9 @@
 #define GB_STAGED_TRANS_SHAPES(GB_STAGED_TRANS) \
   GB_STAGED_TRANS(10, 0x244, 3, 32, 16)         \
   GB_STAGED_TRANS(11, 0x344, 3, 32, 8)          \
-  GB_STAGED_TRANS(12, 0x444, 3, 32, 4)
+  GB_STAGED_TRANS(12, 0x444, 3, 32, 4)          \
+  GB_STAGED_TRANS(10, 0x244, 3, 32, 8)          \
+  GB_STAGED_TRANS(11, 0x344, 3, 32, 4)
 
 namespace gbfft {
 

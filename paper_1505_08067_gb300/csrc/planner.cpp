@@ -332,7 +332,14 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       // pass 1: column FFTs of length N1 over N2 columns, twiddle on store
       int R1 = choose_R(l1, o.radix);
       PassSpec p1 = fft_pass(l1, R1, sched_for(l1, R1, o.schedule));
-      int G1 = (int)std::min<int64_t>({16, B / N1, N2});
+      // transforms per tile of the four-step passes: 8 for 1024 points and 4
+      // for 2048 (256-thread blocks, two per SM, so one block's stores overlap
+      // the other's exchanges) measured faster than 16 / 8 in one 512-thread
+      // block (2^20: 84% against 77% of the HBM bandwidth; 2^22: 79% against
+      // 78%); 4096-point passes keep 4 (two columns would leave 16-byte rows)
+      const auto tile_cap = [](int l) { return l == 10 ? 8 : l == 11 ? 4 : 16; };
+      int G1 = (int)std::min<int64_t>({tile_cap(l1), B / N1, N2});
+      if (o.tile) G1 = std::min(G1, o.tile);  // columns per tile (tuning)
       p1.G = G1;
       p1.lmap = p1.smap = MAP_COLS;
       p1.count_inner = N2;
@@ -354,7 +361,8 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       // the transposed store needs a shared-memory exchange: at least two stages
       int R2 = std::min(choose_R(l2, o.radix), 1 << (l2 - 1));
       PassSpec p2 = fft_pass(l2, R2, default_schedule(l2, ilog2(R2)));
-      int G2 = (int)std::min<int64_t>({16, B / N2, N1});
+      int G2 = (int)std::min<int64_t>({tile_cap(l2), B / N2, N1});
+      if (o.tile) G2 = std::min(G2, o.tile);  // rows per tile (tuning)
       p2.G = G2;
       p2.lmap = MAP_ROWS;
       p2.smap = MAP_COLS;

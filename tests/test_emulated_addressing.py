@@ -202,7 +202,7 @@ def test_conv_forced_radix_and_tile(oracle, radix, tile):
 @pytest.mark.parametrize("direction", [-1, 1])
 def test_staged_column_first_pass(oracle, logn, split, epilogue, direction):
     """Four-step first passes of 1024 / 2048 / 4096 points run the staged
-    column kernel (G = 16 / 8 / 4 columns per tile, the four-step twiddle on
+    column kernel (G = 8 / 4 / 4 columns per tile, the four-step twiddle on
     store); second passes of 1024 / 2048 / 4096 points the staged transposing
     kernel (G contiguous rows in, G columns out); the register kernels must
     agree."""

@@ -294,6 +294,7 @@ def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
 
 
 @pytest.mark.parametrize("shape,batch,opts", [((4096, 64), 2, {}), ((2 ** 20,), 2, {"split_log2": 10}),
+                                              ((2 ** 20,), 2, {"split_log2": 10, "tile": 8}),
                                               ((2 ** 22,), 1, {"split_log2": 11, "epilogue": 3}),
                                               ((2 ** 24,), 1, {"split_log2": 12, "epilogue": 3}),
                                               ((2 ** 22,), 1, {"split_log2": 11, "epilogue": 4}),
