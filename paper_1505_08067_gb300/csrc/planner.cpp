@@ -402,6 +402,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       PassSpec p = fft_pass(lr, R, default_schedule(lr, ilog2(R)));
       const int64_t B = int64_t(1) << bmax;
       int G = (int)std::min<int64_t>({16, B / rows, cols});
+      if (o.tile) G = std::min(G, o.tile);  // columns per tile (tuning)
       p.G = G;
       p.lmap = p.smap = MAP_COLS;
       p.count_inner = cols;
