@@ -127,3 +127,16 @@ def test_conv_dry_run_rejects(n, batch, filters, status):
     with pytest.raises(g.GbfftError) as e:
         g.fft_conv_plan_dry_run(n, batch, filters)
     assert e.value.status == status
+
+
+@pytest.mark.parametrize("logn,split,g1,g2", [(20, 10, 8, 8), (21, 10, 8, 4), (22, 11, 4, 4),
+                                              (24, 12, 4, 4), (16, 8, 16, 16)])
+def test_four_step_tile_widths(logn, split, g1, g2):
+    """Transforms per tile of the four-step passes: 8 at 1024 points and 4 at
+    2048 and 4096 (256-thread blocks, two per SM, for 1024 and 2048), 16 for
+    shorter passes; the tile option narrows them."""
+    d = g.fft_plan_dry_run(2 ** logn, 4)
+    p1, p2 = d["passes"]
+    assert p1["L"] == 2 ** split and (p1["G"], p2["G"]) == (g1, g2)
+    d = g.fft_plan_dry_run(2 ** logn, 4, tile=2)
+    assert [p["G"] for p in d["passes"]] == [min(2, g1), min(2, g2)]
