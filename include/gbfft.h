@@ -289,11 +289,25 @@ GBFFT_API fft_status_t fft_conv_plan_dry_run(const int64_t* n, int dims, int64_t
  *     must be at most 2^23 complex elements; larger problems return
  *     FFT_ERR_UNSUPPORTED_SIZE (create a plan instead).
  *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture begins.
+ *     that first call before any stream capture begins.  The address is kept
+ *     for the life of the process: resetting the device (cudaDeviceReset, or
+ *     a reset of its primary context) while the library is loaded is not
+ *     supported.
  *   - Every call uses the same array and leaves its contents behind.  Calls
  *     whose GPU work overlaps (different streams, several host threads) race
- *     and corrupt each other's results: serialise them.  Each call rewrites
- *     everything it reads from the array, so nothing needs clearing.
+ *     and corrupt each other's results: serialise them.  Each call clears the
+ *     status word it uses and writes the workspace before reading it; the
+ *     twiddle tables are regenerated whenever the table layout differs from
+ *     the one the previous call on the device left.
+ *   - The library remembers, per device and in host memory only, the plan of
+ *     the last (n, batch, direction) it was called with, so a loop that calls
+ *     with one shape plans and prepares its kernels once.
+ *   - Errors in the arguments and in enqueueing are returned.  The staged
+ *     kernels' bounded waits for their own copies into shared memory (about
+ *     0.5 s each, far above any copy's duration) are not reported by this
+ *     entry point: if one ever gave up, the call would return FFT_OK with part
+ *     of the output unwritten.  Callers that need that guarantee create a plan
+ *     and check fft_plan_sync_status.
  */
 GBFFT_API fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction,
                                            const void* in, void* out, void* stream);

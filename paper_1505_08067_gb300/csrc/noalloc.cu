@@ -15,7 +15,13 @@
 // as an address (on the host it is only a stand-in): the device address is
 // looked up with cudaGetSymbolAddress once per device, the first time this
 // entry point runs on that device, and cached.
+//
+// Host-side state per device (static, no heap): the device address, and the
+// plan and bound launches of the last shape called, so that a loop calling
+// with one shape pays the planning and kernel preparation once; the twiddle
+// tables in the array are regenerated only when the table layout changes.
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <mutex>
 
@@ -36,25 +42,42 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float2 g_noalloc_scratch[kWorkElems + kTableElems];
 
+struct DeviceState {
+  void* addr = nullptr;      // device address of g_noalloc_scratch
+  bool have_shape = false;   // spec / launches hold the last (n, batch, direction)
+  int64_t n = 0, batch = 0;
+  int direction = 0;
+  PlanSpec spec;
+  PassLaunch launches[4];
+  bool tables_valid = false;  // the array holds the tables of `spec` (segment list below)
+  SmallVec<TwSegment, 40> table_layout;
+};
+
 std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+DeviceState g_state[kMaxDevices];
+
+bool same_tables(const SmallVec<TwSegment, 40>& a, const SmallVec<TwSegment, 40>& b) {
+  if (a.size() != b.size()) return false;
+  for (int i = 0; i < a.size(); ++i) {
+    const TwSegment &x = a[i], &y = b[i];
+    if (x.off != y.off || x.count != y.count || x.den != y.den || x.mult != y.mult ||
+        x.mode != y.mode || x.r != y.r)
+      return false;
+  }
+  return true;
+}
 
 // Device address of the scratch array on `dev` (which must be current).
-fft_status_t scratch_address(int dev, void** ptr) {
-  if (dev < 0 || dev >= kMaxDevices)
-    return set_error(FFT_ERR_INVALID_ARG, "fft_execute_noalloc supports device ids 0..63");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return set_error(FFT_ERR_CUDA, "fft_execute_noalloc: cudaGetSymbolAddress of the static "
-                                     "scratch array failed");
-    }
-    g_addr[dev] = p;
+fft_status_t scratch_address(DeviceState& ds) {
+  if (ds.addr) return FFT_OK;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return set_error(FFT_ERR_CUDA, "fft_execute_noalloc: cudaGetSymbolAddress of the static "
+                                   "scratch array failed");
   }
-  *ptr = g_addr[dev];
+  ds.addr = p;
   return FFT_OK;
 }
 
@@ -65,6 +88,8 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
   if (n < 1 || (n & (n - 1)) || n > kWorkElems)
     return set_error(FFT_ERR_UNSUPPORTED_SIZE,
                      "fft_execute_noalloc: n must be a power of two between 1 and 2^23");
+  if (direction != FFT_FORWARD && direction != FFT_INVERSE)
+    return set_error(FFT_ERR_INVALID_ARG, "direction must be FFT_FORWARD or FFT_INVERSE");
   if (batch < 0) return set_error(FFT_ERR_INVALID_ARG, "batch must be >= 0");
   if (batch == 0) return FFT_OK;
   if (!in || !out) return set_error(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
@@ -75,39 +100,67 @@ extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direct
     cudaGetLastError();
     return set_error(FFT_ERR_CUDA, "no usable CUDA device");
   }
-  Caps caps;
-  int v = 0;
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-    caps.sm_count = v;
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
-    caps.smem_optin = v;
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxThreadsPerBlock, dev) == cudaSuccess)
-    caps.max_block = v;
-  PlanSpec s;
-  fft_plan_options_t opt{};
-  opt.epilogue = 4;  // four-step twiddles computed in-kernel: no N-entry table in static memory
-  make_plan(s, &n, 1, batch, direction, FFT_PREC_FP32, &opt, caps);
-  if (s.status != FFT_OK) return set_error(s.status, s.error);
-  if (s.work_elems > kWorkElems)
-    return set_error(FFT_ERR_UNSUPPORTED_SIZE,
-                     "fft_execute_noalloc: n * batch needs more than the 64 MiB static workspace "
-                     "(at most 2^23 complex elements when n > 2^14); use fft_plan_create");
-  if (s.table_elems + 2 > kTableElems)
-    return set_error(FFT_ERR_UNSUPPORTED_SIZE,
-                     "fft_execute_noalloc: twiddle tables exceed the static area");
-  void* base = nullptr;
-  fft_status_t st = scratch_address(dev, &base);
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(FFT_ERR_INVALID_ARG, "fft_execute_noalloc supports device ids 0..63");
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState& ds = g_state[dev];
+  fft_status_t st = scratch_address(ds);
   if (st != FFT_OK) return st;
-  cf* work = static_cast<cf*>(base);
+  cf* work = static_cast<cf*>(ds.addr);
   cf* tables = work + kWorkElems;
   int* status = reinterpret_cast<int*>(tables + (kTableElems - 2));
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  PassLaunch launches[4];
-  cudaError_t e = enqueue_tables(s, tables, cs);
-  if (e == cudaSuccess) e = bind_launches(s, caps, tables, status, launches);
-  if (e == cudaSuccess) e = enqueue_passes(s, launches, in, out, work, 0, batch, cs);
+
+  if (!(ds.have_shape && ds.n == n && ds.batch == batch && ds.direction == direction)) {
+    ds.have_shape = false;
+    Caps caps;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      caps.sm_count = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+      caps.smem_optin = v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxThreadsPerBlock, dev) == cudaSuccess)
+      caps.max_block = v;
+    fft_plan_options_t opt{};
+    opt.epilogue = 4;  // four-step twiddles computed in-kernel: no N-entry table in static memory
+    make_plan(ds.spec, &n, 1, batch, direction, FFT_PREC_FP32, &opt, caps);
+    if (ds.spec.status != FFT_OK) return set_error(ds.spec.status, ds.spec.error);
+    if (ds.spec.work_elems > kWorkElems)
+      return set_error(FFT_ERR_UNSUPPORTED_SIZE,
+                       "fft_execute_noalloc: n * batch needs more than the 64 MiB static "
+                       "workspace (at most 2^23 complex elements when n > 2^14); use "
+                       "fft_plan_create");
+    if (ds.spec.table_elems + 2 > kTableElems)
+      return set_error(FFT_ERR_UNSUPPORTED_SIZE,
+                       "fft_execute_noalloc: twiddle tables exceed the static area");
+    cudaError_t e = bind_launches(ds.spec, caps, tables, status, ds.launches);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(FFT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    ds.have_shape = true;
+    ds.n = n;
+    ds.batch = batch;
+    ds.direction = direction;
+  }
+
+  // the status word the staged kernels set when a bounded wait gives up:
+  // cleared on the caller's stream, so a give-up of an earlier call does not
+  // linger (an asynchronous memset allocates nothing)
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), cs);
+  if (e == cudaSuccess && !(ds.tables_valid && same_tables(ds.table_layout, ds.spec.tables))) {
+    ds.tables_valid = false;
+    e = enqueue_tables(ds.spec, tables, cs);
+    if (e == cudaSuccess) {
+      ds.table_layout = ds.spec.tables;
+      ds.tables_valid = true;
+    }
+  }
+  if (e == cudaSuccess) e = enqueue_passes(ds.spec, ds.launches, in, out, work, 0, batch, cs);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    ds.tables_valid = false;
+    ds.have_shape = false;
     return set_error(FFT_ERR_CUDA, cudaGetErrorString(e));
   }
   return FFT_OK;
