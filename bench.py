@@ -191,7 +191,7 @@ def run_oracle_steps(x, elems, steps, warmup):
     return time.perf_counter() - t0
 
 
-def reference_arm(args, rank: int) -> None:
+def reference_arm(args, rank: int, world: int = 1) -> None:
     if rank != 0:
         return
     _, threads, elems, x = oracle_gflops(60.0, args.steps + args.warmup)
@@ -204,7 +204,7 @@ def reference_arm(args, rank: int) -> None:
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": headline_config(args, world),
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -220,57 +220,109 @@ def _tuned(plan):
     return t.get("chosen") or t.get("cached")
 
 
-def ours_other(args, rank: int, world: int) -> None:
-    """Other configs (not the headline line): multi-pass 1D and the 2D SAR frame.
-    One step = every item forward and inverse; roofline with 16 B per element
-    per pass (two passes each)."""
+def _model_record(plan, n: int, batch: int):
+    """The autotuner's model step for a single-pass plan (Sec. 3.2): the
+    shortest path over the measured per-(radix, start stage) costs, its
+    predicted cost per element, and the whole-pass times the runtime
+    validation measured on the trial batch: the default schedule's (the
+    first candidate) and the model's (a candidate of its own only where it
+    differs from the default; otherwise the two are the same plan)."""
+    from paper_1505_08067_gb300 import gbfft
+    t = plan.describe().get("tuning") or {}
+    m = t.get("model")
+    if not m:
+        return None
+    cands = t.get("candidates") or []
+    default_ms = cands[0]["ms"] if cands else None
+    model_ms = None
+    for c in cands[1:]:
+        if c["opts"].get("schedule"):
+            model_ms = c["ms"]
+    default = gbfft.fft_plan_dry_run(n, batch)["passes"][0]["radices"]
+    return {"model_schedule": m["schedule"], "predicted_ns_per_element": m["cost_ns_per_element"],
+            "default_schedule": default, "model_equals_default": model_ms is None,
+            "timed_ms_default": default_ms,
+            "timed_ms_model": default_ms if model_ms is None else model_ms,
+            "trial_batch": t.get("trial_batch"),
+            "chosen_radices": plan.describe()["passes"][0]["radices"],
+            "chosen": t.get("chosen")}
+
+
+def _free_device_memory():
+    import gc
+
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+SECTION_DESC = {
+    "multipass": ("large multi-pass 1D complex64 FFTs: N=2^20 batch 64, N=2^22 batch 16, "
+                  "N=2^24 batch 4 (2^26 elements each), forward and inverse, FP32"),
+    "sar": ("2D SAR frame 4096 azimuth x 8192 range complex64 (LFM chirp echoes BT=500, "
+            "50 scatterers, SNR 10 dB), row then column FFTs, forward and inverse, FP32"),
+    "tc": ("batched 1D complex64 FFT N=4096 batch=32768 (2^27 elements, uniform plus a "
+           "1e-3 tone): FP32 path and the tensor-core classes FP16, BF16, split BF16x3, "
+           "forward and inverse"),
+}
+TC_BOUNDS = {"tc_fp16": 2e-3, "tc_bf16": 2e-3, "tc_bf16x3": 5e-6 * 12}
+
+
+def section_items(kind: str, args, x_reuse=None) -> dict:
+    """Multi-pass 1D (cfg3), the 2D SAR frame (cfg3) or the tensor-core class
+    (cfg4): every item forward and inverse per step; per item the median
+    CUDA-event time of its launch sequence and its fraction of the HBM
+    roofline at 16 B per element per pass.  Clocks are sampled during the
+    timed steps."""
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     from paper_1505_08067_gb300 import gbfft, synth
 
-    if args.workload == "tc":
+    if kind == "tc":
         items = [((4096,), 2 ** (TOTAL_LOG - 12))]
-        desc = (f"batched 1D complex64 FFT N=4096 batch={2 ** (TOTAL_LOG - 12)} (2^{TOTAL_LOG} "
-                "elements): FP32 path and the tensor-core classes (FP16, BF16, split BF16x3), "
-                "forward and inverse")
-    elif args.workload == "multipass":
+    elif kind == "multipass":
         items = [((2 ** 20,), 64), ((2 ** 22,), 16), ((2 ** 24,), 4)]
-        desc = ("large multi-pass 1D complex64 FFTs: N=2^20 batch 64, N=2^22 batch 16, "
-                "N=2^24 batch 4 (2^26 elements each), forward and inverse")
     else:
         items = [((4096, 8192), 1)]
-        desc = ("2D SAR frame 4096 azimuth x 8192 range complex64 (LFM chirp echoes, "
-                "50 scatterers, SNR 10 dB), forward and inverse")
     if args.only:
         items = [it for it in items if int(np.log2(np.prod(it[0]))) == args.only] or items
     dev = torch.device("cuda", torch.cuda.current_device())
     E = max(int(np.prod(s)) * b for s, b in items)
-    if args.workload == "sar":
+    tone_bins = None
+    if kind == "sar":
         x = torch.from_numpy(synth.sar_frame(31).reshape(-1)).to(dev)
-    elif args.workload == "tc":
+        data = "synth.sar_frame seed 31"
+    elif kind == "tc":
         xt, tone_bins = synth.buried_tone(4, E // 4096, 4096)
         x = torch.from_numpy(xt.reshape(-1)).to(dev)
         del xt
+        data = "synth.buried_tone seed 4 (iid U[-1,1] plus a 1e-3 tone at a seeded bin)"
+    elif x_reuse is not None and x_reuse.numel() >= E:
+        x = x_reuse[:E]
+        data = "iid U[-1,1] (the headline's seed-2 input, first 2^26 elements)"
     else:
         x = torch.from_numpy(synth.uniform(3, 1, E)[0]).to(dev)
+        data = "iid U[-1,1] seed 3"
     y = torch.empty_like(x)
     plans, order = {}, []
-    precs = [0, 1, 2, 3] if args.workload == "tc" else [0]
+    precs = [0, 1, 2, 3] if kind == "tc" else [0]
+    t_plan = time.perf_counter()
     for shape, batch in items:
         for prec in precs:
             for d in DIRS:
-                key = (shape, d, prec)
                 opts = {"epilogue": args.epilogue} if args.epilogue else {}
                 if args.variant and prec == 0:
                     opts["variant"] = args.variant
                 if args.tile and prec == 0:
                     opts["tile"] = args.tile
                 opts["autotune"] = args.autotune if prec == 0 else 0
+                key = (shape, d, prec)
                 plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, prec,
                                         **opts)
                 order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
+    t_plan = time.perf_counter() - t_plan
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         for key, e, _lg in order:
@@ -278,12 +330,12 @@ def ours_other(args, rank: int, world: int) -> None:
     torch.cuda.synchronize()
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in order] for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
+    sampler = ClockSampler(gpu_id_of(dev))
+    sampler.start()
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     bnd = torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed_steps")  # lets ncu select the timed launches only
+    torch.cuda.nvtx.range_push("timed_steps")
     a.record(stream)
     for s in range(args.steps):
         for i, (key, e, _lg) in enumerate(order):
@@ -293,6 +345,7 @@ def ours_other(args, rank: int, world: int) -> None:
     bnd.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    clocks = sampler.stop()
     ms = a.elapsed_time(bnd)
     flops = sum(5.0 * e * lg for _k, e, lg in order)
     peaks = load_peaks()
@@ -300,30 +353,40 @@ def ours_other(args, rank: int, world: int) -> None:
     for i, (key, e, lg) in enumerate(order):
         t = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
         passes = len(plans[key].describe()["passes"])
-        pname = ["fp32", "tc_fp16", "tc_bf16", "tc_bf16x3"][key[2]]
+        pname = PREC_NAMES[key[2]]
+        gbs = 16.0 * passes * e / (t * 1e-3) / 1e9
         per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'} {pname}"] = {
             "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
-            "passes": passes, "gbs": round(16.0 * passes * e / (t * 1e-3) / 1e9, 1),
-            "frac": round(16.0 * passes * e / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+            "passes": passes, "gbs": round(gbs, 1), "frac": round(gbs / peaks["hbm_gbs"], 4),
             "tuned": _tuned(plans[key])}
-    accuracy = _tc_accuracy(gbfft, x, tone_bins) if args.workload == "tc" else None
-    if rank == 0:
-        tot_bytes = sum(16.0 * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
-        line = {
-            "metric": METRIC, "value": world * flops * args.steps / (ms * 1e-3) / 1e9,
-            "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "dtype": "f32+tc" if args.workload == "tc" else "f32", "data": "synthetic",
-            "config": {"workload": desc},
-            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                         "achieved": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9, 1),
-                         "frac": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
-            "per_item": per}
-        if accuracy:
-            line["accuracy_vs_fp32"] = accuracy
-        print(json.dumps(line))
+    tot_bytes = sum(16.0 * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
+    launches = sum(plans[k].launch_count for k, _e, _l in order) * args.steps
+    out = {
+        "workload": SECTION_DESC[kind], "data": data, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "gflops": flops * args.steps / (ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                     "achieved": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9, 1),
+                     "frac": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                     "alg_bytes": "16 B per element per pass"},
+        "per_item": per, "clocks": clocks, "gpu_launches": launches,
+        "plan_create_s": round(t_plan, 2),
+        "l2": "inputs of 256 MiB to 1 GiB per launch, larger than L2; no flush"}
+    if kind == "tc":
+        acc = _tc_accuracy(gbfft, x, tone_bins)
+        for name, rec in acc.items():
+            rec["bound"] = TC_BOUNDS[name]
+            rec["within_bound"] = rec["rel_l2_max"] <= TC_BOUNDS[name]
+        out["accuracy_vs_fp32"] = acc
+        fp32 = {d: per[f"4096 {d} fp32"]["ms"] for d in ("fwd", "inv")}
+        out["vs_fp32"] = {p: {d: round(fp32[d] / per[f"4096 {d} {p}"]["ms"], 3)
+                              for d in ("fwd", "inv")} for p in ("tc_fp16", "tc_bf16", "tc_bf16x3")}
     for p in plans.values():
         p.close()
+    del x, y
+    return out
+
+
+PREC_NAMES = ["fp32", "tc_fp16", "tc_bf16", "tc_bf16x3"]
 
 
 def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: float = 1e-3):
@@ -337,7 +400,7 @@ def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: floa
 
     xs = x[:count * n]
     outs = {}
-    for prec, name in ((0, "fp32"), (1, "tc_fp16"), (2, "tc_bf16"), (3, "tc_bf16x3")):
+    for prec, name in enumerate(PREC_NAMES):
         with gbfft.Plan(n, count, -1, prec) as p:
             outs[name] = p.execute(xs).cpu().numpy().reshape(count, n).astype(np.complex128)
             torch.cuda.synchronize()
@@ -352,13 +415,13 @@ def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: floa
     return acc
 
 
-def ours_serve(args, rank: int, world: int) -> None:
-    """Serving: a Poisson stream of FFT jobs, sizes
-    log-uniform over N = 2^8..2^22, batch 1..256, forward / inverse 50/50, 80%
-    FP32 and 20% tensor-core class (those take N = 256 or 4096, the lengths the
-    class covers), admitted under a 64 GB budget.  Offered load: algorithmic
-    bytes per second = `load` x measured HBM bandwidth.  Inputs are slices of
-    one seeded device buffer; outputs rotate through a ring that is reused only
+def section_serve(args, jobs: int, load: float) -> dict:
+    """Serving (cfg5): a Poisson stream of FFT jobs, sizes log-uniform over
+    N = 2^8..2^22, batch 1..256, forward / inverse 50/50, 80% FP32 and 20%
+    tensor-core class (those take N = 256 or 4096, the lengths the class
+    covers), admitted under a 64 GB budget.  Offered load: algorithmic bytes
+    per second = `load` x measured HBM bandwidth.  Inputs are slices of one
+    seeded device buffer; outputs rotate through a ring that is reused only
     after the job holding it completes.  Reports p50/p99 latency and aggregate
     GFLOP/s (5 N log2 N of completed jobs over the wall time of the stream)."""
     import threading
@@ -370,7 +433,7 @@ def ours_serve(args, rank: int, world: int) -> None:
     from paper_1505_08067_gb300 import gbfft, synth
 
     rng = np.random.default_rng(5)
-    njobs = args.jobs
+    njobs = jobs
     logn = rng.integers(8, 23, njobs)
     batch = rng.integers(1, 257, njobs)
     dirs = np.where(rng.random(njobs) < 0.5, -1, 1)
@@ -380,7 +443,7 @@ def ours_serve(args, rank: int, world: int) -> None:
     passes = np.where(logn > 14, 2, 1)
     alg_bytes = 16.0 * passes * elems
     peaks = load_peaks()
-    rate = args.load * peaks["hbm_gbs"] * 1e9 / alg_bytes.mean()      # jobs per second
+    rate = load * peaks["hbm_gbs"] * 1e9 / alg_bytes.mean()            # jobs per second
     gaps = rng.exponential(1.0 / rate, njobs)
     dev = torch.device("cuda", torch.cuda.current_device())
     in_elems = 1 << 30                                                 # 8 GiB of inputs
@@ -390,6 +453,7 @@ def ours_serve(args, rank: int, world: int) -> None:
         xin[off:off + chunk.numel()].copy_(chunk)
     ring_elems = 6 << 30                                               # 48 GiB of outputs
     yout = torch.empty(ring_elems, dtype=torch.complex64, device=dev)
+    torch.cuda.synchronize()
     srv = gbfft.fft_server_create(memory_budget_bytes=64 * 10 ** 9, streams=args.streams,
                                   strict_order=int(args.strict_order))
     # warm the plans of every key outside the measured stream
@@ -401,7 +465,6 @@ def ours_serve(args, rank: int, world: int) -> None:
     lock = threading.Lock()
     results = []
     done_flag = threading.Event()
-
     errors = []
 
     def waiter():
@@ -423,21 +486,27 @@ def ours_serve(args, rank: int, world: int) -> None:
             done_flag.set()
 
     base_stats = gbfft.fft_server_stats(srv)
+    sampler = ClockSampler(gpu_id_of(dev))
+    sampler.start()
     th = threading.Thread(target=waiter)
     th.start()
     ring = 0
+    ring_waits = 0
     t0 = time.perf_counter()
     t_next = t0
     for j in range(njobs):
         need = int(elems[j])
         if ring + need > ring_elems:
             ring = 0
+        waited = False
         while True:                 # the ring slice must be free
             with lock:
                 busy = any(not (ring + need <= s or ring >= e) for _, s, e in outstanding)
             if not busy or errors:
                 break
+            waited = True
             time.sleep(0.0002)
+        ring_waits += waited
         t_next += gaps[j]
         while time.perf_counter() < t_next:
             pass
@@ -451,41 +520,50 @@ def ours_serve(args, rank: int, world: int) -> None:
     t_sub = time.perf_counter() - t0
     done_flag.set()
     th.join()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
     if errors:
         raise RuntimeError("serving waiter failed: " + errors[0])
-    wall = time.perf_counter() - t0
     stats = gbfft.fft_server_stats(srv)
     gbfft.fft_server_destroy(srv)
     lat = np.array([r["latency_ms"] for r in results if r["status"] == 0])
+    queue = np.array([r["queue_ms"] for r in results if r["status"] == 0])
     ok = sum(r["status"] == 0 for r in results)
     status_counts = {}
     for r in results:
         status_counts[str(r["status"])] = status_counts.get(str(r["status"]), 0) + 1
     flops = float(np.sum(5.0 * elems * logn))
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": flops / wall / 1e9, "unit": "GFLOP/s", "n_gpus": world,
-            "higher_is_better": True, "scaling": "weak", "dtype": "f32+tc", "data": "synthetic",
-            "config": {"workload": "serving: Poisson stream of FFT jobs, N = 2^8..2^22, "
-                                   "batch 1..256, 64 GB budget",
-                       "jobs": njobs, "offered_load_frac_of_hbm": args.load,
-                       "offered_jobs_per_s": rate, "streams": args.streams,
-                       "budget_bytes": 64 * 10 ** 9, "mean_job_elements": float(elems.mean()),
-                       "admission": "strict arrival order" if args.strict_order else "backfilling",
-                       "tc_share": float((prec > 0).mean())},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean": float(lat.mean()), "max": float(lat.max())},
-            "completed": int(ok), "waited": len(results), "status_counts": status_counts,
-            "submit_s": t_sub, "wall_s": wall,
-            "achieved_alg_gbs": float(alg_bytes.sum() / wall / 1e9),
-            "server": {k: stats[k] - base_stats.get(k, 0) if k in ("launches", "groups",
-                       "coalesced_jobs", "completed", "backfilled_jobs") else stats[k]
-                       for k in ("launches", "groups", "coalesced_jobs", "completed",
-                                 "backfilled_jobs", "peak_bytes_in_flight",
-                                 "workspace_allocations")}}))
+    offered_s = float(np.sum(gaps))
+    del xin, yout
+    return {
+        "workload": "serving: Poisson stream of FFT jobs, N = 2^8..2^22 (tensor-core jobs "
+                    "N = 2^8 or 2^12), batch 1..256, 50/50 forward/inverse, 80% FP32 / 20% "
+                    "tensor-core class, 64 GB budget",
+        "jobs": njobs, "offered_load_frac_of_hbm": load, "offered_jobs_per_s": rate,
+        "streams": args.streams,
+        "admission": "strict arrival order" if args.strict_order else "backfilling",
+        "tc_share": float((prec > 0).mean()), "mean_job_elements": float(elems.mean()),
+        "gflops": flops / wall / 1e9,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_ms": {"p50": float(np.percentile(queue, 50)), "p99": float(np.percentile(queue, 99))},
+        "completed": int(ok), "waited": len(results), "status_counts": status_counts,
+        "submit_s": t_sub, "offered_s": offered_s, "wall_s": wall,
+        "submitter_ring_waits": int(ring_waits),
+        "offered_alg_gbs": float(alg_bytes.sum() / offered_s / 1e9),
+        "achieved_alg_gbs": float(alg_bytes.sum() / wall / 1e9),
+        "achieved_frac_of_hbm": float(alg_bytes.sum() / wall / 1e9 / peaks["hbm_gbs"]),
+        "all_offered_served": bool(wall <= offered_s * 1.05 and ok == njobs),
+        "clocks": clocks,
+        "server": {k: stats[k] - base_stats.get(k, 0) if k in ("launches", "groups",
+                   "coalesced_jobs", "completed", "backfilled_jobs", "host_launch_s",
+                   "group_stream_s") else stats[k]
+                   for k in ("launches", "groups", "coalesced_jobs", "completed",
+                             "backfilled_jobs", "peak_bytes_in_flight",
+                             "workspace_allocations", "host_launch_s", "group_stream_s")}}
 
 
-def ours_compress(args, rank: int, world: int) -> None:
+def section_compress(args) -> dict:
     """SAR range + azimuth compression of one 4096 (azimuth) x 8192 (range)
     raw frame: two fused convolution passes (forward FFT, matched filter,
     inverse FFT per line), the azimuth pass with one filter per range bin.
@@ -534,8 +612,8 @@ def ours_compress(args, rank: int, world: int) -> None:
     sampler = ClockSampler(gpu_id_of(dev))
     sampler.start()
     ms_full = timed(full, args.steps)
-    clocks = sampler.stop()
     ms_rng = timed(rng_only, args.steps)
+    clocks = sampler.stop()
     ms_az = max(ms_full - ms_rng, 1e-6)
     # end to end: pinned host frame in, compressed frame out
     h_in = torch.from_numpy(frame.reshape(-1)).pin_memory()
@@ -555,50 +633,48 @@ def ours_compress(args, rank: int, world: int) -> None:
     peaks = load_peaks()
     g_rng = 16.0 * E / (ms_rng * 1e-3) / 1e9
     g_az = 24.0 * E / (ms_az * 1e-3) / 1e9
-    ms_max, fps = replica_throughput(ms_full, flops, world, dev)
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": fps / 1e9, "unit": "GFLOP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic: 50 point scatterers, LFM range chirp BT=500, range-dependent "
-                    "azimuth chirps of 512 samples, SNR 10 dB (seed 31)",
-            "config": {"workload": "SAR range + azimuth compression, 4096 x 8192 complex64 frame, "
-                                   "per-range-bin azimuth filters", "variant": args.variant,
-                       "l2": "frame and azimuth filters 256 MiB each, larger than L2; no flush"},
-            "frames_per_s": 1e3 / ms_full,
-            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                         "kernel": "stockham_conv (azimuth pass)", "achieved": round(g_az, 1),
-                         "frac": round(g_az / peaks["hbm_gbs"], 4), "traffic": None,
-                         "alg_bytes_per_launch": 24.0 * E},
-            "passes": {"range": {"ms": round(ms_rng, 4), "gbs": round(g_rng, 1),
-                                 "frac": round(g_rng / peaks["hbm_gbs"], 4), "alg_bytes": 16.0 * E},
-                       "azimuth": {"ms": round(ms_az, 4), "gbs": round(g_az, 1),
-                                   "frac": round(g_az / peaks["hbm_gbs"], 4),
-                                   "alg_bytes": 24.0 * E}},
-            "e2e": {"value": flops / (ms_e2e * 1e-3) / 1e9, "unit": "GFLOP/s",
-                    "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * E,
-                    "api": "fft_execute_host"},
-            "clocks": clocks, "gpu_launches": 2 * args.steps}))
     full.close()
     rng_only.close()
+    del x, y, hr, ha
+    return {
+        "workload": "SAR range + azimuth compression, 4096 x 8192 complex64 frame, "
+                    "per-range-bin azimuth filters",
+        "data": "synthetic: 50 point scatterers, LFM range chirp BT=500, range-dependent "
+                "azimuth chirps of 512 samples, SNR 10 dB (seed 31)",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_frame": ms_full,
+        "frames_per_s": 1e3 / ms_full, "gflops": flops / (ms_full * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                     "kernel": "stockham_conv (azimuth pass)", "achieved": round(g_az, 1),
+                     "frac": round(g_az / peaks["hbm_gbs"], 4), "alg_bytes_per_launch": 24.0 * E},
+        "passes": {"range": {"ms": round(ms_rng, 4), "gbs": round(g_rng, 1),
+                             "frac": round(g_rng / peaks["hbm_gbs"], 4), "alg_bytes": 16.0 * E},
+                   "azimuth": {"ms": round(ms_az, 4), "gbs": round(g_az, 1),
+                               "frac": round(g_az / peaks["hbm_gbs"], 4), "alg_bytes": 24.0 * E}},
+        "e2e": {"value": flops / (ms_e2e * 1e-3) / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": 8 * E, "d2h_bytes_per_step": 8 * E,
+                "api": "fft_execute_host"},
+        "clocks": clocks, "gpu_launches": 2 * args.steps,
+        "l2": "frame and azimuth filters 256 MiB each, larger than L2; no flush"}
 
 
-def ours_small(args, rank: int, world: int) -> None:
-    """Small batch: N = 1024, batch 64 (512 KiB), launch-latency bound.
-    Device time per call of fft_execute (one kernel launch) and of
-    fft_execute_graph (the same launch replayed from a CUDA graph), with the
-    calls back to back on one stream."""
+def section_small(args) -> dict:
+    """Small batch (cfg1): N = 1024, batch 64 (512 KiB), launch-latency bound.
+    Per call of fft_execute (one kernel launch), fft_execute_graph (the same
+    launch replayed from a CUDA graph) and fft_execute_noalloc: measured from
+    C by the library's call_latency program (host enqueue time, device time
+    back to back, and the median round trip of single synchronised calls,
+    beside an empty kernel's), and through this Python binding."""
     import torch
 
+    from paper_1505_08067_gb300 import build as gbuild
     from paper_1505_08067_gb300 import gbfft, synth
     dev = torch.device("cuda", torch.cuda.current_device())
     x = torch.from_numpy(synth.uniform(1, 64, 1024)).to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
-    out = {}
+    py = {}
     with gbfft.Plan(1024, 64, -1) as p:
-        for name, fn in (("execute", p.execute), ("graph", p.execute_graph)):
+        for name, fn in (("fft_execute", p.execute), ("fft_execute_graph", p.execute_graph)):
             for _ in range(20):
                 fn(x, y, stream)
             torch.cuda.synchronize()
@@ -613,12 +689,29 @@ def ours_small(args, rank: int, world: int) -> None:
             torch.cuda.synchronize()
             host = (time.perf_counter() - t0) / reps * 1e6
             dev_us = a.elapsed_time(b_) / reps * 1e3
-            out[name] = {"us_per_call_device": round(dev_us, 3), "us_per_call_host": round(host, 3),
-                         "gflops": round(5.0 * 1024 * 10 * 64 / (dev_us * 1e-6) / 1e9, 1)}
-    if rank == 0:
-        print(json.dumps({"metric": METRIC, "unit": "us per transform batch", "n_gpus": world,
-                          "config": {"workload": "N=1024 batch 64 complex64 forward (512 KiB)"},
-                          "calls": out}))
+            py[name] = {"device_us": round(dev_us, 3), "host_us": round(host, 3),
+                        "gflops": round(5.0 * 1024 * 10 * 64 / (dev_us * 1e-6) / 1e9, 1)}
+    del x, y
+    c = None
+    if not os.path.exists(gbuild.CALL_LATENCY):
+        raise RuntimeError(f"{gbuild.CALL_LATENCY} is missing: build the package first")
+    env = dict(os.environ)
+    env["CUDA_VISIBLE_DEVICES"] = env.get("CUDA_VISIBLE_DEVICES", str(torch.cuda.current_device()))
+    r = subprocess.run([gbuild.CALL_LATENCY, "1024", "64", "2000"], capture_output=True,
+                       text=True, timeout=300)
+    if r.returncode != 0:
+        raise RuntimeError(f"call_latency failed ({r.returncode}): {r.stderr.strip()[-400:]}")
+    c = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"workload": "N=1024 batch 64 complex64 forward (512 KiB), calls back to back on "
+                        "one stream", "from_c": c, "through_python_ctypes": py}
+
+
+def headline_config(args, world: int) -> dict:
+    return {"workload": WORKLOAD, "sizes": [2 ** l for l in LOGS],
+            "elements_per_launch": 2 ** TOTAL_LOG, "precision": "FP32",
+            "l2": "inputs larger than L2 (1 GiB per launch), no flush",
+            "autotune": bool(args.autotune), "variant": args.variant,
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def ours(args, rank: int, world: int) -> None:
@@ -693,6 +786,7 @@ def ours(args, rank: int, world: int) -> None:
     sha = kernel_source_sha()
     traffic = load_traffic(sha)
     per_size = {}
+    model = {}
     for lg in LOGS:
         tms = statistics.median(per_launch[(lg, -1)] + per_launch[(lg, +1)])
         per_size[f"2^{lg}"] = {"ms": round(tms, 4),
@@ -701,12 +795,16 @@ def ours(args, rank: int, world: int) -> None:
                                "frac": round(alg_bytes / (tms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                                "radices": plans[(lg, -1)].describe()["passes"][0]["radices"],
                                "tuned": _tuned(plans[(lg, -1)])}
+        rec = _model_record(plans[(lg, -1)], 2 ** lg, E >> lg)
+        if rec:
+            model[f"2^{lg}"] = rec
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
         h_in = torch.from_numpy(x_np).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
+
         def e2e_step():
             for key in order:
                 plans[key].execute_host(h_in, h_out, x, y, stream)
@@ -728,7 +826,11 @@ def ours(args, rank: int, world: int) -> None:
         e2e = {"value": world * step_flops(E) * k2 / (float(t2.item()) * 1e-3) / 1e9,
                "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * E * len(order),
                "d2h_bytes_per_step": 8 * E * len(order), "steps": k2,
-               "api": "fft_execute_host (pinned host buffers, chunked H2D/kernel/D2H overlap)"}
+               "api": "fft_execute_host (pinned host buffers, chunked H2D/kernel/D2H overlap)",
+               "host_numa": host_numa_record(dev)}
+        del h_in, h_out
+    for p in plans.values():
+        p.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -738,6 +840,39 @@ def ours(args, rank: int, world: int) -> None:
                "kind": "oracle",
                "sample": f"one sweep step on {elems} of the 2^27 elements per size and direction"}
 
+    configs = None
+    if args.sections and world == 1:
+        configs = {}
+        x_keep = x
+        del y
+        _free_device_memory()
+        for name in args.sections:
+            t0 = time.perf_counter()
+            try:
+                if name == "small":
+                    rec = section_small(args)
+                elif name == "multipass":
+                    rec = section_items("multipass", args, x_keep)
+                elif name == "sar":
+                    rec = section_items("sar", args)
+                elif name == "tc":
+                    rec = section_items("tc", args)
+                elif name == "serve":
+                    rec = section_serve(args, args.serve_jobs, args.load)
+                elif name == "sar_compress":
+                    rec = section_compress(args)
+                else:
+                    rec = {"error": f"unknown section {name}"}
+            except Exception as exc:  # recorded in the line, not hidden
+                rec = {"error": f"{type(exc).__name__}: {exc}"}
+            rec["section_s"] = round(time.perf_counter() - t0, 1)
+            configs[SECTION_KEYS.get(name, name)] = rec
+            if name == "multipass":
+                x_keep = None
+            _free_device_memory()
+    elif args.sections:
+        configs = {"skipped": "the per-configuration sections run at n_gpus = 1 only"}
+
     if rank == 0:
         frac = achieved / peaks["hbm_gbs"]
         line = {
@@ -745,11 +880,7 @@ def ours(args, rank: int, world: int) -> None:
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: iid U[-1,1] complex64 (seed 2), generated on the host",
-            "config": {"workload": WORKLOAD, "sizes": [2 ** l for l in LOGS],
-                       "elements_per_launch": E, "precision": "FP32",
-                       "l2": "inputs larger than L2 (1 GiB per launch), no flush",
-                       "autotune": bool(args.autotune), "variant": args.variant,
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": headline_config(args, world),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(frac, 4),
                          "traffic": traffic, "kernel": "stockham_pass",
@@ -757,14 +888,56 @@ def ours(args, rank: int, world: int) -> None:
                          "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)"},
             "pct_hbm_roofline": round(100 * frac, 2),
             "per_size": per_size,
+            "autotune_model": model,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,
         }
+        if configs is not None:
+            line["configs"] = configs
         print(json.dumps(line))
-    for p in plans.values():
-        p.close()
+
+
+SECTION_KEYS = {"small": "cfg1_small_call", "multipass": "cfg3_multipass", "sar": "cfg3_sar_frame",
+                "tc": "cfg4_tensor_core", "serve": "cfg5_serving",
+                "sar_compress": "sar_compression"}
+DEFAULT_SECTIONS = "small,multipass,sar,tc,serve,sar_compress"
+
+
+def host_numa_record(dev) -> dict:
+    """Where the pinned host buffers of the e2e leg live relative to the GPU:
+    the NUMA node the GPU's PCI/C2C device reports, the nodes this process may
+    allocate on, and the CPUs it runs on (read from sysfs and procfs; nothing is
+    changed)."""
+    rec = {}
+    try:
+        import torch
+        props = torch.cuda.get_device_properties(dev)
+        bus = getattr(props, "pci_bus_id", None)
+        dom = getattr(props, "pci_domain_id", None)
+        devid = getattr(props, "pci_device_id", None)
+        if bus is not None:
+            addr = f"{dom or 0:04x}:{bus:02x}:{devid or 0:02x}.0"
+            p = f"/sys/bus/pci/devices/{addr}/numa_node"
+            rec["gpu_pci"] = addr
+            if os.path.exists(p):
+                rec["gpu_numa_node"] = int(open(p).read().strip())
+    except Exception as exc:
+        rec["gpu_error"] = str(exc)
+    try:
+        for line in open("/proc/self/status"):
+            if line.startswith(("Mems_allowed_list", "Cpus_allowed_list")):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    except Exception:
+        pass
+    try:
+        nodes = sorted(d for d in os.listdir("/sys/devices/system/node") if d.startswith("node"))
+        rec["host_numa_nodes"] = nodes
+    except Exception:
+        pass
+    return rec
 
 
 def main() -> None:
@@ -783,8 +956,8 @@ def main() -> None:
     ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve", "small",
                                            "sar_compress"],
                     default="sweep",
-                    help="sweep: the headline batched N=2^8..2^14 line; multipass / sar: "
-                         "the large-transform configs, reported as separate lines")
+                    help="sweep: the headline batched N=2^8..2^14 line with every other "
+                         "configuration as a section; the others: one configuration alone")
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--only", type=int, default=0, help="run only N = 2^ONLY (profiling)")
     ap.add_argument("--tile", type=int, default=0,
@@ -799,7 +972,14 @@ def main() -> None:
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sections", default=DEFAULT_SECTIONS,
+                    help="sweep workload: comma-separated per-configuration sections timed after "
+                         "the headline and reported under 'configs' (small, multipass, sar, tc, "
+                         "serve, sar_compress), or 'none'")
+    ap.add_argument("--serve-jobs", type=int, default=4000,
+                    help="jobs of the serving section of the sweep workload")
     args = ap.parse_args()
+    args.sections = [] if args.sections in ("", "none") else args.sections.split(",")
     if args.warmup < 3:
         args.warmup = 3
     if args.only:
@@ -808,7 +988,7 @@ def main() -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
-        reference_arm(args, rank)
+        reference_arm(args, rank, world)
         return
     import torch
     if world > 1:
@@ -817,14 +997,19 @@ def main() -> None:
         dist.init_process_group("nccl")
     if args.workload == "sweep":
         ours(args, rank, world)
-    elif args.workload == "serve":
-        ours_serve(args, rank, world)
-    elif args.workload == "small":
-        ours_small(args, rank, world)
-    elif args.workload == "sar_compress":
-        ours_compress(args, rank, world)
     else:
-        ours_other(args, rank, world)
+        # one configuration alone, printed as its own line (not the headline)
+        if args.workload == "serve":
+            rec = section_serve(args, args.jobs, args.load)
+        elif args.workload == "small":
+            rec = section_small(args)
+        elif args.workload == "sar_compress":
+            rec = section_compress(args)
+        else:
+            rec = section_items(args.workload, args)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "n_gpus": world, "section": args.workload,
+                              **rec}))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -368,6 +368,10 @@ typedef struct {
   double wall_s;            /* first submit -> last completion */
   double gflops;            /* 5 N log2 N of completed jobs / wall_s */
   uint64_t backfilled_jobs; /* jobs admitted ahead of an older waiting job */
+  double host_launch_s;     /* worker thread time spent enqueueing groups */
+  double group_stream_s;    /* sum over completed groups of the time from their first
+                               launch to their completion on their stream (CUDA events);
+                               above wall_s when groups overlap on the device */
 } fft_server_stats_t;
 
 /* Start a server on the current device (options may be NULL). */

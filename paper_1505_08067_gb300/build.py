@@ -17,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libgbfft.so")
+MEASURE = os.path.join(HERE, "measure")
+CALL_LATENCY = os.path.join(OUT_DIR, "call_latency")  # C-side per-call timing of the ABI
 SOURCES = ["kernels.cu", "generic_rows.cu", "generic_cols.cu", "generic_transposing.cu",
            "shapes_contig.cu", "shapes_fourstep.cu", "kernels_tc.cu", "conv.cu", "noalloc.cu", "api.cpp",
            "exec.cpp", "server.cpp",
@@ -43,13 +45,16 @@ def _flags(src: str) -> list[str]:
 
 def _newest_input() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    paths += [os.path.join(MEASURE, f) for f in os.listdir(MEASURE)]
     paths.append(os.path.join(ROOT, "include", "gbfft.h"))
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
+    newest = _newest_input()
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest
+            and os.path.exists(CALL_LATENCY) and os.path.getmtime(CALL_LATENCY) >= newest):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     objdir = os.path.join(OUT_DIR, "obj")
@@ -74,6 +79,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    # the C timing program of the small-call path links the library just built
+    tmp = CALL_LATENCY + f".tmp{os.getpid()}"
+    cmd = [exe] + ARCH + ["-O2", "-std=c++17", "-I" + os.path.join(ROOT, "include"),
+                          os.path.join(MEASURE, "call_latency.cu"), "-o", tmp, "-L" + OUT_DIR,
+                          "-lgbfft", "-Xlinker", "-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"call_latency build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, CALL_LATENCY)
     return LIB
 
 

@@ -84,7 +84,8 @@ struct JobRec {
 
 struct Running {
   SchedGroup group;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr;  // recorded on the group's stream before its launches
+  cudaEvent_t done = nullptr;   // after them
 };
 
 }  // namespace
@@ -106,13 +107,15 @@ struct fft_server_s {
   std::unordered_map<uint64_t, JobRec> jobs;
   std::vector<Running> running;
   cudaMemPool_t ws_pool = nullptr;  // stream-ordered workspace allocations
-  std::vector<cudaEvent_t> free_events;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> free_events;  // (start, done) pairs
   uint64_t next_id = 1;
   uint64_t submitted = 0, completed = 0, failed = 0, launches = 0, coalesced = 0;
   std::vector<double> latencies;  // the most recent kLatencyWindow completions (a ring)
   size_t latency_next = 0;
   double first_submit = 0, last_done = 0, flops = 0;
   size_t ws_allocs = 0;
+  double host_launch_s = 0;   // worker time spent enqueueing groups
+  double group_stream_s = 0;  // sum over completed groups of start -> done on their stream
 
   fft_server_s(size_t budget, int max_group, size_t group_bytes, bool backfill)
       : sched(budget, max_group, group_bytes, backfill) {}
@@ -220,6 +223,20 @@ bool launch_group(fft_server_t s, Running& r) {
     if (s->stream_free[i] < s->stream_free[si]) si = i;
   cudaStream_t st = s->streams[si];
   s->stream_free[si] = std::max(s->stream_free[si], t) + g.cost;
+  if (s->free_events.empty()) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      if (a) cudaEventDestroy(a);
+      fail_all(FFT_ERR_CUDA);
+      return false;
+    }
+    s->free_events.emplace_back(a, b);
+  }
+  r.start = s->free_events.back().first;
+  r.done = s->free_events.back().second;
+  s->free_events.pop_back();
+  cudaEventRecord(r.start, st);
   cudaError_t e = cudaSuccess;
   if (pe->groupable && g.jobs.size() > 1) {
     // one coalesced launch per kMaxGroup jobs
@@ -263,16 +280,11 @@ bool launch_group(fft_server_t s, Running& r) {
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
+    s->free_events.emplace_back(r.start, r.done);
+    r.start = r.done = nullptr;
     fail_all(e == cudaErrorMemoryAllocation ? FFT_ERR_OUT_OF_MEMORY : FFT_ERR_CUDA);
     return false;
   }
-  if (s->free_events.empty()) {
-    cudaEvent_t ev;
-    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    s->free_events.push_back(ev);
-  }
-  r.done = s->free_events.back();
-  s->free_events.pop_back();
   cudaEventRecord(r.done, st);
   for (const SchedJob& j : g.jobs) s->jobs[j.id].t_launch = t;
   return true;
@@ -309,9 +321,14 @@ void worker_loop(fft_server_t s) {
         }
       }
       if (q != cudaSuccess) cudaGetLastError();
+      float gms = 0;
+      if (q == cudaSuccess && cudaEventElapsedTime(&gms, r.start, r.done) == cudaSuccess)
+        s->group_stream_s += gms * 1e-3;
+      else
+        cudaGetLastError();
       s->last_done = t;
       s->sched.finished(r.group);
-      s->free_events.push_back(r.done);
+      s->free_events.emplace_back(r.start, r.done);
       s->running.erase(s->running.begin() + i);
       progress = true;
     }
@@ -322,7 +339,10 @@ void worker_loop(fft_server_t s) {
            s->sched.next(g, now_s())) {
       Running r;
       r.group = g;
-      if (launch_group(s, r)) {
+      const double tl = now_s();
+      const bool launched = launch_group(s, r);
+      s->host_launch_s += now_s() - tl;
+      if (launched) {
         s->running.push_back(std::move(r));
       } else {
         s->sched.finished(g);
@@ -497,6 +517,8 @@ fft_status_t fft_server_stats(fft_server_t s, fft_server_stats_t* out) {
   out->budget_bytes = s->sched.budget();
   out->workspace_allocations = s->ws_allocs;
   out->backfilled_jobs = s->sched.backfilled();
+  out->host_launch_s = s->host_launch_s;
+  out->group_stream_s = s->group_stream_s;
   std::vector<double> l = s->latencies;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());
@@ -534,10 +556,15 @@ fft_status_t fft_server_destroy(fft_server_t s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
-  for (Running& r : s->running)
+  for (Running& r : s->running) {
+    if (r.start) cudaEventDestroy(r.start);
     if (r.done) cudaEventDestroy(r.done);
+  }
   if (s->ws_pool) cudaMemPoolDestroy(s->ws_pool);
-  for (cudaEvent_t ev : s->free_events) cudaEventDestroy(ev);
+  for (auto& ev : s->free_events) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
   for (auto& kv : s->plans) {
     cudaFree(kv.second->tables);
     delete kv.second;

@@ -81,7 +81,8 @@ class fft_server_stats_t(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("wall_s", ctypes.c_double), ("gflops", ctypes.c_double),
-                ("backfilled_jobs", ctypes.c_uint64)]
+                ("backfilled_jobs", ctypes.c_uint64), ("host_launch_s", ctypes.c_double),
+                ("group_stream_s", ctypes.c_double)]
 
 
 _lib = None

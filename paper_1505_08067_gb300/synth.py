@@ -70,11 +70,18 @@ def tones(seed: int, batch: int, n: int, ntones: int = 1) -> np.ndarray:
 def buried_tone(seed: int, batch: int, n: int, amplitude: float = 1e-3):
     """``uniform`` plus one tone of the given amplitude at a seeded bin per
     transform.  Returns (x complex64 (batch, n), bins int64 (batch,))."""
-    x = uniform(seed, batch, n).astype(np.complex128)
+    x = uniform(seed, batch, n)
     bins = np.random.default_rng(seed + 0x5EED).integers(0, n, size=batch)
-    for b in range(batch):
-        x[b] += amplitude * _exp_bins(bins[b:b + 1], n)[0]
-    return x.astype(np.complex64), bins
+    # exp(2 pi i m / n) for m < n, indexed by the integer-reduced phase k*j mod n:
+    # the same values _exp_bins forms, computed once
+    table = _exp_bins(np.ones(1, dtype=np.int64), n)[0]
+    j = np.arange(n, dtype=np.int64)
+    rows = max(1, (1 << 22) // max(n, 1))          # rows per chunk: bounded host memory
+    for b0 in range(0, batch, rows):
+        b1 = min(batch, b0 + rows)
+        tone = table[(bins[b0:b1, None].astype(np.int64) * j[None, :]) % n]
+        x[b0:b1] = (x[b0:b1].astype(np.complex128) + amplitude * tone).astype(np.complex64)
+    return x, bins
 
 
 def chirp(bt: float = 500.0, oversample: float = 1.2) -> np.ndarray:
