@@ -455,7 +455,8 @@ def section_serve(args, jobs: int, load: float) -> dict:
     yout = torch.empty(ring_elems, dtype=torch.complex64, device=dev)
     torch.cuda.synchronize()
     srv = gbfft.fft_server_create(memory_budget_bytes=64 * 10 ** 9, streams=args.streams,
-                                  strict_order=int(args.strict_order))
+                                  strict_order=int(args.strict_order),
+                                  large_group_log2=args.large_group_log2)
     # warm the plans of every key outside the measured stream
     keys = sorted(set(zip(logn.tolist(), dirs.tolist(), prec.tolist())))
     for lg, d, p in keys:
@@ -540,7 +541,7 @@ def section_serve(args, jobs: int, load: float) -> dict:
                     "N = 2^8 or 2^12), batch 1..256, 50/50 forward/inverse, 80% FP32 / 20% "
                     "tensor-core class, 64 GB budget",
         "jobs": njobs, "offered_load_frac_of_hbm": load, "offered_jobs_per_s": rate,
-        "streams": args.streams,
+        "streams": args.streams, "large_group_log2": args.large_group_log2,
         "admission": "strict arrival order" if args.strict_order else "backfilling",
         "tc_share": float((prec > 0).mean()), "mean_job_elements": float(elems.mean()),
         "gflops": flops / wall / 1e9,
@@ -951,6 +952,9 @@ def main() -> None:
     ap.add_argument("--load", type=float, default=0.5,
                     help="serve workload: offered algorithmic bytes/s as a fraction of HBM")
     ap.add_argument("--streams", type=int, default=4, help="serve workload: server streams")
+    ap.add_argument("--large-group-log2", type=int, default=0,
+                    help="serve workload: groups of at least 2^k elements run in order on the "
+                         "first stream (0: library default, -1: any stream)")
     ap.add_argument("--strict-order", action="store_true",
                     help="serve workload: admit strictly in arrival order (no backfilling)")
     ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve", "small",

@@ -240,8 +240,9 @@ fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_o
       return cuda_fail(e, "host-to-device copy");
     cudaEventRecord(plan->ev_h2d, plan->s_h2d);
     cudaStreamWaitEvent(plan->s_k, plan->ev_h2d, 0);
-    e = enqueue_passes(s, plan->launches, di + off, dout + off, wk ? wk + off : nullptr, b0, nb,
-                       plan->s_k);
+    // the chunks run one after the other on s_k, so each reuses the workspace
+    // from its start
+    e = enqueue_passes(s, plan->launches, di + off, dout + off, wk, b0, nb, plan->s_k);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     cudaEventRecord(plan->ev_k, plan->s_k);
     cudaStreamWaitEvent(plan->s_d2h, plan->ev_k, 0);

@@ -73,8 +73,27 @@ cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st) {
   return cudaSuccess;
 }
 
+static cudaError_t enqueue_range(const PlanSpec& s, const PassLaunch* launches, const void* in,
+                                 void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st);
+
 cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const void* in,
                            void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st) {
+  if (nb <= 0) return cudaSuccess;
+  if (s.chunk_batch <= 0 || nb <= s.chunk_batch)
+    return enqueue_range(s, launches, in, out, work, b0, nb, st);
+  // sub-batches in stream order, each reusing the workspace from its start
+  const int64_t E = s.dims == 1 ? s.n[0] : s.n[0] * s.n[1];
+  for (int64_t c = 0; c < nb; c += s.chunk_batch) {
+    const int64_t n = std::min(s.chunk_batch, nb - c);
+    cudaError_t e = enqueue_range(s, launches, static_cast<const cf*>(in) + c * E,
+                                  static_cast<cf*>(out) + c * E, work, b0 + c, n, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t enqueue_range(const PlanSpec& s, const PassLaunch* launches, const void* in,
+                                 void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st) {
   if (nb <= 0) return cudaSuccess;
   const int64_t E = s.dims == 1 ? s.n[0] : s.n[0] * s.n[1];
   for (int i = 0; i < s.passes.size(); ++i) {

@@ -18,8 +18,10 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
 // Enqueues the twiddle-table generation of `s` into `tables` on `st`.
 cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st);
 
-// Enqueues every pass for batch entries [b0, b0 + nb); `in`, `out` and `work`
-// already point at entry b0.
+// Enqueues every pass for batch entries [b0, b0 + nb); `in` and `out` already
+// point at entry b0, `work` holds min(nb, s.chunk_batch) entries (all nb when
+// the plan has no sub-batches) starting with entry b0.  Two-pass plans with
+// chunk_batch > 0 run in sub-batches of chunk_batch entries, in stream order.
 cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const void* in,
                            void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st);
 

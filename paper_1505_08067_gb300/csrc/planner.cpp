@@ -377,7 +377,11 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p2.conj_out = inv;
       s.passes.push_back(p1);
       s.passes.push_back(p2);
-      s.work_elems = batch * N;
+      // sub-batches keep the strided passes' working set bounded; the
+      // workspace holds one sub-batch
+      const int64_t chunk = two_pass_chunk(N);
+      s.chunk_batch = batch > chunk ? chunk : 0;
+      s.work_elems = std::min(batch, chunk) * N;
     }
   } else {
     const int64_t rows = n[0], cols = n[1];
@@ -513,6 +517,7 @@ std::string describe(const PlanSpec& s) {
     << ",\"precision\":" << s.precision << ",\"max_block_log2\":" << s.max_block_log2
     << ",\"generic\":" << (s.generic_only ? 1 : 0) << ",\"conv\":" << (s.conv ? 1 : 0)
     << ",\"workspace_bytes\":" << s.work_elems * 8 << ",\"table_elems\":" << s.table_elems
+    << ",\"chunk_batch\":" << s.chunk_batch
     << ",\"passes\":[";
   for (size_t i = 0; i < s.passes.size(); ++i) {
     const PassSpec& p = s.passes[i];

@@ -169,6 +169,9 @@ PlanEntry* plan_for(fft_server_t s, const JobKey& k, fft_status_t* st) {
     *st = FFT_ERR_CUDA;
     return nullptr;
   }
+  // jobs of any batch run the two-pass plans in sub-batches (the plan was made
+  // for the nominal batch, below the sub-batch size)
+  if (k.dims == 1 && pe->spec.work_elems > 0) pe->spec.chunk_batch = two_pass_chunk(elems);
   const PassSpec& p0 = pe->spec.passes[0];
   pe->groupable = k.dims == 1 && pe->spec.passes.size() == 1 && p0.kind == PASS_FFT &&
                   p0.batch_is_tiles && p0.tc_prec == 0;
@@ -218,9 +221,20 @@ bool launch_group(fft_server_t s, Running& r) {
     fail_all(pst);
     return false;
   }
-  size_t si = 0;  // the stream whose queued work is estimated to end first
-  for (size_t i = 1; i < s->streams.size(); ++i)
-    if (s->stream_free[i] < s->stream_free[si]) si = i;
+  // large groups in order on the first stream; the others on the stream
+  // whose queued work is estimated to end first (the first one too when
+  // there is no other, or when large groups are not set apart)
+  int64_t group_elems = 0;
+  for (const SchedJob& j : g.jobs) group_elems += job_elems(s->jobs[j.id].job) * j.batch;
+  const int lg = s->opt.large_group_log2 == 0 ? 23 : s->opt.large_group_log2;
+  const bool apart = lg > 0 && s->streams.size() > 1;
+  size_t si = 0;
+  if (!(apart && group_elems >= (int64_t(1) << std::min(lg, 62)))) {
+    const size_t first = apart ? 1 : 0;
+    si = first;
+    for (size_t i = first + 1; i < s->streams.size(); ++i)
+      if (s->stream_free[i] < s->stream_free[si]) si = i;
+  }
   cudaStream_t st = s->streams[si];
   s->stream_free[si] = std::max(s->stream_free[si], t) + g.cost;
   if (s->free_events.empty()) {
@@ -264,7 +278,9 @@ bool launch_group(fft_server_t s, Running& r) {
     for (const SchedJob& j : g.jobs) {
       const JobRec& rec = s->jobs[j.id];
       void* ws = nullptr;
-      const size_t wsb = (size_t)pe->work_per_entry * 8 * (size_t)rec.job.batch;
+      const int64_t ws_entries =
+          pe->spec.chunk_batch > 0 ? std::min(rec.job.batch, pe->spec.chunk_batch) : rec.job.batch;
+      const size_t wsb = (size_t)pe->work_per_entry * 8 * (size_t)ws_entries;
       if (wsb) {
         ws = ws_get(s, wsb, st);
         if (!ws) {
@@ -379,6 +395,8 @@ fft_status_t fft_server_create(fft_server_t* server, const fft_server_options_t*
   if (o.max_group <= 0) o.max_group = 256;
   if (o.max_running <= 0) o.max_running = 4 * o.streams;
   if (o.streams > 64) return set_error(FFT_ERR_INVALID_ARG, "at most 64 streams");
+  if (o.large_group_log2 < -1 || o.large_group_log2 > 40)
+    return set_error(FFT_ERR_INVALID_ARG, "large_group_log2 must be -1, 0 or 1..40");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -434,7 +452,10 @@ fft_status_t fft_server_submit(fft_server_t s, const fft_job_t* job, uint64_t* t
   if (((uintptr_t)job->in & 7) || ((uintptr_t)job->out & 7))
     return set_error(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned");
   const int64_t e = job_elems(*job) * job->batch;
-  const size_t ws = (size_t)probe.work_elems * 8 * (size_t)job->batch;
+  // workspace of one sub-batch (two-pass plans run large batches in sub-batches)
+  const int64_t ws_entries =
+      probe.work_elems > 0 ? std::min<int64_t>(job->batch, two_pass_chunk(job_elems(*job))) : 0;
+  const size_t ws = (size_t)probe.work_elems * 8 * (size_t)ws_entries;
   const size_t bytes = (size_t)e * 16 + (ws ? ws_class(ws) : 0);
   std::lock_guard<std::mutex> lock(s->mu);
   SchedJob sj;

@@ -58,7 +58,7 @@ class fft_server_options_t(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int),
                 ("max_group", ctypes.c_int), ("max_running", ctypes.c_int),
                 ("fail_workspace_alloc", ctypes.c_int), ("strict_order", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("large_group_log2", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class fft_job_t(ctypes.Structure):
@@ -443,9 +443,9 @@ class ConvPlan(Plan):
 
 def fft_server_create(memory_budget_bytes: int = 0, streams: int = 0, max_group: int = 0,
                       max_running: int = 0, fail_workspace_alloc: int = 0,
-                      strict_order: int = 0) -> int:
+                      strict_order: int = 0, large_group_log2: int = 0) -> int:
     o = fft_server_options_t(memory_budget_bytes, streams, max_group, max_running,
-                             fail_workspace_alloc, strict_order)
+                             fail_workspace_alloc, strict_order, large_group_log2)
     h = _vp()
     _check(load().fft_server_create(ctypes.byref(h), ctypes.byref(o)))
     return h.value

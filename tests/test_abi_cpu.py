@@ -80,7 +80,9 @@ def test_planner_limits(logn, batch):
         assert max(p["radices"]) <= p["R"]
         assert p["tiles_inner"] * p["G"] >= p["count_inner"]
     if logn > 14:
-        assert d["workspace_bytes"] == 8 * batch * 2 ** logn
+        chunk = max(1, 2 ** 28 // 2 ** logn)
+        assert d["workspace_bytes"] == 8 * min(batch, chunk) * 2 ** logn
+        assert d["chunk_batch"] == (chunk if batch > chunk else 0)
         p1, p2 = passes
         assert p1["L"] * p2["L"] == 2 ** logn and p1["epi"] == 4 and p2["smap"] == "cols"
 
@@ -140,3 +142,13 @@ def test_four_step_tile_widths(logn, split, g1, g2):
     assert p1["L"] == 2 ** split and (p1["G"], p2["G"]) == (g1, g2)
     d = g.fft_plan_dry_run(2 ** logn, 4, tile=2)
     assert [p["G"] for p in d["passes"]] == [min(2, g1), min(2, g2)]
+
+
+@pytest.mark.parametrize("logn,batch", [(22, 64), (22, 65), (22, 256), (20, 1024), (24, 17), (15, 9000)])
+def test_two_pass_sub_batches(logn, batch):
+    """Two-pass plans run batches above 2^28 elements in sub-batches of
+    max(1, 2^28 / N) transforms and hold one sub-batch of workspace."""
+    d = g.fft_plan_dry_run(2 ** logn, batch)
+    chunk = max(1, 2 ** 28 // 2 ** logn)
+    assert d["chunk_batch"] == (chunk if batch > chunk else 0)
+    assert d["workspace_bytes"] == 8 * min(batch, chunk) * 2 ** logn

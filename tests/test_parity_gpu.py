@@ -233,6 +233,27 @@ def test_full_size_multipass(gb, oracle, logn, batch):
     _full(gb, oracle, 2 ** logn, batch, 6000 + logn, samples=1)
 
 
+def test_two_pass_sub_batches(gb, oracle):
+    """N = 2^22 x 65 runs as sub-batches of 64 and 1 transforms sharing one
+    sub-batch of workspace: the transforms on both sides of the boundary, and
+    the same plan replayed from a CUDA graph."""
+    n, batch = 2 ** 22, 65
+    x_np = synth.uniform(6500, batch, n)
+    x = torch.from_numpy(x_np).cuda()
+    with gb.Plan(n, batch, -1) as p:
+        assert p.describe()["chunk_batch"] == 64
+        assert p.workspace_bytes == 8 * 64 * n
+        y = p.execute(x)
+        y2 = torch.empty_like(x)
+        p.execute_graph(x, y2)
+        torch.cuda.synchronize()
+    idx = np.array([0, 63, 64])
+    ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.fft_select(x_np, idx, -1)
+    assert np.max(oracle.rel_l2(ys, ref)) <= _tol(n)
+    assert torch.equal(y, y2)
+
+
 def test_sar_frame(gb, oracle):
     """The 4096 azimuth x 8192 range chirp frame, whole, against the oracle."""
     frame = synth.sar_frame(7000)[None]
