@@ -263,8 +263,9 @@ SECTION_DESC = {
     "sar": ("2D SAR frame 4096 azimuth x 8192 range complex64 (LFM chirp echoes BT=500, "
             "50 scatterers, SNR 10 dB), row then column FFTs, forward and inverse, FP32"),
     "tc": ("batched 1D complex64 FFT N=4096 batch=32768 (2^27 elements, uniform plus a "
-           "1e-3 tone): FP32 path and the tensor-core classes FP16, BF16, split BF16x3, "
-           "forward and inverse"),
+           "1e-3 tone), and N=8192 / 16384 on the same 2^27 elements: FP32 path and the "
+           "tensor-core classes FP16, BF16, split BF16x3 (tcgen05 kernel; at N=4096 also the "
+           "warp-level MMA kernel), forward and inverse"),
 }
 TC_BOUNDS = {"tc_fp16": 2e-3, "tc_bf16": 2e-3, "tc_bf16x3": 5e-6 * 12}
 
@@ -281,7 +282,8 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
     from paper_1505_08067_gb300 import gbfft, synth
 
     if kind == "tc":
-        items = [((4096,), 2 ** (TOTAL_LOG - 12))]
+        items = [((4096,), 2 ** (TOTAL_LOG - 12)), ((8192,), 2 ** (TOTAL_LOG - 13)),
+                 ((16384,), 2 ** (TOTAL_LOG - 14))]
     elif kind == "multipass":
         items = [((2 ** 20,), 64), ((2 ** 22,), 16), ((2 ** 24,), 4)]
     else:
@@ -307,18 +309,23 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         data = "iid U[-1,1] seed 3"
     y = torch.empty_like(x)
     plans, order = {}, []
-    precs = [0, 1, 2, 3] if kind == "tc" else [0]
+    # (precision, variant): FP32, the tcgen05 classes, and at N = 4096 the
+    # warp-level MMA classes beside them
+    precs = [(0, 0), (1, 0), (2, 0), (3, 0)] if kind == "tc" else [(0, 0)]
     t_plan = time.perf_counter()
     for shape, batch in items:
-        for prec in precs:
+        extra = [(1, 1), (2, 1), (3, 1)] if kind == "tc" and shape == (4096,) else []
+        for prec, var in precs + extra:
             for d in DIRS:
                 opts = {"epilogue": args.epilogue} if args.epilogue else {}
                 if args.variant and prec == 0:
                     opts["variant"] = args.variant
+                if prec:
+                    opts["variant"] = var
                 if args.tile and prec == 0:
                     opts["tile"] = args.tile
                 opts["autotune"] = args.autotune if prec == 0 else 0
-                key = (shape, d, prec)
+                key = (shape, d, prec, var)
                 plans[key] = gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, d, prec,
                                         **opts)
                 order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
@@ -353,7 +360,7 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
     for i, (key, e, lg) in enumerate(order):
         t = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
         passes = len(plans[key].describe()["passes"])
-        pname = PREC_NAMES[key[2]]
+        pname = PREC_NAMES[key[2]] + ("_warp_mma" if key[3] == 1 else "")
         gbs = 16.0 * passes * e / (t * 1e-3) / 1e9
         per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'} {pname}"] = {
             "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
@@ -374,12 +381,20 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
     if kind == "tc":
         acc = _tc_accuracy(gbfft, x, tone_bins)
         for name, rec in acc.items():
-            rec["bound"] = TC_BOUNDS[name]
-            rec["within_bound"] = rec["rel_l2_max"] <= TC_BOUNDS[name]
+            rec["bound"] = TC_BOUNDS[name.replace("_warp_mma", "")]
+            rec["within_bound"] = rec["rel_l2_max"] <= rec["bound"]
         out["accuracy_vs_fp32"] = acc
-        fp32 = {d: per[f"4096 {d} fp32"]["ms"] for d in ("fwd", "inv")}
-        out["vs_fp32"] = {p: {d: round(fp32[d] / per[f"4096 {d} {p}"]["ms"], 3)
-                              for d in ("fwd", "inv")} for p in ("tc_fp16", "tc_bf16", "tc_bf16x3")}
+        # time ratio FP32 / class per length and direction (> 1: the class is faster)
+        vs = {}
+        for shape, _b in items:
+            nm = "x".join(map(str, shape))
+            fp32 = {d: per[f"{nm} {d} fp32"]["ms"] for d in ("fwd", "inv")}
+            names = ["tc_fp16", "tc_bf16", "tc_bf16x3"]
+            if shape == (4096,):
+                names += ["tc_fp16_warp_mma", "tc_bf16_warp_mma", "tc_bf16x3_warp_mma"]
+            vs[nm] = {p: {d: round(fp32[d] / per[f"{nm} {d} {p}"]["ms"], 3) for d in ("fwd", "inv")}
+                      for p in names}
+        out["vs_fp32"] = vs
     for p in plans.values():
         p.close()
     del x, y
@@ -400,8 +415,9 @@ def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: floa
 
     xs = x[:count * n]
     outs = {}
-    for prec, name in enumerate(PREC_NAMES):
-        with gbfft.Plan(n, count, -1, prec) as p:
+    for prec, var in ((0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)):
+        name = PREC_NAMES[prec] + ("_warp_mma" if var == 1 else "")
+        with gbfft.Plan(n, count, -1, prec, **({"variant": var} if prec else {})) as p:
             outs[name] = p.execute(xs).cpu().numpy().reshape(count, n).astype(np.complex128)
             torch.cuda.synchronize()
     ref = outs.pop("fp32")

@@ -99,7 +99,7 @@ fft_status_t build_plan(fft_plan_t* out, const int64_t* n, int dims, int64_t bat
   if (spec.status != FFT_OK) return fail(spec.status, "%s", spec.error);
   if (conv) {
     for (int d = 0; d < dims; ++d) spec.filter[d] = filters[d];
-  } else if (opt && opt->autotune) {
+  } else if (opt && opt->autotune && precision == FFT_PREC_FP32) {
     // choose the options on this GPU, then plan with them
     fft_plan_options_t chosen{};
     char report[sizeof spec.tuning];
@@ -369,7 +369,8 @@ fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len) {
     const PassSpec& p = plan->spec.passes[i];
     const PassLaunch& l = plan->launches[i];
     const char* kind = p.kind != PASS_FFT ? "copy"
-                       : p.tc_prec        ? "tensor_core"
+                       : p.tc_prec        ? (p.variant == 1 ? "tensor_core_warp_mma"
+                                                                : "tensor_core_tcgen05")
                        : l.has_staged     ? "staged"  // for a 16-byte-aligned source
                        : l.specialised    ? "compile_time"
                                           : "generic";

@@ -24,7 +24,8 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       l.block = p.block;
       l.smem = p.smem;
       if (p.tc_prec) {
-        l.fn = resolve_tc(p.logL, p.tc_prec);
+        l.fn = resolve_tc_pass(p.logL, p.tc_prec, p.variant);
+        if (!l.fn) return cudaErrorInvalidDeviceFunction;
         l.specialised = true;
       } else {
         l.fn = resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
@@ -113,7 +114,7 @@ static cudaError_t enqueue_range(const PlanSpec& s, const PassLaunch* launches, 
         d.status = l.d.status;
         d.h = l.d.h;
         l.d = d;
-        l.fn = p.tc_prec ? resolve_tc(p.logL, p.tc_prec)
+        l.fn = p.tc_prec ? resolve_tc_pass(p.logL, p.tc_prec, p.variant)
                          : resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
         e = prepare_launch(l);
         if (e != cudaSuccess) return e;

@@ -65,8 +65,17 @@ bool encode_cols_maps(PassDesc& d, bool map_in, bool map_out, const void* in, vo
 const void* resolve_kernel(int R, int lmap, int smap, const PassDesc& d, bool generic_only,
                            bool* specialised);
 
-// Tensor-core class kernel for length 2^logL (4, 8, 12) and FFT_PREC_TC_*.
+// Tensor-core class kernel for length 2^logL (4, 8, 12) and FFT_PREC_TC_*:
+// the warp-level MMA form.
 const void* resolve_tc(int logL, int prec);
+// The tcgen05 form for length 2^logL (4 .. 14); *smem = the shared memory it
+// needs (the plan may ask for more to bound the CTAs per SM).
+const void* resolve_umma(int logL, int prec, size_t* smem);
+// The kernel of a tensor-core pass of the given variant (0 tcgen05, 1 warp MMA).
+inline const void* resolve_tc_pass(int logL, int prec, int variant) {
+  size_t sm = 0;
+  return variant == 1 ? resolve_tc(logL, prec) : resolve_umma(logL, prec, &sm);
+}
 
 // Per-kernel attributes a launch needs (opt-in shared memory); call once after
 // resolving, before the first launch_pass.

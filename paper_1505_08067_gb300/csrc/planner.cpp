@@ -55,15 +55,39 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
     p.grid = 0;
     return true;
   }
-  if (p.tc_prec) {
-    // fixed shape: 8 warps, two shared buffers of 4096 complex, a staging
-    // buffer for the next tile (chunks of 2^8 or 2^4 elements each followed
-    // by a 2-slot gap) and its mbarrier
+  if (p.tc_prec && p.variant == 1) {
+    // warp-level MMA kernel: 8 warps, two shared buffers of 4096 complex, a
+    // staging buffer for the next tile (chunks of 2^8 or 2^4 elements each
+    // followed by a 2-slot gap) and its mbarrier
     const int chunk_log = p.logL >= 12 ? 8 : 4;
     p.block = 256;
     p.pitch = 0;
     p.smem_elems = 2 * 4096 + 4096 + 2 * (4096 >> chunk_log);
     p.smem = (size_t)p.smem_elems * 8 + 16;
+    if (p.smem > (size_t)caps.smem_optin) {
+      err = "tensor-core tile does not fit in shared memory";
+      return false;
+    }
+    return true;
+  }
+  if (p.tc_prec) {
+    // tcgen05 kernel: 8 warps; the A operand of a tile (T/16 rows of 64
+    // bytes; twice for the split class), the DFT matrix and its low part
+    // (2 KB each), an mbarrier and the tensor-memory address, 1 KB of
+    // alignment slack.  Each CTA holds 32 tensor-memory columns per 128
+    // rows; the shared-memory request keeps the CTAs an SM can hold within
+    // its 512 columns.
+    const int logT = p.logL > 12 ? p.logL : 12;
+    const int rows = 1 << (logT - 4);
+    const size_t a = (size_t)rows * 64;
+    p.block = 256;
+    p.pitch = 0;
+    p.smem = (p.tc_prec == FFT_PREC_TC_BF16X3 ? 2 : 1) * a + 2 * 2048 + 16 + 1024;
+    const int cols = 32 * (rows / 128);
+    const size_t per_sm = (size_t)caps.smem_optin + 1024;  // the runtime keeps 1 KB per CTA
+    const size_t floor_smem = per_sm / (size_t)(512 / cols + 1) + 1 - 1024;
+    if (p.smem < floor_smem) p.smem = floor_smem;
+    p.smem_elems = (int)(p.smem / 8);
     if (p.smem > (size_t)caps.smem_optin) {
       err = "tensor-core tile does not fit in shared memory";
       return false;
@@ -200,11 +224,20 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   if (precision < FFT_PREC_FP32 || precision > FFT_PREC_TC_BF16X3)
     { fail(FFT_ERR_INVALID_ARG, "unknown precision"); return; }
   if (precision != FFT_PREC_FP32) {
-    // tensor-core class: batched 1D lengths that are powers of 16 up to 4096
-    const bool ok = dims == 1 && n && (n[0] == 16 || n[0] == 256 || n[0] == 4096);
+    // tensor-core classes: batched 1D lengths 2^4 .. 2^14 on the tcgen05
+    // kernel; the warp-level MMA kernel (variant 1) covers 16, 256 and 4096
+    const int64_t l = (dims == 1 && n) ? n[0] : 0;
+    if (o.variant != 0 && o.variant != 1) {
+      fail(FFT_ERR_INVALID_ARG, "tensor-core plans take variant 0 (tcgen05) or 1 (warp MMA)");
+      return;
+    }
+    const bool ok = o.variant == 1 ? (l == 16 || l == 256 || l == 4096)
+                                   : (l >= 16 && l <= 16384 && is_pow2(l));
     if (!ok) {
       fail(FFT_ERR_NOT_IMPLEMENTED,
-           "the tensor-core classes cover batched 1D transforms of length 16, 256 or 4096");
+           o.variant == 1
+               ? "the warp-level tensor-core kernel covers batched 1D lengths 16, 256, 4096"
+               : "the tensor-core classes cover batched 1D transforms of length 2^4 .. 2^14");
       return;
     }
   }
@@ -299,12 +332,15 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p.copy_count = batch;
       s.passes.push_back(p);
     } else if (precision != FFT_PREC_FP32) {
-      // radix-16 stages as DFT matmuls; tiles of 4096 elements (4096 / N transforms)
+      // radix-16 stages as DFT matmuls, after a radix-2/4/8 FP32 stage when N
+      // is not a power of 16; tiles of max(N, 4096) elements
       Sched sch;
+      if (logN % 4) sch.push_back(logN % 4);
       for (int i = 0; i < logN / 4; ++i) sch.push_back(4);
-      PassSpec p = contiguous_pass(logN, batch, 1, 16, 0, 4096 >> logN, caps);
+      const int logT = logN > 12 ? logN : 12;
+      PassSpec p = contiguous_pass(logN, batch, 1, 16, 0, 1 << (logT - logN), caps);
       p.rlogs = sch;
-      p.G = 4096 >> logN;
+      p.G = 1 << (logT - logN);
       p.tiles_inner = (batch + p.G - 1) / p.G;
       p.tiles = p.tiles_inner;
       p.in = Strides{0, (int64_t)p.G * N, N, 1};

@@ -13,7 +13,7 @@ CSRC = os.path.join(ROOT, "paper_1505_08067_gb300", "csrc")
 LIB = os.path.join(HERE, "_emu.so")
 SRCS = [os.path.join(HERE, "emu_harness.cpp"), os.path.join(CSRC, "planner.cpp")]
 DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "fft_split.h", "planner.h", "kernel_shapes.h",
-                                    "tc_stage.h")] + \
+                                    "tc_stage.h", "umma_stage.h", "tc_stage.h")] + \
     [os.path.join(ROOT, "include", "gbfft.h")]
 _lib = None
 

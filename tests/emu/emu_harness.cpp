@@ -26,6 +26,7 @@
 #include "kernel_shapes.h"
 #include "planner.h"
 #include "tc_stage.h"
+#include "umma_stage.h"
 
 using namespace gbfft;
 
@@ -545,6 +546,125 @@ bool run_tc(int logL, int prec, const PassDesc& d, const cf* in, cf* out) {
   return false;
 }
 
+// ------------------------------------------------ tcgen05 class replay --
+// The UMMA kernel's per-thread body (umma_stage.h) on the CPU.  Shared
+// memory is a byte array holding the A operand(s); every 32-bit store must
+// land inside it and no word may be written twice in one phase, and after each
+// phase every word of the operand must have been written.  The UMMA itself is
+// emulated from the operand layout the hardware reads (K-major, 64-byte
+// swizzle: element (m, k) at (m / 8) * 512 + (m % 8) * 64 + ((k / 8) ^
+// ((m % 8) / 2)) * 16 + (k % 8) * 2), written here independently of the
+// kernel's per-pair offsets; tensor memory is a row-major FP32 array whose
+// rows the replay hands to the same (warp, lane, row block) that reads them
+// on the GPU, each exactly once per stage.
+struct UmmaReplay {
+  std::vector<uint8_t> bytes;
+  std::vector<int64_t> word_phase;
+  int64_t phase = 0;
+};
+UmmaReplay g_umma;
+
+struct UmmaCheckMem : CheckMem {
+  static void sts32(uint32_t addr, uint32_t v) {
+    if (addr % 4 || addr + 4 > g_umma.bytes.size()) { err("A-operand store out of bounds", addr); return; }
+    if (g_umma.word_phase[addr / 4] == g_umma.phase) err("two writes to one A word in one phase", addr);
+    g_umma.word_phase[addr / 4] = g_umma.phase;
+    memcpy(&g_umma.bytes[addr], &v, 4);
+  }
+};
+
+GB_HD uint32_t umma_hw_offset(int m, int k) {
+  return (uint32_t)((m / 8) * 512 + (m % 8) * 64 + (((k / 8) ^ ((m % 8) / 2)) & 3) * 16 + (k % 8) * 2);
+}
+
+template <int LOGL, int PREC>
+void run_umma_t(const PassDesc& d, const cf* in, cf* out) {
+  using Body = UmmaBody<LOGL, PREC, UmmaCheckMem>;
+  using G = UmmaGeo<LOGL>;
+  constexpr int P = Body::P;
+  constexpr bool SPLIT = Body::SPLIT;
+  const uint32_t a_hi = 0, a_lo = G::A_BYTES;
+  g_umma.bytes.assign((SPLIT ? 2 : 1) * G::A_BYTES, 0);
+  g_umma.word_phase.assign(g_umma.bytes.size() / 4, -1);
+  // the DFT matrix as the kernel builds it, read back through the B layout
+  double Bh[32][32], Bl[32][32];
+  for (int n = 0; n < 32; ++n)
+    for (int k = 0; k < 32; ++k) {
+      const float v = umma_dft_entry(k, n);
+      const uint16_t h = P == TC_FP16 ? f32_to_f16_bits(v) : f32_to_bf16_bits(v);
+      Bh[k][n] = from16<P>(h);
+      Bl[k][n] = SPLIT ? bf16_bits_to_f32(f32_to_bf16_bits(v - bf16_bits_to_f32(h))) : 0.0;
+      if (umma_boff(n, k) != umma_hw_offset(n, k)) err("B offset differs from the UMMA layout", n * 32 + k);
+    }
+  auto a_val = [&](uint32_t base, int m, int k) {
+    uint16_t h;
+    memcpy(&h, &g_umma.bytes[base + umma_hw_offset(m, k)], 2);
+    return (double)from16<P>(h);
+  };
+  auto check_written = [&](const char* what) {
+    for (size_t w = 0; w < g_umma.word_phase.size(); ++w)
+      if (g_umma.word_phase[w] != g_umma.phase) { err(what, (int64_t)w); break; }
+  };
+  std::vector<float> D((size_t)G::ROWS * 32);
+  std::vector<int> row_reads(G::ROWS);
+  for (int64_t tile = 0; tile < d.tiles; ++tile) {
+    const int64_t first = tile * G::TPT;
+    const int valid = (int)std::min<int64_t>(G::TPT, d.count_inner - first);
+    const cf* gin = in + first * G::L;
+    cf* gout = out + first * G::L;
+    ++g_umma.phase;
+    for (int warp = 0; warp < 8; ++warp)
+      for (int lane = 0; lane < 32; ++lane)
+        for (int it = 0; it < G::ITEMS_PER_THREAD; ++it)
+          Body::load_item(d, gin, valid, a_hi, a_lo, warp, lane, it);
+    check_written("A-operand word not written by the loader");
+    auto stage = [&](auto t_) {
+      constexpr int t = decltype(t_)::value;
+      for (int m = 0; m < G::ROWS; ++m)
+        for (int n = 0; n < 32; ++n) {
+          double acc = 0;
+          for (int k = 0; k < 32; ++k) {
+            const double ah = a_val(a_hi, m, k);
+            acc += ah * Bh[k][n];
+            if (SPLIT) acc += ah * Bl[k][n] + a_val(a_lo, m, k) * Bh[k][n];
+          }
+          D[(size_t)m * 32 + n] = (float)acc;
+        }
+      ++g_umma.phase;
+      std::fill(row_reads.begin(), row_reads.end(), 0);
+      for (int warp = 0; warp < 8; ++warp)
+        for (int lane = 0; lane < 32; ++lane)
+          for (int rb = warp >> 2; rb < G::RB; rb += 2) {
+            const int m = rb * 128 + (warp & 3) * 32 + lane;
+            ++row_reads[m];
+            uint32_t r[32];
+            memcpy(r, &D[(size_t)m * 32], sizeof r);
+            Body::template epilogue_row<t>(d, gout, valid, m, r, a_hi, a_lo);
+          }
+      for (int m = 0; m < G::ROWS; ++m)
+        if (row_reads[m] != 1) { err("tensor-memory row not read exactly once", m); break; }
+      if (t < G::NTC - 1) check_written("A-operand word not written by the epilogue");
+    };
+    stage(std::integral_constant<int, 0>());
+    if constexpr (G::NTC > 1) stage(std::integral_constant<int, 1>());
+    if constexpr (G::NTC > 2) stage(std::integral_constant<int, 2>());
+  }
+}
+
+bool run_umma(int logL, int prec, const PassDesc& d, const cf* in, cf* out) {
+#define GB_UM(LG)                                                        \
+  if (logL == LG) {                                                      \
+    if (prec == 1) run_umma_t<LG, 1>(d, in, out);                        \
+    else if (prec == 2) run_umma_t<LG, 2>(d, in, out);                   \
+    else run_umma_t<LG, 3>(d, in, out);                                  \
+    return true;                                                         \
+  }
+  GB_UM(4) GB_UM(5) GB_UM(6) GB_UM(7) GB_UM(8) GB_UM(9) GB_UM(10) GB_UM(11) GB_UM(12)
+  GB_UM(13) GB_UM(14)
+#undef GB_UM
+  return false;
+}
+
 template <int LM, int SM>
 void run_maps(int R, const PassDesc& d, const cf* in, cf* out) {
   switch (R) {
@@ -624,7 +744,11 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
       else if (specialised && !s.generic_only && run_conv_special(p.R, p.lmap, d, src, dst)) ++g.special_passes;
       else if (p.lmap == MAP_ROWS) run_conv_maps<0>(p.R, d, src, dst);
       else run_conv_maps<1>(p.R, d, src, dst);
-    } else if (p.tc_prec) run_tc(p.logL, p.tc_prec, d, src, dst);
+    } else if (p.tc_prec) {
+      if (!(p.variant == 1 ? run_tc(p.logL, p.tc_prec, d, src, dst)
+                           : run_umma(p.logL, p.tc_prec, d, src, dst)))
+        err("no replay for this tensor-core pass", p.logL);
+    }
     else if (specialised && !s.generic_only && (p.variant == 0 || p.variant == 2) &&
              (p.lmap == MAP_COLS ? run_staged_cols(p.lmap, p.smap, d, src, dst)
               : p.smap == MAP_COLS ? run_staged_trans(p.lmap, p.smap, d, src, dst)

@@ -101,14 +101,33 @@ TC_TOL = {1: lambda n: 2e-3, 2: lambda n: 5e-3, 3: lambda n: 5e-6 * np.log2(n)}
 @pytest.mark.parametrize("n", [16, 256, 4096])
 @pytest.mark.parametrize("precision", [1, 2, 3])
 def test_tensor_core_class_replay(oracle, n, precision):
-    """Fragment layouts, addressing and ping-pong buffers of the tensor-core
-    kernel, with the warp MMA emulated from its documented fragment layout."""
+    """Fragment layouts, addressing and ping-pong buffers of the warp-level
+    tensor-core kernel (variant 1), with the warp MMA emulated from its
+    documented fragment layout."""
     batch = 4096 // n * 2 + 1                       # two full tiles and a ragged one
     x = synth.uniform(77, batch, n)
     for d in (-1, 1):
-        y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision)
+        y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision, variant=1)
         assert nerr == 0, msg
         assert np.max(oracle.rel_l2(y, oracle.fft(x, d))) <= TC_TOL[precision](n)
+
+
+@pytest.mark.parametrize("logn", range(4, 15))
+@pytest.mark.parametrize("precision", [1, 2, 3])
+def test_tcgen05_class_replay(oracle, logn, precision):
+    """The tcgen05 tensor-core kernel's loader (with the radix-2/4/8 first
+    stage where N is not a power of 16), A-operand layout, row permutations,
+    tensor-memory row ownership and epilogue, with the UMMA emulated from the
+    operand layout the hardware reads: every A word written once per phase,
+    every output once, and the transform within the class tolerance."""
+    n = 2 ** logn
+    tile = max(n, 4096)
+    batch = tile // n * 2 + 1 if n < 4096 else 3     # two full tiles and a ragged one
+    x = synth.uniform(78 + logn, batch, n)
+    for d in (-1, 1):
+        y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision)
+        assert nerr == 0, msg
+        assert np.max(oracle.rel_l2(y, oracle.fft(x, d))) <= TC_TOL[precision](n), logn
 
 
 # ---------------------------------------------------------------- convolution --

@@ -1,5 +1,6 @@
 """Tensor-core class on the GPU (radix-16 stages as DFT matmuls, FP32
-accumulation) against the FP64 oracle.
+accumulation) against the FP64 oracle: the tcgen05 kernel (variant 0, every
+length 2^4 .. 2^14) and the warp-level MMA kernel (variant 1, 16 / 256 / 4096).
 
 Tolerances (relative L2 per transform): FP16 2e-3; split BF16x3 5e-6 log2 N;
 plain BF16 5e-3.  Plain BF16 keeps 8 significant bits: rounding both the stage
@@ -20,29 +21,64 @@ TOL = {1: lambda n: 2e-3, 2: lambda n: 5e-3, 3: lambda n: 5e-6 * np.log2(n)}
 NAMES = {0: "fp32", 1: "tc_fp16", 2: "tc_bf16", 3: "tc_bf16x3"}
 
 
-def _run(gb, x_np, n, direction, precision):
+def _run(gb, x_np, n, direction, precision, variant=0):
     x = torch.from_numpy(x_np).cuda()
-    with gb.Plan(n, x_np.shape[0], direction, precision) as p:
+    with gb.Plan(n, x_np.shape[0], direction, precision, variant=variant) as p:
         y = p.execute(x)
-        torch.cuda.synchronize()
+        gb.fft_plan_sync_status(p.handle, torch.cuda.current_stream().cuda_stream)
     return y.cpu().numpy()
 
 
-@pytest.mark.parametrize("n", [16, 256, 4096])
+@pytest.mark.parametrize("logn", range(4, 15))
 @pytest.mark.parametrize("precision", [1, 2, 3])
 @pytest.mark.parametrize("direction", [-1, 1])
-def test_tc_class(gb, oracle, n, precision, direction):
-    batch = 4096 // n * 5 + 3
+def test_tcgen05_class(gb, oracle, logn, precision, direction):
+    """The tcgen05 kernel (radix-16 UMMA stages after a radix-2/4/8 FP32
+    first stage where N is not a power of 16) at every length it covers: five
+    full tiles and a ragged one."""
+    n = 2 ** logn
+    batch = max(4096 // n, 1) * 5 + 3
     x = synth.uniform(9500 + n + precision, batch, n)
     y = _run(gb, x, n, direction, precision)
     err = oracle.rel_l2(y, oracle.fft(x, direction))
     assert np.max(err) <= TOL[precision](n), float(np.max(err))
 
 
+@pytest.mark.parametrize("n", [16, 256, 4096])
+@pytest.mark.parametrize("precision", [1, 2, 3])
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_warp_mma_class(gb, oracle, n, precision, direction):
+    """The warp-level MMA form (variant 1) of the same class."""
+    batch = 4096 // n * 5 + 3
+    x = synth.uniform(9500 + n + precision, batch, n)
+    y = _run(gb, x, n, direction, precision, variant=1)
+    err = oracle.rel_l2(y, oracle.fft(x, direction))
+    assert np.max(err) <= TOL[precision](n), float(np.max(err))
+
+
+@pytest.mark.parametrize("logn", [12, 13, 14])
+@pytest.mark.parametrize("precision", [2, 3])
+def test_tcgen05_many_tiles_per_cta(gb, oracle, logn, precision):
+    """A batch of many tiles per CTA of the persistent grid (the tensor memory,
+    mbarrier phases and DFT matrix carried from tile to tile), sampled."""
+    n = 2 ** logn
+    batch = (1 << 24) // n + 1
+    x_np = synth.uniform(9700 + logn + precision, batch, n)
+    x = torch.from_numpy(x_np).cuda()
+    with gb.Plan(n, batch, -1, precision) as p:
+        y = p.execute(x)
+        gb.fft_plan_sync_status(p.handle, torch.cuda.current_stream().cuda_stream)
+    idx = np.unique(np.concatenate([[0, batch - 1], np.arange(1, batch, 997)]))
+    ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+    err = oracle.rel_l2(ys, oracle.fft_select(x_np, idx, -1))
+    assert np.max(err) <= TOL[precision](n), float(np.max(err))
+
+
 def test_tc_rejects_other_lengths(gb):
-    with pytest.raises(gb.GbfftError) as e:
-        gb.fft_plan_create(1024, 4, -1, 2)
-    assert e.value.status == gb.FFT_ERR_NOT_IMPLEMENTED
+    for n, variant in ((2 ** 15, 0), (8, 0), (1024, 1)):
+        with pytest.raises(gb.GbfftError) as e:
+            gb.fft_plan_create(n, 4, -1, 2, variant=variant)
+        assert e.value.status == gb.FFT_ERR_NOT_IMPLEMENTED, (n, variant)
 
 
 def test_tc_buried_tone_accuracy_report(gb, oracle, capsys):
@@ -55,15 +91,16 @@ def test_tc_buried_tone_accuracy_report(gb, oracle, capsys):
     idx = np.arange(0, batch, 1023)
     ref = oracle.fft_select(x, idx)
     report = {}
-    for prec in (0, 1, 2, 3):
-        with gb.Plan(n, batch, -1, prec) as p:
+    for prec, variant in ((0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)):
+        with gb.Plan(n, batch, -1, prec, variant=variant) as p:
             y = p.execute(xt)
             torch.cuda.synchronize()
         ys = y[torch.from_numpy(idx).cuda()].cpu().numpy()
         err = oracle.rel_l2(ys, ref)
         tone = np.abs(ys[np.arange(idx.size), bins[idx]] - ref[np.arange(idx.size), bins[idx]])
-        report[NAMES[prec]] = {"rel_l2_max": float(err.max()), "rel_l2_mean": float(err.mean()),
-                               "tone_bin_err_rel": float(tone.max() / (n * 1e-3))}
+        name = NAMES[prec] + ("_warp_mma" if variant == 1 else "")
+        report[name] = {"rel_l2_max": float(err.max()), "rel_l2_mean": float(err.mean()),
+                        "tone_bin_err_rel": float(tone.max() / (n * 1e-3))}
         tol = 1e-6 * np.log2(n) if prec == 0 else TOL[prec](n)
         assert err.max() <= tol
     with capsys.disabled():
@@ -72,7 +109,8 @@ def test_tc_buried_tone_accuracy_report(gb, oracle, capsys):
 
 @pytest.mark.parametrize("n", [16, 256, 4096])
 @pytest.mark.parametrize("precision", [1, 3])
-def test_tc_staged_and_unaligned_input(gb, oracle, n, precision):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tc_staged_and_unaligned_input(gb, oracle, n, precision, variant):
     """The kernel copies each next tile into shared memory when the input is
     16-byte aligned and reads global memory directly when it is only 8-byte
     aligned; both give the same accuracy (a ragged last tile, many tiles per
@@ -85,7 +123,7 @@ def test_tc_staged_and_unaligned_input(gb, oracle, n, precision):
         xin = buf[shift:shift + batch * n]
         xin.copy_(torch.from_numpy(x_np.reshape(-1)))
         out = torch.empty(batch * n, dtype=torch.complex64, device="cuda")
-        with gb.Plan(n, batch, -1, precision) as p:
+        with gb.Plan(n, batch, -1, precision, variant=variant) as p:
             st = torch.cuda.current_stream().cuda_stream
             gb.fft_execute(p.handle, xin.data_ptr(), out.data_ptr(), st)
             gb.fft_plan_sync_status(p.handle, st)
