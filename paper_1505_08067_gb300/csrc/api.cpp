@@ -376,8 +376,8 @@ fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len) {
                                           : "generic";
     char b[160];
     snprintf(b, sizeof b, "%s{\"kernel\":\"%s\",\"conv\":%d,\"persistent_grid\":%d,"
-             "\"l2_prefetch\":%d}", i ? "," : "", kind, p.conv, l.persistent_grid,
-             (int)l.d.l2_prefetch);
+             "\"ctas_per_sm\":%d,\"l2_prefetch\":%d}", i ? "," : "", kind, p.conv,
+             l.persistent_grid, l.ctas_per_sm, (int)l.d.l2_prefetch);
     k += b;
   }
   k += "]";

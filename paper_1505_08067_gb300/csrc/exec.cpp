@@ -35,9 +35,27 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       if (p.tc_prec) {
         // persistent grid: the DFT-matrix fragments a block builds once serve
         // many tiles
+        if (p.variant != 1) {
+          // the tcgen05 kernel keeps its operands in shared memory: prefer the
+          // largest shared-memory carveout so that the blocks the registers
+          // allow are resident together
+          e = cudaFuncSetAttribute(l.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+          if (e != cudaSuccess) return e;
+        }
         int per_sm = 0;
         e = occupancy(l, &per_sm);
         if (e != cudaSuccess) return e;
+        if (p.variant != 1) {
+          // the occupancy query reports one block per SM for this kernel
+          // where its registers and shared memory allow more (measured):
+          // count from the kernel's attributes, within the SM's tensor memory
+          int own = 0;
+          e = resident_blocks(l.fn, l.block, l.smem, umma_tmem_cols(p.logL), &own);
+          if (e != cudaSuccess) return e;
+          per_sm = std::max(per_sm, own);
+        }
+        l.ctas_per_sm = per_sm;
         const int64_t g = (int64_t)std::max(per_sm, 1) * caps.sm_count;
         l.grid = (int)std::min<int64_t>(g, l.grid);
         l.persistent_grid = l.grid;

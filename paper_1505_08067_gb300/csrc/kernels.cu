@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -193,6 +194,30 @@ cudaError_t occupancy(const PassLaunch& p, int* ctas_per_sm) {
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, (const void*)k, p.block,
                                                        p.smem);
+}
+
+cudaError_t resident_blocks(const void* fn, int block, size_t smem, int tmem_cols, int* blocks) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  int regs_sm = 0, smem_sm = 0, threads_sm = 0, blocks_sm = 0, reserved = 0;
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = (block + 31) / 32;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in 256s
+  int n = blocks_sm;
+  if (regs_warp > 0) n = std::min(n, regs_sm / (regs_warp * warps));
+  n = std::min(n, threads_sm / block);
+  const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
+  if (per_block > 0) n = std::min(n, (int)((size_t)smem_sm / per_block));
+  if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
+  *blocks = std::max(n, 0);
+  return cudaSuccess;
 }
 
 cudaError_t launch_stage_bench(int R, const PassDesc& d, int Ns, int reps, int grid, int block,

@@ -33,6 +33,7 @@ struct PassLaunch {
   bool specialised = false;
   bool has_staged = false;   // a staged kernel exists for this shape (see below)
   int persistent_grid = 0;   // nonzero: grid capped at resident blocks (L2-prefetch variant)
+  int ctas_per_sm = 0;       // persistent kernels: resident blocks per SM the grid assumes
   struct StagedLaunchData {
     const void* fn = nullptr;
     int grid = 0, block = 0;
@@ -71,6 +72,12 @@ const void* resolve_tc(int logL, int prec);
 // The tcgen05 form for length 2^logL (4 .. 14); *smem = the shared memory it
 // needs (the plan may ask for more to bound the CTAs per SM).
 const void* resolve_umma(int logL, int prec, size_t* smem);
+// Tensor-memory columns one tcgen05 block of length 2^logL allocates.
+int umma_tmem_cols(int logL);
+// Blocks of `fn` one SM holds at once by its registers, shared memory and
+// threads (from the kernel's attributes and the device's limits), and by
+// tensor memory when tmem_cols > 0 (512 columns per SM).
+cudaError_t resident_blocks(const void* fn, int block, size_t smem, int tmem_cols, int* blocks);
 // The kernel of a tensor-core pass of the given variant (0 tcgen05, 1 warp MMA).
 inline const void* resolve_tc_pass(int logL, int prec, int variant) {
   size_t sm = 0;

@@ -66,12 +66,31 @@ __device__ __forceinline__ void umma16(uint32_t d_tmem, uint64_t a, uint64_t b, 
       : "memory");
 }
 
+// Brings [p, p + bytes) into L2 ahead of its loads (a bulk prefetch: no
+// shared memory, no completion to wait for).  Both 16-byte aligned.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // The mbarrier completes one phase when every UMMA this thread issued is done.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's tensor-memory lane.
@@ -93,9 +112,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // Device memory policy of the per-thread body: the pass kernels' global
 // accesses plus 32-bit shared stores at byte addresses.
+// The stores carry no memory clobber, so the compiler may hoist the next
+// global or twiddle loads above them (with the clobber every load waited for
+// the store before it); the fence and barrier before each UMMA issue order
+// them for the tensor cores.
 struct UmmaDevMem : DevMem {
   __device__ __forceinline__ static void sts32(uint32_t saddr, uint32_t v) {
-    asm volatile("st.shared.b32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(saddr), "r"(v));
   }
 };
 
@@ -137,15 +160,19 @@ struct Umma {
     const int q = warp & 3;
 #pragma unroll 1
     for (int rb = warp >> 2; rb < G::RB; rb += 2) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + 32u * rb, r);
-      Body::template epilogue_row<t>(d, gout, valid, rb * 128 + q * 32 + lane, r, a_hi, a_lo);
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + 32u * rb;
+      const int m = rb * 128 + q * 32 + lane;
+      uint32_t r[16];
+      tmem_ld16(ta, r);  // outputs 0..7
+      Body::template epilogue_row<t, 0, 8>(d, gout, valid, m, r, a_hi, a_lo);
+      tmem_ld16(ta + 16u, r);  // outputs 8..15
+      Body::template epilogue_row<t, 8, 8>(d, gout, valid, m, r, a_hi, a_lo);
     }
   }
 };
 
 template <int LOGL, int PREC>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   using U = Umma<LOGL, PREC>;
   using G = typename U::G;
@@ -187,7 +214,18 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
     const int valid = rem < G::TPT ? (int)rem : G::TPT;
     const cf* gin = in + first * G::L;
     cf* gout = out + first * G::L;
-#pragma unroll 4
+    // the tile this CTA takes next, into L2 while this one is computed
+    // (whole 16-byte units inside the tile only; none for a ragged tile)
+    if (tid == 0 && tile + gridDim.x < d.tiles) {
+      const int64_t nfirst = (tile + gridDim.x) * G::TPT;
+      if (nfirst + G::TPT <= d.count_inner) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(in + nfirst * G::L);
+        const uintptr_t a16 = (a + 15) & ~uintptr_t(15);
+        const uintptr_t e16 = (a + (uintptr_t)G::T * 8) & ~uintptr_t(15);
+        if (e16 > a16) prefetch_l2(reinterpret_cast<const void*>(a16), (uint32_t)(e16 - a16));
+      }
+    }
+#pragma unroll 8
     for (int it = 0; it < G::ITEMS_PER_THREAD; ++it)
       U::Body::load_item(d, gin, valid, a_hi, a_lo, warp, lane, it);
     fence_smem_async();

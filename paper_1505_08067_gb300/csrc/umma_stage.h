@@ -290,9 +290,11 @@ GB_UNROLL
   // else twiddled, rounded and stored as the next stage's A operand.  The
   // next row, input and twiddle index are the thread's part once, XORed with
   // a per-output constant.
-  template <int t>
+  // Outputs O0 .. O0 + NO - 1 (r holds their 2 NO FP32 values), so that a
+  // thread can read its tensor-memory row in parts.
+  template <int t, int O0 = 0, int NO = 16>
   GB_HD static void epilogue_row(const PassDesc& d, cf* gout, int valid, int m,
-                                 const uint32_t (&r)[32], uint32_t a_hi, uint32_t a_lo) {
+                                 const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
     const int u = umma_u_of_row<LOGL>(t, m);
     if (t == G::NTC - 1) {
       const int tr = u >> G::BPSB, jb = u & ((1 << G::BPSB) - 1);
@@ -300,8 +302,9 @@ GB_UNROLL
       cf* o_base = gout + (int64_t)tr * G::L;
       const bool swap = d.conj_out != 0;
 GB_UNROLL
-      for (int o = 0; o < 16; ++o) {
-        cf v = mk(u32_as_f32(r[2 * o]), u32_as_f32(r[2 * o + 1]));
+      for (int j = 0; j < NO; ++j) {
+        const int o = O0 + j;
+        cf v = mk(u32_as_f32(r[2 * j]), u32_as_f32(r[2 * j + 1]));
         if (P == TC_FP16) {  // undo the 1/16 of every stage: exact powers of two
           const float sc = (float)(1 << (4 * G::NTC));
           v = mk(v.x * sc, v.y * sc);
@@ -314,11 +317,12 @@ GB_UNROLL
       const uint32_t offt = umma_aoff(umma_row_of_u<LOGL>(t + 1, u2t), i2t);
       const cf* tw = d.tw + d.tw_off[ST0 + t + 1];
 GB_UNROLL
-      for (int o = 0; o < 16; ++o) {
+      for (int j = 0; j < NO; ++j) {
+        const int o = O0 + j;
         int u2o, i2o, two;
         umma_next<LOGL>(t, 0, o, u2o, i2o, two);
         const uint32_t off = offt ^ umma_aoff(umma_row_of_u<LOGL>(t + 1, u2o), i2o);
-        cf v = mk(u32_as_f32(r[2 * o]), u32_as_f32(r[2 * o + 1]));
+        cf v = mk(u32_as_f32(r[2 * j]), u32_as_f32(r[2 * j + 1]));
         v = cmul(v, Mem::ldtw(tw + (twt ^ two)));
         put_a(a_hi, a_lo, off, v);
       }
