@@ -35,14 +35,6 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       if (p.tc_prec) {
         // persistent grid: the DFT-matrix fragments a block builds once serve
         // many tiles
-        if (p.variant != 1) {
-          // the tcgen05 kernel keeps its operands in shared memory: prefer the
-          // largest shared-memory carveout so that the blocks the registers
-          // allow are resident together
-          e = cudaFuncSetAttribute(l.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                   (int)cudaSharedmemCarveoutMaxShared);
-          if (e != cudaSuccess) return e;
-        }
         int per_sm = 0;
         e = occupancy(l, &per_sm);
         if (e != cudaSuccess) return e;

@@ -162,17 +162,18 @@ struct Umma {
     for (int rb = warp >> 2; rb < G::RB; rb += 2) {
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + 32u * rb;
       const int m = rb * 128 + q * 32 + lane;
+      const typename Body::RowPart rp = Body::template row_part<t>(m);
       uint32_t r[16];
       tmem_ld16(ta, r);  // outputs 0..7
-      Body::template epilogue_row<t, 0, 8>(d, gout, valid, m, r, a_hi, a_lo);
+      Body::template epilogue_part<t, 0, 8>(d, gout, valid, rp, r, a_hi, a_lo);
       tmem_ld16(ta + 16u, r);  // outputs 8..15
-      Body::template epilogue_row<t, 8, 8>(d, gout, valid, m, r, a_hi, a_lo);
+      Body::template epilogue_part<t, 8, 8>(d, gout, valid, rp, r, a_hi, a_lo);
     }
   }
 };
 
 template <int LOGL, int PREC>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   using U = Umma<LOGL, PREC>;
   using G = typename U::G;
@@ -225,9 +226,7 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
         if (e16 > a16) prefetch_l2(reinterpret_cast<const void*>(a16), (uint32_t)(e16 - a16));
       }
     }
-#pragma unroll 8
-    for (int it = 0; it < G::ITEMS_PER_THREAD; ++it)
-      U::Body::load_item(d, gin, valid, a_hi, a_lo, warp, lane, it);
+    U::Body::load_tile(d, gin, valid, a_hi, a_lo, warp, lane);
     fence_smem_async();
     tc05_fence_before();
     __syncthreads();

@@ -248,58 +248,121 @@ struct UmmaBody {
     if (SPLIT) Mem::sts32(a_lo + off, pack_rn<P>(v.x - lo16_to_f32<P>(h), v.y - hi16_to_f32<P>(h)));
   }
 
-  // Loader work item `it` of thread (warp, lane): a tile element (r0 = 1), or
-  // a radix-r0 first-stage butterfly computed in FP32, into the stage-0 A
-  // operand.  `valid` transforms of the tile are read; the rest are zeros.
-  GB_HD static void load_item(const PassDesc& d, const cf* gin, int valid, uint32_t a_hi,
-                              uint32_t a_lo, int warp, int lane, int it) {
+  // The loader: every work item of thread (warp, lane) -- tile elements
+  // (r0 = 1), or radix-r0 first-stage butterflies computed in FP32 -- into
+  // the stage-0 A operand.  `valid` transforms of the tile are read; the rest
+  // are zeros.  Item e = e_t | e_b | e_j: e_t from (lane, warp), e_b from the
+  // block of CH items, e_j from the item within the block.  Every index below
+  // (element, A row and offset, twiddle) is linear in the bits of e, so it is
+  // the thread's part (once), the block's part (once per CH items) and a
+  // compile-time constant, XORed.
+  static constexpr int CH = G::ITEMS_PER_THREAD < 8 ? G::ITEMS_PER_THREAD : 8;
+  GB_HD static int elem_of(int e) {  // first element of first-stage butterfly e
+    return G::R0B ? ((e >> (LOGL - G::R0B)) << LOGL) | (e & ((1 << (LOGL - G::R0B)) - 1)) : e;
+  }
+  GB_HD static int tr_of(int e) { return e >> (LOGL - G::R0B); }
+  GB_HD static uint32_t off_of(int e) {  // r0 = 1: A-operand offset of tile element e
+    int u, i;
+    umma_load_target<LOGL>(e, u, i);
+    return umma_aoff(umma_row_of_u<LOGL>(0, u), i);
+  }
+  GB_HD static void first_of(int e, int o, uint32_t& off, int& i, int& tw) {  // r0 > 1
+    int u;
+    umma_first_target<LOGL>(e, o, u, i, tw);
+    off = umma_aoff(umma_row_of_u<LOGL>(0, u), i);
+  }
+
+  GB_HD static void load_tile(const PassDesc& d, const cf* gin, int valid, uint32_t a_hi,
+                              uint32_t a_lo, int warp, int lane) {
     const bool swap = d.conj_in != 0;
-    const int e = umma_load_item<LOGL>(lane, it * 8 + warp);
-    if (G::R0B == 0) {
-      const int tr = e >> LOGL;
-      cf v = tr < valid ? Mem::ldg(gin, e) : mk(0.f, 0.f);
-      if (swap) v = mk(v.y, v.x);
-      int u, i;
-      umma_load_target<LOGL>(e, u, i);
-      put_a(a_hi, a_lo, umma_aoff(umma_row_of_u<LOGL>(0, u), i), v);
-    } else {
-      const int tr = e >> (LOGL - G::R0B), jb0 = e & ((1 << (LOGL - G::R0B)) - 1);
-      cf y[G::R0];
+    const int et = umma_load_item<LOGL>(lane, warp);
+#pragma unroll 1
+    for (int kb = 0; kb < G::ITEMS_PER_THREAD; kb += CH) {
+      const int eb = et | umma_load_item<LOGL>(0, kb * 8);
+      if (G::R0B == 0) {
+        const uint32_t offb = off_of(eb);
+        cf v[CH];
 GB_UNROLL
-      for (int q = 0; q < G::R0; ++q) {
-        cf v = tr < valid ? Mem::ldg(gin, (int64_t)tr * G::L + jb0 + q * (G::L / G::R0))
-                          : mk(0.f, 0.f);
-        y[q] = swap ? mk(v.y, v.x) : v;
-      }
-      if (G::R0 == 2) dft_small<2, 1>(y);
-      else if (G::R0 == 4) dft_small<4, 1>(y);
-      else dft_pq<2, 4>(y);
-      const cf* tw = d.tw + d.tw_off[1];
+        for (int j = 0; j < CH; ++j) {
+          const int e = eb | umma_load_item<LOGL>(0, j * 8);
+          v[j] = tr_of(e) < valid ? Mem::ldg(gin, e) : mk(0.f, 0.f);
+        }
 GB_UNROLL
-      for (int o = 0; o < G::R0; ++o) {
-        int u, i, twi;
-        umma_first_target<LOGL>(e, o, u, i, twi);
-        const cf v = i > 0 ? cmul(y[o], Mem::ldtw(tw + twi)) : y[o];
-        put_a(a_hi, a_lo, umma_aoff(umma_row_of_u<LOGL>(0, u), i), v);
+        for (int j = 0; j < CH; ++j) {
+          const cf x = swap ? mk(v[j].y, v[j].x) : v[j];
+          put_a(a_hi, a_lo, offb ^ off_of(umma_load_item<LOGL>(0, j * 8)), x);
+        }
+      } else {
+        uint32_t offb;
+        int ib, twb;
+        first_of(eb, 0, offb, ib, twb);
+        const int xb = elem_of(eb);
+        const cf* tw = d.tw + d.tw_off[1];
+GB_UNROLL
+        for (int j = 0; j < CH; ++j) {
+          const int ej = umma_load_item<LOGL>(0, j * 8);
+          const bool ok = tr_of(eb | ej) < valid;
+          cf y[G::R0];
+GB_UNROLL
+          for (int q = 0; q < G::R0; ++q) {
+            const cf v = ok ? Mem::ldg(gin, (xb | elem_of(ej)) + q * (G::L / G::R0)) : mk(0.f, 0.f);
+            y[q] = swap ? mk(v.y, v.x) : v;
+          }
+          if (G::R0 == 2) dft_small<2, 1>(y);
+          else if (G::R0 == 4) dft_small<4, 1>(y);
+          else dft_pq<2, 4>(y);
+          uint32_t offj;
+          int ij, twj;
+          first_of(ej, 0, offj, ij, twj);
+GB_UNROLL
+          for (int o = 0; o < G::R0; ++o) {
+            uint32_t offo;
+            int io, two;
+            first_of(0, o, offo, io, two);
+            const int i = ib ^ ij ^ io;
+            const cf v = i > 0 ? cmul(y[o], Mem::ldtw(tw + (twb ^ twj ^ two))) : y[o];
+            put_a(a_hi, a_lo, offb ^ offj ^ offo, v);
+          }
+        }
       }
     }
   }
 
-  // The 16 outputs r[2o], r[2o + 1] (FP32 bits) of the butterfly in A row m
-  // of tensor-core stage t: stored to global memory after the last stage,
-  // else twiddled, rounded and stored as the next stage's A operand.  The
-  // next row, input and twiddle index are the thread's part once, XORed with
-  // a per-output constant.
-  // Outputs O0 .. O0 + NO - 1 (r holds their 2 NO FP32 values), so that a
-  // thread can read its tensor-memory row in parts.
-  template <int t, int O0 = 0, int NO = 16>
-  GB_HD static void epilogue_row(const PassDesc& d, cf* gout, int valid, int m,
-                                 const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
+  // The thread's part of the addressing of the butterfly in A row m of
+  // tensor-core stage t: after the last stage its transform (tr) and the
+  // position bits of its outputs that do not depend on the output index;
+  // before, the next stage's A offset and twiddle index of its output 0.
+  struct RowPart {
+    int tr, pos;
+    uint32_t off;
+    int tw;
+  };
+  template <int t>
+  GB_HD static RowPart row_part(int m) {
+    RowPart rp{};
     const int u = umma_u_of_row<LOGL>(t, m);
     if (t == G::NTC - 1) {
-      const int tr = u >> G::BPSB, jb = u & ((1 << G::BPSB) - 1);
-      if (tr >= valid) return;
-      cf* o_base = gout + (int64_t)tr * G::L;
+      rp.tr = u >> G::BPSB;
+      rp.pos = umma_out_pos(G::ns_log(t), u & ((1 << G::BPSB) - 1), 0);
+    } else {
+      int u2, i2;
+      umma_next<LOGL>(t, u, 0, u2, i2, rp.tw);
+      rp.off = umma_aoff(umma_row_of_u<LOGL>(t + 1, u2), i2);
+    }
+    return rp;
+  }
+
+  // Outputs O0 .. O0 + NO - 1 of that butterfly (r holds their 2 NO FP32
+  // values, so a thread can read its tensor-memory row in parts): stored to
+  // global memory after the last stage, else twiddled, rounded and stored as
+  // the next stage's A operand.  Each output's own part of the addressing is
+  // a compile-time constant XORed into the row's part.
+  template <int t, int O0 = 0, int NO = 16>
+  GB_HD static void epilogue_part(const PassDesc& d, cf* gout, int valid, const RowPart& rp,
+                                  const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
+    if (t == G::NTC - 1) {
+      if (rp.tr >= valid) return;
+      cf* o_base = gout + (int64_t)rp.tr * G::L;
       const bool swap = d.conj_out != 0;
 GB_UNROLL
       for (int j = 0; j < NO; ++j) {
@@ -309,24 +372,27 @@ GB_UNROLL
           const float sc = (float)(1 << (4 * G::NTC));
           v = mk(v.x * sc, v.y * sc);
         }
-        Mem::stg(o_base, umma_out_pos(G::ns_log(t), jb, o), swap ? mk(v.y, v.x) : v);
+        Mem::stg(o_base, rp.pos | (o << G::ns_log(t)), swap ? mk(v.y, v.x) : v);
       }
     } else {
-      int u2t, i2t, twt;
-      umma_next<LOGL>(t, u, 0, u2t, i2t, twt);
-      const uint32_t offt = umma_aoff(umma_row_of_u<LOGL>(t + 1, u2t), i2t);
       const cf* tw = d.tw + d.tw_off[ST0 + t + 1];
 GB_UNROLL
       for (int j = 0; j < NO; ++j) {
         const int o = O0 + j;
         int u2o, i2o, two;
         umma_next<LOGL>(t, 0, o, u2o, i2o, two);
-        const uint32_t off = offt ^ umma_aoff(umma_row_of_u<LOGL>(t + 1, u2o), i2o);
+        const uint32_t off = rp.off ^ umma_aoff(umma_row_of_u<LOGL>(t + 1, u2o), i2o);
         cf v = mk(u32_as_f32(r[2 * j]), u32_as_f32(r[2 * j + 1]));
-        v = cmul(v, Mem::ldtw(tw + (twt ^ two)));
+        v = cmul(v, Mem::ldtw(tw + (rp.tw ^ two)));
         put_a(a_hi, a_lo, off, v);
       }
     }
+  }
+
+  template <int t, int O0 = 0, int NO = 16>
+  GB_HD static void epilogue_row(const PassDesc& d, cf* gout, int valid, int m,
+                                 const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
+    epilogue_part<t, O0, NO>(d, gout, valid, row_part<t>(m), r, a_hi, a_lo);
   }
 };
 

@@ -614,9 +614,7 @@ void run_umma_t(const PassDesc& d, const cf* in, cf* out) {
     cf* gout = out + first * G::L;
     ++g_umma.phase;
     for (int warp = 0; warp < 8; ++warp)
-      for (int lane = 0; lane < 32; ++lane)
-        for (int it = 0; it < G::ITEMS_PER_THREAD; ++it)
-          Body::load_item(d, gin, valid, a_hi, a_lo, warp, lane, it);
+      for (int lane = 0; lane < 32; ++lane) Body::load_tile(d, gin, valid, a_hi, a_lo, warp, lane);
     check_written("A-operand word not written by the loader");
     auto stage = [&](auto t_) {
       constexpr int t = decltype(t_)::value;

@@ -58,9 +58,21 @@ def test_dry_run_rejects_options():
         g.fft_plan_dry_run(1024, 1, schedule=0x333)     # 8*8*8 != 1024
     with pytest.raises(g.GbfftError):
         g.fft_plan_dry_run(1024, 1, precision=9)
+    # tensor-core classes: 2^4 .. 2^14 on the tcgen05 kernel, 16 / 256 / 4096
+    # on the warp-level MMA kernel (variant 1)
+    for n, variant in ((2 ** 15, 0), (8, 0), (1024, 1)):
+        with pytest.raises(g.GbfftError) as e:
+            g.fft_plan_dry_run(n, 1, precision=g.FFT_PREC_TC_BF16, variant=variant)
+        assert e.value.status == g.FFT_ERR_NOT_IMPLEMENTED
     with pytest.raises(g.GbfftError) as e:
-        g.fft_plan_dry_run(1024, 1, precision=g.FFT_PREC_TC_BF16)
-    assert e.value.status == g.FFT_ERR_NOT_IMPLEMENTED
+        g.fft_plan_dry_run(1024, 1, precision=g.FFT_PREC_TC_BF16, variant=2)
+    assert e.value.status == g.FFT_ERR_INVALID_ARG
+    for logn in range(4, 15):
+        d = g.fft_plan_dry_run(2 ** logn, 5, precision=g.FFT_PREC_TC_BF16X3)
+        (p,) = d["passes"]
+        assert p["tc_prec"] == 3 and 1 << sum(r.bit_length() - 1 for r in p["radices"]) == 2 ** logn
+        first = [2 ** (logn % 4)] if logn % 4 else []   # FP32 first stage, then radix 16
+        assert p["radices"] == first + [16] * (logn // 4) and p["smem"] <= 232448
 
 
 @pytest.mark.parametrize("logn", range(0, 25))
