@@ -434,7 +434,7 @@ def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: floa
 def section_serve(args, jobs: int, load: float) -> dict:
     """Serving (cfg5): a Poisson stream of FFT jobs, sizes log-uniform over
     N = 2^8..2^22, batch 1..256, forward / inverse 50/50, 80% FP32 and 20%
-    tensor-core class (those take N = 256 or 4096, the lengths the class
+    tensor-core class (those take N = 2^8..2^14, the lengths the class
     covers), admitted under a 64 GB budget.  Offered load: algorithmic bytes
     per second = `load` x measured HBM bandwidth.  Inputs are slices of one
     seeded device buffer; outputs rotate through a ring that is reused only
@@ -454,7 +454,8 @@ def section_serve(args, jobs: int, load: float) -> dict:
     batch = rng.integers(1, 257, njobs)
     dirs = np.where(rng.random(njobs) < 0.5, -1, 1)
     prec = np.where(rng.random(njobs) < 0.2, rng.integers(1, 4, njobs), 0)
-    logn = np.where(prec > 0, np.where(rng.random(njobs) < 0.5, 8, 12), logn)
+    # tensor-core jobs: log-uniform over the lengths the class covers (2^8..2^14)
+    logn = np.where(prec > 0, rng.integers(8, 15, njobs), logn)
     elems = (2 ** logn) * batch
     passes = np.where(logn > 14, 2, 1)
     alg_bytes = 16.0 * passes * elems
@@ -554,7 +555,7 @@ def section_serve(args, jobs: int, load: float) -> dict:
     del xin, yout
     return {
         "workload": "serving: Poisson stream of FFT jobs, N = 2^8..2^22 (tensor-core jobs "
-                    "N = 2^8 or 2^12), batch 1..256, 50/50 forward/inverse, 80% FP32 / 20% "
+                    "N = 2^8..2^14), batch 1..256, 50/50 forward/inverse, 80% FP32 / 20% "
                     "tensor-core class, 64 GB budget",
         "jobs": njobs, "offered_load_frac_of_hbm": load, "offered_jobs_per_s": rate,
         "streams": args.streams, "large_group_log2": args.large_group_log2,

@@ -464,7 +464,11 @@ def test_kernel_selection_conv_and_tc(gb):
     assert [k["kernel"] for k in ks] == ["staged", "compile_time"] and all(k["conv"] for k in ks)
     with gb.Plan(4096, 64, -1, gb.FFT_PREC_TC_BF16) as p:
         ks = p.describe()["kernels"]
-    assert ks[0]["kernel"] == "tensor_core" and ks[0]["persistent_grid"] > 0
+    assert ks[0]["kernel"] == "tensor_core_tcgen05" and ks[0]["persistent_grid"] > 0
+    assert ks[0]["ctas_per_sm"] >= 1
+    with gb.Plan(4096, 64, -1, gb.FFT_PREC_TC_BF16, variant=1) as p:
+        ks = p.describe()["kernels"]
+    assert ks[0]["kernel"] == "tensor_core_warp_mma" and ks[0]["persistent_grid"] > 0
 
 
 def test_execute_argument_errors(gb):

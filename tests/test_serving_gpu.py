@@ -23,7 +23,7 @@ def _mix(seed, count):
         shape = shapes[rng.integers(len(shapes))]
         n = int(np.prod(shape))
         prec = 0
-        if shape == (4096,) and rng.random() < 0.5:
+        if len(shape) == 1 and n <= 2 ** 14 and rng.random() < 0.4:  # tensor-core class
             prec = int(rng.integers(1, 4))
         batch = int(rng.integers(1, max(2, min(64, 2 ** 22 // n))))
         d = -1 if rng.random() < 0.5 else 1
