@@ -34,7 +34,17 @@
   GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 0)              \
   GB_SHAPE(10, 0x244, 3, 16, 16, 1, 1, false, 4)             \
   GB_SHAPE(11, 0x344, 3, 16, 8, 1, 1, false, 4)              \
-  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 4)
+  GB_SHAPE(12, 0x444, 3, 16, 4, 1, 1, false, 4)              \
+  GB_SHAPES_FOURSTEP_MID(GB_SHAPE)
+
+/* four-step N = 2^15..2^19 (passes of 128..512 points, 16 transforms per */
+/* tile): column passes with the factored twiddle, transposing row passes */
+#define GB_SHAPES_FOURSTEP_MID(GB_SHAPE)                      \
+  GB_SHAPE(7, 0x34, 2, 16, 16, 1, 1, false, 4)                \
+  GB_SHAPE(8, 0x44, 2, 16, 16, 1, 1, false, 4)                \
+  GB_SHAPE(9, 0x144, 3, 16, 16, 1, 1, false, 4)               \
+  GB_SHAPE(8, 0x44, 2, 16, 16, 0, 1, false, 0)                \
+  GB_SHAPE(9, 0x144, 3, 16, 16, 0, 1, false, 0)
 
 /* fast convolution: range lines of 4096 / 8192 / 16384, azimuth columns */
 /* of 4096 (the 2D frame's column pass) */
