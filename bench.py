@@ -303,10 +303,11 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         data = "synth.buried_tone seed 4 (iid U[-1,1] plus a 1e-3 tone at a seeded bin)"
     elif x_reuse is not None and x_reuse.numel() >= E:
         x = x_reuse[:E]
-        data = "iid U[-1,1] (the headline's seed-2 input, first 2^26 elements)"
+        data = "iid U[-1,1) from the device generator (the headline's seed-2 input, first 2^26 elements)"
     else:
-        x = torch.from_numpy(synth.uniform(3, 1, E)[0]).to(dev)
-        data = "iid U[-1,1] seed 3"
+        x = torch.empty(E, dtype=torch.complex64, device=dev)
+        gbfft.fft_fill_uniform(x.data_ptr(), E, 3, 0, torch.cuda.current_stream().cuda_stream)
+        data = "iid U[-1,1) from the device generator, seed 3"
     y = torch.empty_like(x)
     plans, order = {}, []
     # (precision, variant): FP32, the tcgen05 classes, and at N = 4096 the
@@ -465,9 +466,7 @@ def section_serve(args, jobs: int, load: float) -> dict:
     dev = torch.device("cuda", torch.cuda.current_device())
     in_elems = 1 << 30                                                 # 8 GiB of inputs
     xin = torch.empty(in_elems, dtype=torch.complex64, device=dev)
-    chunk = torch.from_numpy(synth.uniform(5, 1, 1 << 24)[0]).to(dev)
-    for off in range(0, in_elems, chunk.numel()):
-        xin[off:off + chunk.numel()].copy_(chunk)
+    gbfft.fft_fill_uniform(xin.data_ptr(), in_elems, 5, 0, torch.cuda.current_stream().cuda_stream)
     ring_elems = 6 << 30                                               # 48 GiB of outputs
     yout = torch.empty(ring_elems, dtype=torch.complex64, device=dev)
     torch.cuda.synchronize()
@@ -741,8 +740,10 @@ def ours(args, rank: int, world: int) -> None:
 
     dev = torch.device("cuda", torch.cuda.current_device())
     E = 2 ** TOTAL_LOG
-    x_np = synth.uniform(2, 1, E)[0]
-    x = torch.from_numpy(x_np).to(dev)
+    # seeded uniform noise generated on the device (counter-based hash; the
+    # same values as synth.uniform_hash(2, E))
+    x = torch.empty(E, dtype=torch.complex64, device=dev)
+    gbfft.fft_fill_uniform(x.data_ptr(), E, 2, 0, torch.cuda.current_stream().cuda_stream)
     y = torch.empty_like(x)
     plans = {}
     for lg in LOGS:
@@ -820,7 +821,8 @@ def ours(args, rank: int, world: int) -> None:
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
-        h_in = torch.from_numpy(x_np).pin_memory()
+        h_in = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        h_in.copy_(x)
         h_out = torch.empty_like(h_in).pin_memory()
 
         def e2e_step():
@@ -897,7 +899,8 @@ def ours(args, rank: int, world: int) -> None:
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic: iid U[-1,1] complex64 (seed 2), generated on the host",
+            "data": "synthetic: iid U[-1,1) complex64 from a counter-based hash (SplitMix64, "
+                    "seed 2), generated on the device (fft_fill_uniform)",
             "config": headline_config(args, world),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1),
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(frac, 4),

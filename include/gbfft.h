@@ -404,6 +404,18 @@ GBFFT_API fft_status_t fft_server_stats(fft_server_t server, fft_server_stats_t*
 /* Stop the worker, wait for running work, free plans and workspaces. */
 GBFFT_API fft_status_t fft_server_destroy(fft_server_t server);
 
+/* ---------------------------------------------------- synthetic inputs --
+ * Seeded test signals generated on the device (the paper's workloads are
+ * synthetic radar data; this fills the uniform-noise inputs of the benchmarks
+ * without a host round trip).  Writes `count` complex64 values to the device
+ * buffer `out` (8-byte aligned), element j with real and imaginary parts
+ * uniform in [-1, 1) from a counter-based hash (SplitMix64 at stream indices
+ * 2 (first + j) and 2 (first + j) + 1 for `seed`), so out = values
+ * first .. first + count - 1 of one endless seeded sequence: slices can be
+ * generated separately.  Asynchronous on `stream`.  No plan is involved. */
+GBFFT_API fft_status_t fft_fill_uniform(void* out, int64_t count, uint64_t seed, uint64_t first,
+                                        void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 GBFFT_API const char* fft_last_error(void);
 

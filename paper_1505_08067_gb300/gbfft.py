@@ -97,6 +97,7 @@ _SIGS = {
     "fft_execute_host": [_vp, _vp, _vp, _vp, _vp, _vp],
     "fft_execute_graph": [_vp, _vp, _vp, _vp],
     "fft_execute_noalloc": [_i64, _i64, ctypes.c_int, _vp, _vp, _vp],
+    "fft_fill_uniform": [_vp, _i64, ctypes.c_uint64, ctypes.c_uint64, _vp],
     "fft_plan_destroy": [_vp],
     "fft_plan_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "fft_plan_launch_count": [_vp, ctypes.POINTER(ctypes.c_int)],
@@ -209,6 +210,14 @@ def fft_execute_noalloc(n: int, batch: int, direction: int, in_ptr: int, out_ptr
                         stream: int = 0) -> None:
     """Plan-free transform that allocates no device memory (see include/gbfft.h)."""
     _check(load().fft_execute_noalloc(int(n), int(batch), direction, in_ptr, out_ptr, stream))
+
+
+def fft_fill_uniform(out_ptr: int, count: int, seed: int, first: int = 0, stream: int = 0) -> None:
+    """Device buffer out_ptr[0 .. count) <- complex64 values with parts uniform in
+    [-1, 1), values first .. first + count - 1 of the seeded counter-based
+    sequence (synth.uniform_hash computes the same values on the host)."""
+    _check(load().fft_fill_uniform(out_ptr, int(count), int(seed) & (2 ** 64 - 1),
+                                   int(first), stream))
 
 
 def fft_plan_destroy(plan: int) -> None:

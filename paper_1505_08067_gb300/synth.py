@@ -11,6 +11,9 @@ Workload recipes (the paper measures on no public dataset; these stand in for
 its radar workloads):
 
 * ``uniform``      -- iid U[-1, 1] real and imaginary parts.
+* ``uniform_hash`` -- the same distribution from a counter-based hash
+                      (SplitMix64): the host twin of the library's on-device
+                      generator ``fft_fill_uniform``, bit for bit.
 * ``tones``        -- per transform, unit-amplitude complex exponentials at
                       seeded integer bins; the forward DFT of one tone at bin k0
                       is N at k0 and 0 elsewhere.
@@ -27,7 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["uniform", "tones", "tone_bins", "buried_tone", "sar_frame", "chirp"]
+__all__ = ["uniform", "uniform_hash", "tones", "tone_bins", "buried_tone", "sar_frame", "chirp"]
 
 
 def uniform(seed: int, batch: int, n: int) -> np.ndarray:
@@ -38,6 +41,33 @@ def uniform(seed: int, batch: int, n: int) -> np.ndarray:
     out = np.empty((batch, n), dtype=np.complex64)
     out.real = re
     out.imag = im
+    return out
+
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+
+
+def uniform_hash(seed: int, count: int, first: int = 0) -> np.ndarray:
+    """(count,) complex64: values first .. first + count - 1 of the seeded
+    counter-based sequence the library's fft_fill_uniform writes on the
+    device.  SplitMix64 (Steele, Lea, Flood 2014) at stream index k: state
+    seed + (k + 1) * 0x9E3779B97F4A7C15, two xor-shift-multiply rounds and a
+    final xor-shift; the top 24 bits u give 2 u 2^-24 - 1 in [-1, 1).  Element
+    j takes indices 2 (first + j) (real part) and 2 (first + j) + 1."""
+    with np.errstate(over="ignore"):
+        k = (np.uint64(2) * (np.uint64(first) + np.arange(count, dtype=np.uint64)))
+        k = np.stack([k, k + np.uint64(1)], axis=-1).reshape(-1)
+        z = np.uint64(seed & (2 ** 64 - 1)) + (k + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _MIX1
+        z = (z ^ (z >> np.uint64(27))) * _MIX2
+        z = z ^ (z >> np.uint64(31))
+    u = (z >> np.uint64(40)).astype(np.float32) * np.float32(2.0 ** -24)
+    v = np.float32(2.0) * u - np.float32(1.0)
+    out = np.empty(count, dtype=np.complex64)
+    out.real = v[0::2]
+    out.imag = v[1::2]
     return out
 
 
