@@ -162,7 +162,7 @@ struct Umma {
     for (int rb = warp >> 2; rb < G::RB; rb += 2) {
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + 32u * rb;
       const int m = rb * 128 + q * 32 + lane;
-      const typename Body::RowPart rp = Body::template row_part<t>(m);
+      typename Body::RowPart rp = Body::template row_part<t>(d, m);
       uint32_t r[16];
       tmem_ld16(ta, r);  // outputs 0..7
       Body::template epilogue_part<t, 0, 8>(d, gout, valid, rp, r, a_hi, a_lo);

@@ -336,9 +336,18 @@ GB_UNROLL
     int tr, pos;
     uint32_t off;
     int tw;
+    cf step;  // next stages: the ratio of consecutive outputs' twiddles
+    cf run;   // the twiddle of the next output to be stored (updated as outputs are)
   };
+  //
+  // Twiddles: output o of the butterfly becomes input i' of its next-stage
+  // butterfly with k' = k + o*Ns (k = jb mod Ns) and i' independent of o
+  // (the stage's outputs keep their block: (jb / Ns) * 16 Ns lies in one
+  // multiple of L/16), so its twiddle w_{16 Ns'}^{i' k'} = c * s^o with
+  // c = w^{i' k} and s = w^{i' Ns} = (c s) * conj(c): two table loads per
+  // row, then a running product (at most 16 further roundings, ~1e-6).
   template <int t>
-  GB_HD static RowPart row_part(int m) {
+  GB_HD static RowPart row_part(const PassDesc& d, int m) {
     RowPart rp{};
     const int u = umma_u_of_row<LOGL>(t, m);
     if (t == G::NTC - 1) {
@@ -348,6 +357,13 @@ GB_UNROLL
       int u2, i2;
       umma_next<LOGL>(t, u, 0, u2, i2, rp.tw);
       rp.off = umma_aoff(umma_row_of_u<LOGL>(t + 1, u2), i2);
+      int u2o, i2o, two;
+      umma_next<LOGL>(t, 0, 1, u2o, i2o, two);  // output 1's part of the table index
+      const cf* tw = d.tw + d.tw_off[ST0 + t + 1];
+      const cf c0 = Mem::ldtw(tw + rp.tw);
+      const cf c1 = Mem::ldtw(tw + (rp.tw ^ two));
+      rp.step = cmul(c1, cconj(c0));
+      rp.run = c0;
     }
     return rp;
   }
@@ -358,7 +374,7 @@ GB_UNROLL
   // the next stage's A operand.  Each output's own part of the addressing is
   // a compile-time constant XORed into the row's part.
   template <int t, int O0 = 0, int NO = 16>
-  GB_HD static void epilogue_part(const PassDesc& d, cf* gout, int valid, const RowPart& rp,
+  GB_HD static void epilogue_part(const PassDesc& d, cf* gout, int valid, RowPart& rp,
                                   const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
     if (t == G::NTC - 1) {
       if (rp.tr >= valid) return;
@@ -375,7 +391,6 @@ GB_UNROLL
         Mem::stg(o_base, rp.pos | (o << G::ns_log(t)), swap ? mk(v.y, v.x) : v);
       }
     } else {
-      const cf* tw = d.tw + d.tw_off[ST0 + t + 1];
 GB_UNROLL
       for (int j = 0; j < NO; ++j) {
         const int o = O0 + j;
@@ -383,7 +398,8 @@ GB_UNROLL
         umma_next<LOGL>(t, 0, o, u2o, i2o, two);
         const uint32_t off = rp.off ^ umma_aoff(umma_row_of_u<LOGL>(t + 1, u2o), i2o);
         cf v = mk(u32_as_f32(r[2 * j]), u32_as_f32(r[2 * j + 1]));
-        v = cmul(v, Mem::ldtw(tw + (rp.tw ^ two)));
+        v = cmul(v, rp.run);               // c * s^o
+        rp.run = cmul(rp.run, rp.step);
         put_a(a_hi, a_lo, off, v);
       }
     }
@@ -392,7 +408,8 @@ GB_UNROLL
   template <int t, int O0 = 0, int NO = 16>
   GB_HD static void epilogue_row(const PassDesc& d, cf* gout, int valid, int m,
                                  const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
-    epilogue_part<t, O0, NO>(d, gout, valid, row_part<t>(m), r, a_hi, a_lo);
+    RowPart rp = row_part<t>(d, m);
+    epilogue_part<t, O0, NO>(d, gout, valid, rp, r, a_hi, a_lo);
   }
 };
 

@@ -635,11 +635,13 @@ void run_umma_t(const PassDesc& d, const cf* in, cf* out) {
           for (int rb = warp >> 2; rb < G::RB; rb += 2) {
             const int m = rb * 128 + (warp & 3) * 32 + lane;
             ++row_reads[m];
-            uint32_t r[16];  // the kernel reads the row in two halves
+            // as the kernel: one row part, the row read in two halves
+            typename Body::RowPart rp = Body::template row_part<t>(d, m);
+            uint32_t r[16];
             memcpy(r, &D[(size_t)m * 32], sizeof r);
-            Body::template epilogue_row<t, 0, 8>(d, gout, valid, m, r, a_hi, a_lo);
+            Body::template epilogue_part<t, 0, 8>(d, gout, valid, rp, r, a_hi, a_lo);
             memcpy(r, &D[(size_t)m * 32 + 16], sizeof r);
-            Body::template epilogue_row<t, 8, 8>(d, gout, valid, m, r, a_hi, a_lo);
+            Body::template epilogue_part<t, 8, 8>(d, gout, valid, rp, r, a_hi, a_lo);
           }
       for (int m = 0; m < G::ROWS; ++m)
         if (row_reads[m] != 1) { err("tensor-memory row not read exactly once", m); break; }
