@@ -314,13 +314,22 @@ GB_UNROLL
           uint32_t offj;
           int ij, twj;
           first_of(ej, 0, offj, ij, twj);
+          // output o becomes input i of its stage-0 butterfly with k = o and
+          // i the same for every o, so its twiddle is s^o with s = w^i: one
+          // table load (entry i * r0 + 1), powers by a running product
+          const int i = ib ^ ij;
+          const cf s1 = i > 0 ? Mem::ldtw(tw + ((twb ^ twj) | 1)) : mk(1.f, 0.f);
+          cf w = s1;
 GB_UNROLL
           for (int o = 0; o < G::R0; ++o) {
             uint32_t offo;
             int io, two;
             first_of(0, o, offo, io, two);
-            const int i = ib ^ ij ^ io;
-            const cf v = i > 0 ? cmul(y[o], Mem::ldtw(tw + (twb ^ twj ^ two))) : y[o];
+            cf v = y[o];
+            if (o > 0 && i > 0) {
+              v = cmul(v, w);
+              w = cmul(w, s1);
+            }
             put_a(a_hi, a_lo, offb ^ offj ^ offo, v);
           }
         }
