@@ -265,9 +265,25 @@ SECTION_DESC = {
     "tc": ("batched 1D complex64 FFT N=4096 batch=32768 (2^27 elements, uniform plus a "
            "1e-3 tone), and N=8192 / 16384 on the same 2^27 elements: FP32 path and the "
            "tensor-core classes FP16, BF16, split BF16x3 (tcgen05 kernel; at N=4096 also the "
-           "warp-level MMA kernel), forward and inverse"),
+           "warp-level MMA kernel) and FP16 with complex32 storage (the same input rounded to "
+           "FP16 pairs, 4 B per element), forward and inverse"),
 }
-TC_BOUNDS = {"tc_fp16": 2e-3, "tc_bf16": 2e-3, "tc_bf16x3": 5e-6 * 12}
+TC_BOUNDS = {"tc_fp16": 2e-3, "tc_bf16": 2e-3, "tc_bf16x3": 5e-6 * 12, "tc_fp16_c32": 2e-3}
+PREC_C32 = 4  # FFT_PREC_TC_FP16_C32: complex32 input and output
+
+
+def _to_c32(x):
+    """complex64 device tensor -> complex32 (FP16 pairs, round to nearest even)."""
+    import torch
+    return torch.view_as_real(x).to(torch.float16).contiguous().view(torch.complex32).reshape(x.shape)
+
+
+def _c32_to_numpy(y):
+    """complex32 device tensor -> complex128 NumPy array of the same shape."""
+    import numpy as np
+    import torch
+    f = y.reshape(-1).view(torch.float16).float().cpu().numpy().astype(np.float64)
+    return (f[0::2] + 1j * f[1::2]).reshape(tuple(y.shape))
 
 
 def section_items(kind: str, args, x_reuse=None) -> dict:
@@ -309,10 +325,14 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         gbfft.fft_fill_uniform(x.data_ptr(), E, 3, 0, torch.cuda.current_stream().cuda_stream)
         data = "iid U[-1,1) from the device generator, seed 3"
     y = torch.empty_like(x)
+    # complex32 copies of the input and an output for the FP16 class with
+    # complex32 storage (made before the timed region)
+    x16 = _to_c32(x) if kind == "tc" else None
+    y16 = torch.empty_like(x16) if kind == "tc" else None
     plans, order = {}, []
     # (precision, variant): FP32, the tcgen05 classes, and at N = 4096 the
     # warp-level MMA classes beside them
-    precs = [(0, 0), (1, 0), (2, 0), (3, 0)] if kind == "tc" else [(0, 0)]
+    precs = [(0, 0), (1, 0), (2, 0), (3, 0), (PREC_C32, 0)] if kind == "tc" else [(0, 0)]
     t_plan = time.perf_counter()
     for shape, batch in items:
         extra = [(1, 1), (2, 1), (3, 1)] if kind == "tc" and shape == (4096,) else []
@@ -332,9 +352,17 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
                 order.append((key, int(np.prod(shape)) * batch, int(np.log2(np.prod(shape)))))
     t_plan = time.perf_counter() - t_plan
     stream = torch.cuda.current_stream()
+
+    def io(key):  # the buffers of an item: complex32 for that class
+        return (x16, y16) if key[2] == PREC_C32 else (x, y)
+
+    def esz(key):  # bytes per stored element
+        return 4 if key[2] == PREC_C32 else 8
+
     for _ in range(args.warmup):
         for key, e, _lg in order:
-            plans[key].execute(x[:e], y[:e], stream)
+            xi, yi = io(key)
+            plans[key].execute(xi[:e], yi[:e], stream)
     torch.cuda.synchronize()
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in order] for _ in range(args.steps)]
@@ -347,8 +375,9 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
     a.record(stream)
     for s in range(args.steps):
         for i, (key, e, _lg) in enumerate(order):
+            xi, yi = io(key)
             ev[s][i][0].record(stream)
-            plans[key].execute(x[:e], y[:e], stream)
+            plans[key].execute(xi[:e], yi[:e], stream)
             ev[s][i][1].record(stream)
     bnd.record(stream)
     torch.cuda.synchronize()
@@ -362,12 +391,12 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         t = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
         passes = len(plans[key].describe()["passes"])
         pname = PREC_NAMES[key[2]] + ("_warp_mma" if key[3] == 1 else "")
-        gbs = 16.0 * passes * e / (t * 1e-3) / 1e9
+        gbs = 2.0 * esz(key) * passes * e / (t * 1e-3) / 1e9
         per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'} {pname}"] = {
             "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
             "passes": passes, "gbs": round(gbs, 1), "frac": round(gbs / peaks["hbm_gbs"], 4),
             "tuned": _tuned(plans[key])}
-    tot_bytes = sum(16.0 * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
+    tot_bytes = sum(2.0 * esz(k) * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
     launches = sum(plans[k].launch_count for k, _e, _l in order) * args.steps
     out = {
         "workload": SECTION_DESC[kind], "data": data, "steps": args.steps, "warmup": args.warmup,
@@ -375,7 +404,7 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
                      "achieved": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9, 1),
                      "frac": round(tot_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
-                     "alg_bytes": "16 B per element per pass"},
+                     "alg_bytes": "16 B per element per pass (8 B for complex32 storage)"},
         "per_item": per, "clocks": clocks, "gpu_launches": launches,
         "plan_create_s": round(t_plan, 2),
         "l2": "inputs of 256 MiB to 1 GiB per launch, larger than L2; no flush"}
@@ -390,7 +419,7 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         for shape, _b in items:
             nm = "x".join(map(str, shape))
             fp32 = {d: per[f"{nm} {d} fp32"]["ms"] for d in ("fwd", "inv")}
-            names = ["tc_fp16", "tc_bf16", "tc_bf16x3"]
+            names = ["tc_fp16", "tc_bf16", "tc_bf16x3", "tc_fp16_c32"]
             if shape == (4096,):
                 names += ["tc_fp16_warp_mma", "tc_bf16_warp_mma", "tc_bf16x3_warp_mma"]
             vs[nm] = {p: {d: round(fp32[d] / per[f"{nm} {d} {p}"]["ms"], 3) for d in ("fwd", "inv")}
@@ -398,11 +427,11 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         out["vs_fp32"] = vs
     for p in plans.values():
         p.close()
-    del x, y
+    del x, y, x16, y16
     return out
 
 
-PREC_NAMES = ["fp32", "tc_fp16", "tc_bf16", "tc_bf16x3"]
+PREC_NAMES = ["fp32", "tc_fp16", "tc_bf16", "tc_bf16x3", "tc_fp16_c32"]
 
 
 def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: float = 1e-3):
@@ -410,16 +439,20 @@ def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: floa
     tone-bearing input, against this library's FP32 path (itself 2-5e-7 from the
     FP64 oracle in the parity tests): max and mean relative L2 per transform, and
     the error at each transform's tone bin relative to the tone's exact
-    contribution n * amplitude."""
+    contribution n * amplitude.  The complex32 class reads the input rounded to
+    FP16 pairs, so its error includes that rounding."""
     import numpy as np
     import torch
 
     xs = x[:count * n]
     outs = {}
-    for prec, var in ((0, 0), (1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)):
+    for prec, var in ((0, 0), (1, 0), (2, 0), (3, 0), (PREC_C32, 0), (1, 1), (2, 1), (3, 1)):
         name = PREC_NAMES[prec] + ("_warp_mma" if var == 1 else "")
         with gbfft.Plan(n, count, -1, prec, **({"variant": var} if prec else {})) as p:
-            outs[name] = p.execute(xs).cpu().numpy().reshape(count, n).astype(np.complex128)
+            if prec == PREC_C32:
+                outs[name] = _c32_to_numpy(p.execute(_to_c32(xs))).reshape(count, n)
+            else:
+                outs[name] = p.execute(xs).cpu().numpy().reshape(count, n).astype(np.complex128)
             torch.cuda.synchronize()
     ref = outs.pop("fp32")
     k0 = np.asarray(bins[:count])

@@ -17,14 +17,15 @@
  *
  * Conventions shared by every entry point:
  *   - Data are complex64: interleaved (re, im) IEEE float32, 8 bytes per
- *     element, natural order in and out.
+ *     element, natural order in and out (complex32, 4 bytes per element, for
+ *     plans and jobs of precision FFT_PREC_TC_FP16_C32).
  *   - 1D: element i of transform b is at b*n[0] + i.
  *     2D: n = {rows, cols}; frame b is row-major [rows][cols] (cols
  *     contiguous) at b*rows*cols.
  *   - direction FFT_FORWARD (-1) uses exp(-2 pi i nk/N); FFT_INVERSE (+1) uses
  *     exp(+2 pi i nk/N) and is NOT normalised: inverse(forward(x)) = N x.
  *   - Pointers named `in`/`out` are device pointers owned by the caller,
- *     8-byte aligned.  `in` is never written.  in == out (in place) is allowed.
+ *     aligned to the element size (8 bytes; 4 for complex32).  `in` is never written.  in == out (in place) is allowed.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   - Errors are returned as fft_status_t and never abort; fft_last_error()
  *     gives a human-readable message for the calling thread.  No entry point
@@ -63,22 +64,33 @@ typedef enum {
 enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
 
 /*
- * Precision classes.  Data are complex64 in every class; the tensor-core
- * classes compute each radix-16 stage as a dense 16-point DFT matmul on the
- * tensor cores with FP32 accumulation (twiddles stay FP32), for batched 1D
- * lengths 16, 256 and 4096:
+ * Precision classes.  Data are complex64 (two FP32 values, 8 bytes) in every
+ * class but FFT_PREC_TC_FP16_C32; the tensor-core classes compute each
+ * radix-16 stage as a dense 16-point DFT matmul on the tensor cores with FP32
+ * accumulation (twiddles stay FP32), after a radix-2/4/8 FP32 stage when the
+ * length is not a power of 16, for batched 1D lengths 2^4 .. 2^14:
  *   FFT_PREC_TC_FP16    stage inputs and DFT matrix rounded to FP16 (each
  *                       stage's input scaled by 1/16, exactly undone at the end)
  *   FFT_PREC_TC_BF16    rounded to BF16
  *   FFT_PREC_TC_BF16X3  split x = x_hi + x_lo, F = F_hi + F_lo in BF16 and
  *                       x_hi F_hi + x_hi F_lo + x_lo F_hi accumulated (about
  *                       16 significant bits per product: near-FP32 accuracy)
+ *   FFT_PREC_TC_FP16_C32  the FP16 class with input and output stored as
+ *                       complex32: FP16 real and imaginary parts interleaved,
+ *                       4 bytes per element, so a transform moves half the
+ *                       bytes of the complex64 classes.  The output is rounded
+ *                       to FP16 once more; a value beyond the FP16 range
+ *                       (|v| > 65504) becomes an infinity.  Buffers need
+ *                       4-byte alignment.  Plans, fft_execute,
+ *                       fft_execute_graph, fft_execute_host (byte counts of 4
+ *                       per element) and the server take it.
  */
 enum {
   FFT_PREC_FP32 = 0,     /* FP32 data, FP32 arithmetic, FP64-generated twiddles */
   FFT_PREC_TC_FP16 = 1,
   FFT_PREC_TC_BF16 = 2,
-  FFT_PREC_TC_BF16X3 = 3
+  FFT_PREC_TC_BF16X3 = 3,
+  FFT_PREC_TC_FP16_C32 = 4
 };
 
 /*

@@ -173,12 +173,18 @@ fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, in
   return build_plan(plan, n, dims, batch, direction, precision, options);
 }
 
+// Data pointers are aligned to the plan's element size (complex64 or complex32).
+static bool aligned_io(const PlanSpec& s, const void* p) {
+  return ((uintptr_t)p % (uintptr_t)elem_bytes(s.precision)) == 0;
+}
+
 fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream) {
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
   if (plan->spec.batch == 0) return FFT_OK;
   if (!in || !out) return fail(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
-  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7))
-    return fail(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned (complex64)");
+  if (!aligned_io(plan->spec, in) || !aligned_io(plan->spec, out))
+    return fail(FFT_ERR_INVALID_ARG, "in/out must be aligned to the element size (%d bytes)",
+                elem_bytes(plan->spec.precision));
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -198,8 +204,8 @@ fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_o
   if (s.batch == 0) return FFT_OK;
   if (!host_in || !host_out || !dev_in || !dev_out)
     return fail(FFT_ERR_INVALID_ARG, "null buffer");
-  if (((uintptr_t)dev_in & 7) || ((uintptr_t)dev_out & 7))
-    return fail(FFT_ERR_INVALID_ARG, "device buffers must be 8-byte aligned");
+  if (!aligned_io(s, dev_in) || !aligned_io(s, dev_out))
+    return fail(FFT_ERR_INVALID_ARG, "device buffers must be aligned to the element size");
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -218,7 +224,7 @@ fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_o
       return cuda_fail(e, "stream/event creation for host execution");
   }
   const int64_t E = elems_per_batch(s);
-  const size_t per = (size_t)E * 8;
+  const size_t per = (size_t)E * elem_bytes(s.precision);
   // chunks of whole batch entries, about 32 MiB each (1D only; 2D runs whole)
   int64_t chunk = s.batch;
   if (s.dims == 1) chunk = std::max<int64_t>(1, (int64_t)((32u << 20) / per));
@@ -260,8 +266,9 @@ fft_status_t fft_execute_graph(fft_plan_t plan, const void* in, void* out, void*
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
   if (plan->spec.batch == 0) return FFT_OK;
   if (!in || !out) return fail(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
-  if (((uintptr_t)in & 7) || ((uintptr_t)out & 7))
-    return fail(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned (complex64)");
+  if (!aligned_io(plan->spec, in) || !aligned_io(plan->spec, out))
+    return fail(FFT_ERR_INVALID_ARG, "in/out must be aligned to the element size (%d bytes)",
+                elem_bytes(plan->spec.precision));
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");

@@ -24,7 +24,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
       l.block = p.block;
       l.smem = p.smem;
       if (p.tc_prec) {
-        l.fn = resolve_tc_pass(p.logL, p.tc_prec, p.variant);
+        l.fn = resolve_tc_pass(p.logL, p.tc_prec, p.variant, p.io16);
         if (!l.fn) return cudaErrorInvalidDeviceFunction;
         l.specialised = true;
       } else {
@@ -94,10 +94,11 @@ cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const 
     return enqueue_range(s, launches, in, out, work, b0, nb, st);
   // sub-batches in stream order, each reusing the workspace from its start
   const int64_t E = s.dims == 1 ? s.n[0] : s.n[0] * s.n[1];
+  const int64_t eb = elem_bytes(s.precision);
   for (int64_t c = 0; c < nb; c += s.chunk_batch) {
     const int64_t n = std::min(s.chunk_batch, nb - c);
-    cudaError_t e = enqueue_range(s, launches, static_cast<const cf*>(in) + c * E,
-                                  static_cast<cf*>(out) + c * E, work, b0 + c, n, st);
+    cudaError_t e = enqueue_range(s, launches, static_cast<const char*>(in) + c * E * eb,
+                                  static_cast<char*>(out) + c * E * eb, work, b0 + c, n, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -124,7 +125,7 @@ static cudaError_t enqueue_range(const PlanSpec& s, const PassLaunch* launches, 
         d.status = l.d.status;
         d.h = l.d.h;
         l.d = d;
-        l.fn = p.tc_prec ? resolve_tc_pass(p.logL, p.tc_prec, p.variant)
+        l.fn = p.tc_prec ? resolve_tc_pass(p.logL, p.tc_prec, p.variant, p.io16)
                          : resolve_kernel(l.R, l.lmap, l.smap, l.d, s.generic_only, &l.specialised);
         e = prepare_launch(l);
         if (e != cudaSuccess) return e;

@@ -78,9 +78,13 @@ int umma_tmem_cols(int logL);
 // threads (from the kernel's attributes and the device's limits), and by
 // tensor memory when tmem_cols > 0 (512 columns per SM).
 cudaError_t resident_blocks(const void* fn, int block, size_t smem, int tmem_cols, int* blocks);
-// The kernel of a tensor-core pass of the given variant (0 tcgen05, 1 warp MMA).
-inline const void* resolve_tc_pass(int logL, int prec, int variant) {
+// The tcgen05 form of the FP16 class with complex32 input and output.
+const void* resolve_umma_c32(int logL, size_t* smem);
+// The kernel of a tensor-core pass of the given variant (0 tcgen05, 1 warp MMA);
+// io16: complex32 input and output (tcgen05, FP16 only).
+inline const void* resolve_tc_pass(int logL, int prec, int variant, int io16 = 0) {
   size_t sm = 0;
+  if (io16) return variant == 0 && prec == 1 ? resolve_umma_c32(logL, &sm) : nullptr;  // FP16
   return variant == 1 ? resolve_tc(logL, prec) : resolve_umma(logL, prec, &sm);
 }
 

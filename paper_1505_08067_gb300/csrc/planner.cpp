@@ -221,7 +221,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
   if (batch < 0) { fail(FFT_ERR_INVALID_ARG, "batch must be >= 0"); return; }
   if (direction != FFT_FORWARD && direction != FFT_INVERSE)
     { fail(FFT_ERR_INVALID_ARG, "direction must be FFT_FORWARD (-1) or FFT_INVERSE (+1)"); return; }
-  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_TC_BF16X3)
+  if (precision < FFT_PREC_FP32 || precision > FFT_PREC_TC_FP16_C32)
     { fail(FFT_ERR_INVALID_ARG, "unknown precision"); return; }
   if (precision != FFT_PREC_FP32) {
     // tensor-core classes: batched 1D lengths 2^4 .. 2^14 on the tcgen05
@@ -233,6 +233,10 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
     }
     const bool ok = o.variant == 1 ? (l == 16 || l == 256 || l == 4096)
                                    : (l >= 16 && l <= 16384 && is_pow2(l));
+    if (precision == FFT_PREC_TC_FP16_C32 && o.variant == 1) {
+      fail(FFT_ERR_NOT_IMPLEMENTED, "complex32 storage runs on the tcgen05 kernel (variant 0)");
+      return;
+    }
     if (!ok) {
       fail(FFT_ERR_NOT_IMPLEMENTED,
            o.variant == 1
@@ -345,7 +349,8 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p.tiles = p.tiles_inner;
       p.in = Strides{0, (int64_t)p.G * N, N, 1};
       p.out = p.in;
-      p.tc_prec = precision;
+      p.tc_prec = precision == FFT_PREC_TC_FP16_C32 ? FFT_PREC_TC_FP16 : precision;
+      p.io16 = precision == FFT_PREC_TC_FP16_C32;
       p.conj_in = p.conj_out = inv;
       s.passes.push_back(p);
     } else if (logN <= bmax) {
@@ -571,7 +576,8 @@ std::string describe(const PlanSpec& s) {
         << ",\"block\":" << p.block << ",\"grid\":" << p.grid << ",\"smem\":" << p.smem
         << ",\"pitch\":" << p.pitch << ",\"epi\":" << p.epi << ",\"epi_logN\":" << p.epi_logN
         << ",\"conj_in\":" << p.conj_in << ",\"conj_out\":" << p.conj_out
-        << ",\"variant\":" << p.variant << ",\"tc_prec\":" << p.tc_prec;
+        << ",\"variant\":" << p.variant << ",\"tc_prec\":" << p.tc_prec
+        << ",\"io16\":" << p.io16;
       if (p.conv)
         o << ",\"conv\":1,\"h_dim\":" << p.h_dim << ",\"h_lines\":" << p.h_lines
           << ",\"h_scale\":" << p.h_scale;

@@ -70,6 +70,7 @@ struct PassSpec {
   int64_t h_lines = 1;          // 1 or the lines per frame along this dimension
   float h_scale = 1.f;
   int tc_prec = 0;              // tensor-core class (FFT_PREC_TC_*), 0 for FP32
+  int io16 = 0;                 // tensor-core pass with complex32 (FP16) input and output
   bool batch_is_tiles = false;  // contiguous pass: batch maps to tiles of G transforms
   int64_t units_per_batch = 1;  // contiguous pass: transforms per batch entry
   // PASS_COPY
@@ -138,6 +139,10 @@ Sched default_schedule(int logL, int logR);
 
 // Heap-free: fills `s` in place.  With `conv`, every dimension is a fast
 // convolution pass (direction is ignored; the plan's filters are bound later).
+// Bytes of one data element of a plan or job of this precision: complex64,
+// or complex32 for FFT_PREC_TC_FP16_C32.
+inline int elem_bytes(int precision) { return precision == FFT_PREC_TC_FP16_C32 ? 4 : 8; }
+
 void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direction,
                int precision, const fft_plan_options_t* opt, const Caps& caps,
                const ConvSpec* conv = nullptr);

@@ -45,8 +45,9 @@ using namespace gbfft;
 namespace {
 
 constexpr uint32_t kServerMagic = 0x53525646u;
-// Run-time estimate of a job for the scheduler: its algorithmic bytes (16 per
-// element per pass) at an effective rate, plus a launch overhead.
+// Run-time estimate of a job for the scheduler: its algorithmic bytes (one
+// read and one write of each element per pass) at an effective rate, plus a
+// launch overhead.
 constexpr double kEstBytesPerS = 3.0e12;
 constexpr double kEstLaunchS = 6e-6;
 constexpr size_t kLatencyWindow = size_t(1) << 20;  // latency samples kept for p50 / p99
@@ -449,14 +450,15 @@ fft_status_t fft_server_submit(fft_server_t s, const fft_job_t* job, uint64_t* t
   if (probe.status != FFT_OK) return set_error(probe.status, probe.error);
   if (job->batch < 1) return set_error(FFT_ERR_INVALID_ARG, "batch must be >= 1");
   if (!job->in || !job->out) return set_error(FFT_ERR_INVALID_ARG, "in/out must be device buffers");
-  if (((uintptr_t)job->in & 7) || ((uintptr_t)job->out & 7))
-    return set_error(FFT_ERR_INVALID_ARG, "in/out must be 8-byte aligned");
+  const int eb = elem_bytes(job->precision);  // complex64, or complex32
+  if (((uintptr_t)job->in % eb) || ((uintptr_t)job->out % eb))
+    return set_error(FFT_ERR_INVALID_ARG, "in/out must be aligned to the element size");
   const int64_t e = job_elems(*job) * job->batch;
   // workspace of one sub-batch (two-pass plans run large batches in sub-batches)
   const int64_t ws_entries =
       probe.work_elems > 0 ? std::min<int64_t>(job->batch, two_pass_chunk(job_elems(*job))) : 0;
   const size_t ws = (size_t)probe.work_elems * 8 * (size_t)ws_entries;
-  const size_t bytes = (size_t)e * 16 + (ws ? ws_class(ws) : 0);
+  const size_t bytes = (size_t)e * 2 * eb + (ws ? ws_class(ws) : 0);
   std::lock_guard<std::mutex> lock(s->mu);
   SchedJob sj;
   sj.id = s->next_id++;
@@ -470,7 +472,7 @@ fft_status_t fft_server_submit(fft_server_t s, const fft_job_t* job, uint64_t* t
   sj.groupable = probe.passes.size() == 1 && probe.passes[0].batch_is_tiles &&
                  probe.passes[0].tc_prec == 0 && job->dims == 1;
   sj.t_submit = now_s();
-  sj.cost = (double)e * 16.0 * (double)probe.passes.size() / kEstBytesPerS + kEstLaunchS;
+  sj.cost = (double)e * 2.0 * eb * (double)probe.passes.size() / kEstBytesPerS + kEstLaunchS;
   if (!s->sched.submit(sj))
     return set_error(FFT_ERR_OUT_OF_MEMORY, "job needs more bytes than the server's budget");
   JobRec rec;

@@ -227,9 +227,11 @@ GB_HD void umma_first_target(int e, int o, int& u, int& i, int& tw) {
 
 // ------------------------------------------------------- per-thread body --
 // The kernel's per-thread steps, shared with the CPU replay through the memory
-// policy Mem: ldg / stg (global, element offsets), ldtw (twiddle table) and
-// sts32 (a 32-bit store at a byte address of the A operands).  a_hi / a_lo are
-// the byte addresses of the two A operands (a_lo only for the split class).
+// policy Mem: at (a base pointer advanced by elements), ldg_sw / stg_sw (global
+// element loads and stores, real and imaginary parts swapped when asked),
+// ldtw (twiddle table), sts32 (a 32-bit store at a byte address of the A
+// operands) and kHalfIO (complex32 storage).  a_hi / a_lo are the byte
+// addresses of the two A operands (a_lo only for the split class).
 template <int LOGL, int PREC, class Mem>
 struct UmmaBody {
   using G = UmmaGeo<LOGL>;
@@ -237,12 +239,20 @@ struct UmmaBody {
   static constexpr bool SPLIT = PREC == TC_BF16X3;
   // first twiddle table of the tensor-core stages in the pass schedule
   static constexpr int ST0 = G::R0B ? 1 : 0;
+  // FP16: each tensor-core stage's input is scaled by the exact 1/16 so that
+  // the 16-point sums stay in the FP16 range; the scales are undone at the
+  // end.  The loader skips its scale for complex32 input without an FP32
+  // first stage (the input is FP16 already); the later stages' scales ride on
+  // their twiddles.
+  static constexpr bool LOAD_SCALE = P == TC_FP16 && !(Mem::kHalfIO && G::R0B == 0);
+  static constexpr int SCALED_STAGES = P == TC_FP16 ? G::NTC - 1 + (LOAD_SCALE ? 1 : 0) : 0;
 
-  // Rounds the twiddled input v of a stage to 16 bits (FP16: scaled by the
-  // exact 1/16 of every stage first) and stores it at byte offset `off` of
-  // the A operand; for the split class the rounding error goes to a_lo.
+  // Rounds the stage input v to 16 bits (scaled by 1/16 first when SCALE)
+  // and stores it at byte offset `off` of the A operand; for the split class
+  // the rounding error goes to a_lo.
+  template <bool SCALE>
   GB_HD static void put_a(uint32_t a_hi, uint32_t a_lo, uint32_t off, cf v) {
-    if (P == TC_FP16) v = mk(v.x * 0.0625f, v.y * 0.0625f);
+    if (SCALE) v = mk(v.x * 0.0625f, v.y * 0.0625f);
     const uint32_t h = pack_rn<P>(v.x, v.y);
     Mem::sts32(a_hi + off, h);
     if (SPLIT) Mem::sts32(a_lo + off, pack_rn<P>(v.x - lo16_to_f32<P>(h), v.y - hi16_to_f32<P>(h)));
@@ -254,9 +264,10 @@ struct UmmaBody {
   // are zeros.  Item e = e_t | e_b | e_j: e_t from (lane, warp), e_b from the
   // block of CH items, e_j from the item within the block.  Every index below
   // (element, A row and offset, twiddle) is linear in the bits of e, so it is
-  // the thread's part (once), the block's part (once per CH items) and a
-  // compile-time constant, XORed.
+  // the thread's part of the block (BlockPart) and a compile-time constant,
+  // XORed (or added: element offsets have disjoint bits).
   static constexpr int CH = G::ITEMS_PER_THREAD < 8 ? G::ITEMS_PER_THREAD : 8;
+  static constexpr int KB = G::ITEMS_PER_THREAD / CH;
   GB_HD static int elem_of(int e) {  // first element of first-stage butterfly e
     return G::R0B ? ((e >> (LOGL - G::R0B)) << LOGL) | (e & ((1 << (LOGL - G::R0B)) - 1)) : e;
   }
@@ -272,42 +283,54 @@ struct UmmaBody {
     off = umma_aoff(umma_row_of_u<LOGL>(0, u), i);
   }
 
+  // The parts of block b of CH items of the thread whose item part is et
+  // (umma_load_item(lane, warp)): first item, its first element, A offset
+  // and (r0 > 1) stage-0 input and twiddle index.  They do not depend on the
+  // tile, so a kernel may compute them once and keep them.
+  struct BlockPart {
+    int eb, xb;
+    uint32_t offb;
+    int ib, twb;
+  };
+  GB_HD static BlockPart block_part_of(int et, int b) {
+    BlockPart p{};
+    p.eb = et | umma_load_item<LOGL>(0, b * CH * 8);
+    p.xb = elem_of(p.eb);
+    if (G::R0B == 0) p.offb = off_of(p.eb);
+    else first_of(p.eb, 0, p.offb, p.ib, p.twb);
+    return p;
+  }
+
+  // FULL: every transform of the tile is valid (no per-item check).
+  // parts(b) gives the thread's BlockPart of block b.
+  template <bool FULL, class Parts>
   GB_HD static void load_tile(const PassDesc& d, const cf* gin, int valid, uint32_t a_hi,
-                              uint32_t a_lo, int warp, int lane) {
+                              uint32_t a_lo, const Parts& parts) {
     const bool swap = d.conj_in != 0;
-    const int et = umma_load_item<LOGL>(lane, warp);
 #pragma unroll 1
-    for (int kb = 0; kb < G::ITEMS_PER_THREAD; kb += CH) {
-      const int eb = et | umma_load_item<LOGL>(0, kb * 8);
+    for (int b = 0; b < KB; ++b) {
+      const BlockPart bp = parts(b);
+      const cf* gb = Mem::at(gin, bp.xb);
       if (G::R0B == 0) {
-        const uint32_t offb = off_of(eb);
         cf v[CH];
 GB_UNROLL
         for (int j = 0; j < CH; ++j) {
-          const int e = eb | umma_load_item<LOGL>(0, j * 8);
-          v[j] = tr_of(e) < valid ? Mem::ldg(gin, e) : mk(0.f, 0.f);
+          const int ej = umma_load_item<LOGL>(0, j * 8);
+          v[j] = FULL || tr_of(bp.eb | ej) < valid ? Mem::ldg_sw(gb, ej, swap) : mk(0.f, 0.f);
         }
 GB_UNROLL
-        for (int j = 0; j < CH; ++j) {
-          const cf x = swap ? mk(v[j].y, v[j].x) : v[j];
-          put_a(a_hi, a_lo, offb ^ off_of(umma_load_item<LOGL>(0, j * 8)), x);
-        }
+        for (int j = 0; j < CH; ++j)
+          put_a<LOAD_SCALE>(a_hi, a_lo, bp.offb ^ off_of(umma_load_item<LOGL>(0, j * 8)), v[j]);
       } else {
-        uint32_t offb;
-        int ib, twb;
-        first_of(eb, 0, offb, ib, twb);
-        const int xb = elem_of(eb);
         const cf* tw = d.tw + d.tw_off[1];
 GB_UNROLL
         for (int j = 0; j < CH; ++j) {
           const int ej = umma_load_item<LOGL>(0, j * 8);
-          const bool ok = tr_of(eb | ej) < valid;
+          const bool ok = FULL || tr_of(bp.eb | ej) < valid;
           cf y[G::R0];
 GB_UNROLL
-          for (int q = 0; q < G::R0; ++q) {
-            const cf v = ok ? Mem::ldg(gin, (xb | elem_of(ej)) + q * (G::L / G::R0)) : mk(0.f, 0.f);
-            y[q] = swap ? mk(v.y, v.x) : v;
-          }
+          for (int q = 0; q < G::R0; ++q)
+            y[q] = ok ? Mem::ldg_sw(gb, elem_of(ej) + q * (G::L / G::R0), swap) : mk(0.f, 0.f);
           if (G::R0 == 2) dft_small<2, 1>(y);
           else if (G::R0 == 4) dft_small<4, 1>(y);
           else dft_pq<2, 4>(y);
@@ -317,8 +340,8 @@ GB_UNROLL
           // output o becomes input i of its stage-0 butterfly with k = o and
           // i the same for every o, so its twiddle is s^o with s = w^i: one
           // table load (entry i * r0 + 1), powers by a running product
-          const int i = ib ^ ij;
-          const cf s1 = i > 0 ? Mem::ldtw(tw + ((twb ^ twj) | 1)) : mk(1.f, 0.f);
+          const int i = bp.ib ^ ij;
+          const cf s1 = i > 0 ? Mem::ldtw(tw + ((bp.twb ^ twj) | 1)) : mk(1.f, 0.f);
           cf w = s1;
 GB_UNROLL
           for (int o = 0; o < G::R0; ++o) {
@@ -330,7 +353,7 @@ GB_UNROLL
               v = cmul(v, w);
               w = cmul(w, s1);
             }
-            put_a(a_hi, a_lo, offb ^ offj ^ offo, v);
+            put_a<LOAD_SCALE>(a_hi, a_lo, bp.offb ^ offj ^ offo, v);
           }
         }
       }
@@ -338,9 +361,10 @@ GB_UNROLL
   }
 
   // The thread's part of the addressing of the butterfly in A row m of
-  // tensor-core stage t: after the last stage its transform (tr) and the
-  // position bits of its outputs that do not depend on the output index;
-  // before, the next stage's A offset and twiddle index of its output 0.
+  // tensor-core stage t (it does not depend on the tile): after the last
+  // stage its output position (tr * L + the position bits that do not
+  // depend on the output index); before, the next stage's A offset and
+  // twiddles of its output 0.
   struct RowPart {
     int tr, pos;
     uint32_t off;
@@ -354,14 +378,15 @@ GB_UNROLL
   // (the stage's outputs keep their block: (jb / Ns) * 16 Ns lies in one
   // multiple of L/16), so its twiddle w_{16 Ns'}^{i' k'} = c * s^o with
   // c = w^{i' k} and s = w^{i' Ns} = (c s) * conj(c): two table loads per
-  // row, then a running product (at most 16 further roundings, ~1e-6).
+  // row, then a running product (at most 16 further roundings, ~1e-6).  For
+  // FP16, c carries the next stage's exact 1/16.
   template <int t>
   GB_HD static RowPart row_part(const PassDesc& d, int m) {
     RowPart rp{};
     const int u = umma_u_of_row<LOGL>(t, m);
     if (t == G::NTC - 1) {
       rp.tr = u >> G::BPSB;
-      rp.pos = umma_out_pos(G::ns_log(t), u & ((1 << G::BPSB) - 1), 0);
+      rp.pos = (rp.tr << LOGL) | umma_out_pos(G::ns_log(t), u & ((1 << G::BPSB) - 1), 0);
     } else {
       int u2, i2;
       umma_next<LOGL>(t, u, 0, u2, i2, rp.tw);
@@ -372,7 +397,7 @@ GB_UNROLL
       const cf c0 = Mem::ldtw(tw + rp.tw);
       const cf c1 = Mem::ldtw(tw + (rp.tw ^ two));
       rp.step = cmul(c1, cconj(c0));
-      rp.run = c0;
+      rp.run = P == TC_FP16 ? mk(c0.x * 0.0625f, c0.y * 0.0625f) : c0;
     }
     return rp;
   }
@@ -381,23 +406,24 @@ GB_UNROLL
   // values, so a thread can read its tensor-memory row in parts): stored to
   // global memory after the last stage, else twiddled, rounded and stored as
   // the next stage's A operand.  Each output's own part of the addressing is
-  // a compile-time constant XORed into the row's part.
+  // a compile-time constant XORed (or added) to the row's part.
   template <int t, int O0 = 0, int NO = 16>
   GB_HD static void epilogue_part(const PassDesc& d, cf* gout, int valid, RowPart& rp,
                                   const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
     if (t == G::NTC - 1) {
       if (rp.tr >= valid) return;
-      cf* o_base = gout + (int64_t)rp.tr * G::L;
+      // the row's first output in the tile; output o is o << ns_log(t) further
+      cf* o_base = Mem::at(gout, rp.pos);
       const bool swap = d.conj_out != 0;
 GB_UNROLL
       for (int j = 0; j < NO; ++j) {
         const int o = O0 + j;
         cf v = mk(u32_as_f32(r[2 * j]), u32_as_f32(r[2 * j + 1]));
-        if (P == TC_FP16) {  // undo the 1/16 of every stage: exact powers of two
-          const float sc = (float)(1 << (4 * G::NTC));
+        if (SCALED_STAGES > 0) {  // undo the FP16 stages' 1/16: exact powers of two
+          const float sc = (float)(1 << (4 * SCALED_STAGES));
           v = mk(v.x * sc, v.y * sc);
         }
-        Mem::stg(o_base, rp.pos | (o << G::ns_log(t)), swap ? mk(v.y, v.x) : v);
+        Mem::stg_sw(o_base, o << G::ns_log(t), v, swap);
       }
     } else {
 GB_UNROLL
@@ -409,7 +435,7 @@ GB_UNROLL
         cf v = mk(u32_as_f32(r[2 * j]), u32_as_f32(r[2 * j + 1]));
         v = cmul(v, rp.run);               // c * s^o
         rp.run = cmul(rp.run, rp.step);
-        put_a(a_hi, a_lo, off, v);
+        put_a<false>(a_hi, a_lo, off, v);
       }
     }
   }

@@ -33,6 +33,7 @@ FFT_PREC_FP32 = 0
 FFT_PREC_TC_FP16 = 1
 FFT_PREC_TC_BF16 = 2
 FFT_PREC_TC_BF16X3 = 3
+FFT_PREC_TC_FP16_C32 = 4  # FP16 tensor-core class with complex32 (FP16 pair) input and output
 
 
 class GbfftError(RuntimeError):
@@ -353,6 +354,7 @@ class Plan:
         self.shape = _shape(n)
         self.batch = int(batch)
         self.direction = direction
+        self.precision = precision
         self.handle: Optional[int] = fft_plan_create(self.shape, self.batch, direction, precision,
                                                      **options)
 
@@ -365,8 +367,9 @@ class Plan:
 
     def _check_tensor(self, t, name):
         import torch
-        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64:
-            raise TypeError(f"{name} must be a CUDA complex64 tensor")
+        want = torch.complex32 if self.precision == FFT_PREC_TC_FP16_C32 else torch.complex64
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != want:
+            raise TypeError(f"{name} must be a CUDA {str(want).split('.')[-1]} tensor")
         if not t.is_contiguous() or t.numel() != self.elements:
             raise ValueError(f"{name} must be contiguous with {self.elements} elements")
 

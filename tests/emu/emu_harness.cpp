@@ -565,6 +565,14 @@ struct UmmaReplay {
 UmmaReplay g_umma;
 
 struct UmmaCheckMem : CheckMem {
+  static constexpr bool kHalfIO = false;
+  static const cf* at(const cf* p, int64_t e) { return p + e; }
+  static cf* at(cf* p, int64_t e) { return p + e; }
+  static cf ldg_sw(const cf* p, int64_t off, bool swap) {
+    const cf v = ldg(p, off);
+    return swap ? mk(v.y, v.x) : v;
+  }
+  static void stg_sw(cf* p, int64_t off, cf v, bool swap) { stg(p, off, swap ? mk(v.y, v.x) : v); }
   static void sts32(uint32_t addr, uint32_t v) {
     if (addr % 4 || addr + 4 > g_umma.bytes.size()) { err("A-operand store out of bounds", addr); return; }
     if (g_umma.word_phase[addr / 4] == g_umma.phase) err("two writes to one A word in one phase", addr);
@@ -614,7 +622,12 @@ void run_umma_t(const PassDesc& d, const cf* in, cf* out) {
     cf* gout = out + first * G::L;
     ++g_umma.phase;
     for (int warp = 0; warp < 8; ++warp)
-      for (int lane = 0; lane < 32; ++lane) Body::load_tile(d, gin, valid, a_hi, a_lo, warp, lane);
+      for (int lane = 0; lane < 32; ++lane) {
+        const int et = umma_load_item<LOGL>(lane, warp);
+        auto parts = [&](int b) { return Body::block_part_of(et, b); };
+        if (valid == G::TPT) Body::template load_tile<true>(d, gin, valid, a_hi, a_lo, parts);
+        else Body::template load_tile<false>(d, gin, valid, a_hi, a_lo, parts);
+      }
     check_written("A-operand word not written by the loader");
     auto stage = [&](auto t_) {
       constexpr int t = decltype(t_)::value;

@@ -73,6 +73,17 @@ def test_dry_run_rejects_options():
         assert p["tc_prec"] == 3 and 1 << sum(r.bit_length() - 1 for r in p["radices"]) == 2 ** logn
         first = [2 ** (logn % 4)] if logn % 4 else []   # FP32 first stage, then radix 16
         assert p["radices"] == first + [16] * (logn // 4) and p["smem"] <= 232448
+    # complex32 storage: the tcgen05 FP16 kernel at the same lengths, nothing else
+    for logn in range(4, 15):
+        (p,) = g.fft_plan_dry_run(2 ** logn, 5, precision=g.FFT_PREC_TC_FP16_C32)["passes"]
+        assert p["tc_prec"] == g.FFT_PREC_TC_FP16 and p["io16"] == 1
+    for n, variant in ((2 ** 15, 0), (8, 0), (4096, 1)):
+        with pytest.raises(g.GbfftError) as e:
+            g.fft_plan_dry_run(n, 1, precision=g.FFT_PREC_TC_FP16_C32, variant=variant)
+        assert e.value.status == g.FFT_ERR_NOT_IMPLEMENTED
+    with pytest.raises(g.GbfftError) as e:
+        g.fft_plan_dry_run(1024, 1, precision=g.FFT_PREC_TC_FP16_C32 + 1)
+    assert e.value.status == g.FFT_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("logn", range(0, 25))
