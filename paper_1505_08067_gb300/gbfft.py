@@ -438,6 +438,7 @@ class ConvPlan(Plan):
         self.shape = _shape(n)
         self.batch = int(batch)
         self.direction = FFT_FORWARD
+        self.precision = FFT_PREC_FP32
         self.handle = None
         self.filters = []
         spec = []
