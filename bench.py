@@ -713,7 +713,9 @@ def section_small(args) -> dict:
     launch replayed from a CUDA graph) and fft_execute_noalloc: measured from
     C by the library's call_latency program (host enqueue time, device time
     back to back, and the median round trip of single synchronised calls,
-    beside an empty kernel's), and through this Python binding."""
+    beside an empty kernel's; and the persistent work queue's round trip of a
+    submit and a wait, and its time per job back to back), and through this
+    Python binding."""
     import torch
 
     from paper_1505_08067_gb300 import build as gbuild

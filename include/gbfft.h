@@ -416,6 +416,57 @@ GBFFT_API fft_status_t fft_server_stats(fft_server_t server, fft_server_stats_t*
 /* Stop the worker, wait for running work, free plans and workspaces. */
 GBFFT_API fft_status_t fft_server_destroy(fft_server_t server);
 
+/* ------------------------------------------------ persistent work queue --
+ * A persistent batch kernel fed by a device-visible job queue (Sec. 3.4: the
+ * top-level batch handed to every compute unit, here without one kernel
+ * launch per job).  One queue serves one transform shape: batched 1D FP32
+ * transforms of length n (a power of two, 2 .. 2^12), up to max_batch per
+ * job, in one direction.  Jobs are descriptors (in, out, batch) written by
+ * the host into a ring of `slots` entries in mapped pinned host memory; a
+ * worker kernel launched cooperatively (all of its blocks resident at once)
+ * on the queue's own stream polls the ring, and for each job every block
+ * computes its share of the tiles; the last block to finish publishes the
+ * job's completion in the ring.  Jobs complete in ticket order.
+ *
+ * The worker runs while jobs keep arriving: when no job arrives for about
+ * 2^16 polls (tens of milliseconds) or fft_queue_destroy asks it to stop, it
+ * exits, and the next submit or wait launches it again.  Every wait in the
+ * worker is bounded.  While it runs it holds its blocks' SMs (the `blocks`
+ * of fft_queue_create: 0 = one per tile of a max_batch job, at most what the
+ * GPU holds at once) and a device-wide synchronisation waits for it to go
+ * idle.  The queue allocates at creation only; submit and wait allocate
+ * nothing.  Calls on one queue are serialised internally.
+ */
+typedef struct fft_queue_s* fft_queue_t;
+
+/* Create a queue on the current device.  slots: ring entries (1 .. 4096;
+ * 0 = 64).  blocks: worker blocks (0 = automatic).  n outside 2 .. 2^12 (or
+ * not a power of two): FFT_ERR_NOT_IMPLEMENTED / FFT_ERR_UNSUPPORTED_SIZE. */
+GBFFT_API fft_status_t fft_queue_create(fft_queue_t* queue, int64_t n, int64_t max_batch,
+                                        int direction, int slots, int blocks);
+/* Append a job: `batch` (1 .. max_batch) transforms from `in` to `out`
+ * (device pointers, 8-byte aligned, complex64; in == out allowed).  The
+ * worker runs on the queue's own stream and is not ordered after any other
+ * stream: `in` must hold its data when submit is called (the stream that
+ * wrote it synchronised).  The buffers must stay valid and `in` unchanged
+ * until the job completes.
+ * Returns its ticket (1, 2, 3, ...).  When the ring is full, waits (up to
+ * about one second) for the oldest job's slot; FFT_ERR_TIMEOUT if it stays
+ * busy. */
+GBFFT_API fft_status_t fft_queue_submit(fft_queue_t queue, const void* in, void* out,
+                                        int64_t batch, uint64_t* ticket);
+/* Wait until job `ticket` has completed (timeout_s < 0: no limit): FFT_OK,
+ * FFT_ERR_TIMEOUT (still pending), FFT_ERR_INVALID_ARG (ticket never
+ * issued), or FFT_ERR_CUDA (the worker failed).  Once it returns FFT_OK the
+ * job's output is complete in device memory. */
+GBFFT_API fft_status_t fft_queue_wait(fft_queue_t queue, uint64_t ticket, double timeout_s);
+/* Counters: worker launches so far and jobs completed. */
+GBFFT_API fft_status_t fft_queue_info(fft_queue_t queue, int64_t* worker_launches,
+                                      uint64_t* completed);
+/* Stop the worker once the jobs already submitted are done, then free the
+ * queue. */
+GBFFT_API fft_status_t fft_queue_destroy(fft_queue_t queue);
+
 /* ---------------------------------------------------- synthetic inputs --
  * Seeded test signals generated on the device (the paper's workloads are
  * synthetic radar data; this fills the uniform-noise inputs of the benchmarks

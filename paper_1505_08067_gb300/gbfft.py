@@ -119,6 +119,11 @@ _SIGS = {
     "fft_server_pause": [_vp, ctypes.c_int],
     "fft_server_stats": [_vp, ctypes.POINTER(fft_server_stats_t)],
     "fft_server_destroy": [_vp],
+    "fft_queue_create": [ctypes.POINTER(_vp), _i64, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "fft_queue_submit": [_vp, _vp, _vp, _i64, ctypes.POINTER(ctypes.c_uint64)],
+    "fft_queue_wait": [_vp, ctypes.c_uint64, ctypes.c_double],
+    "fft_queue_info": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_uint64)],
+    "fft_queue_destroy": [_vp],
     "fft_schedule_count": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                            ctypes.POINTER(ctypes.c_uint64)],
     "fft_schedule_shortest_path": [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -211,6 +216,62 @@ def fft_execute_noalloc(n: int, batch: int, direction: int, in_ptr: int, out_ptr
                         stream: int = 0) -> None:
     """Plan-free transform that allocates no device memory (see include/gbfft.h)."""
     _check(load().fft_execute_noalloc(int(n), int(batch), direction, in_ptr, out_ptr, stream))
+
+
+class Queue:
+    """Persistent work queue for batched 1D FP32 transforms of one length (see
+    fft_queue_* in include/gbfft.h): submit(x, out, batch) returns a ticket,
+    wait(ticket) blocks until that job's output is complete."""
+
+    def __init__(self, n: int, max_batch: int, direction: int = FFT_FORWARD, slots: int = 0,
+                 blocks: int = 0):
+        self.n, self.max_batch = int(n), int(max_batch)
+        h = _vp()
+        _check(load().fft_queue_create(ctypes.byref(h), self.n, self.max_batch, direction,
+                                       int(slots), int(blocks)))
+        self.handle: Optional[int] = h.value
+
+    def submit_ptr(self, in_ptr: int, out_ptr: int, batch: int) -> int:
+        t = ctypes.c_uint64()
+        _check(load().fft_queue_submit(self.handle, in_ptr, out_ptr, int(batch), ctypes.byref(t)))
+        return t.value
+
+    def submit(self, x, out, batch: Optional[int] = None) -> int:
+        """Queue the transform of CUDA complex64 tensor x into out (batch
+        defaults to x.numel() // n); both must stay alive until the job ends."""
+        import torch
+        for t, name in ((x, "input"), (out, "output")):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64:
+                raise TypeError(f"{name} must be a CUDA complex64 tensor")
+        b = x.numel() // self.n if batch is None else int(batch)
+        if b * self.n > min(x.numel(), out.numel()):
+            raise ValueError("batch x n exceeds the tensors")
+        return self.submit_ptr(x.data_ptr(), out.data_ptr(), b)
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> None:
+        _check(load().fft_queue_wait(self.handle, int(ticket), float(timeout_s)))
+
+    def info(self) -> dict:
+        launches, completed = _i64(), ctypes.c_uint64()
+        _check(load().fft_queue_info(self.handle, ctypes.byref(launches), ctypes.byref(completed)))
+        return {"worker_launches": launches.value, "completed": completed.value}
+
+    def close(self) -> None:
+        if self.handle:
+            _check(load().fft_queue_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fft_fill_uniform(out_ptr: int, count: int, seed: int, first: int = 0, stream: int = 0) -> None:

@@ -11,6 +11,10 @@
 //                    (back to back: launch gaps included)
 //   round_trip_us    median of single calls each followed by a stream
 //                    synchronize (enqueue + execution + completion seen)
+// and for the persistent work queue (fft_queue_*, same shape):
+//   round_trip_us    median of single jobs, submit then wait
+//   per_job_us       jobs submitted back to back, time per job until the
+//                    last one is seen complete
 // Exit status 0 on success, 1 on any library or CUDA error.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -111,6 +115,35 @@ int main(int argc, char** argv) {
   CK(cudaGetLastError());
   ok(fft_plan_sync_status(plan, st), "fft_plan_sync_status");
 
+  // persistent work queue: the worker stays resident while jobs keep coming
+  double q_rt = -1, q_per = -1;
+  int64_t q_launches = 0;
+  if (n >= 2 && n <= 4096) {
+    fft_queue_t q = nullptr;
+    ok(fft_queue_create(&q, n, batch, FFT_FORWARD, 64, 0), "fft_queue_create");
+    uint64_t t = 0;
+    for (int i = 0; i < 50; ++i) {
+      ok(fft_queue_submit(q, in, out, batch, &t), "fft_queue_submit");
+      ok(fft_queue_wait(q, t, 10.0), "fft_queue_wait");
+    }
+    std::vector<double> rt;
+    for (int i = 0; i < 300; ++i) {
+      const double t0 = now_us();
+      ok(fft_queue_submit(q, in, out, batch, &t), "fft_queue_submit");
+      ok(fft_queue_wait(q, t, 10.0), "fft_queue_wait");
+      rt.push_back(now_us() - t0);
+    }
+    std::sort(rt.begin(), rt.end());
+    q_rt = rt[rt.size() / 2];
+    const double t0 = now_us();
+    for (int i = 0; i < reps; ++i) ok(fft_queue_submit(q, in, out, batch, &t), "fft_queue_submit");
+    ok(fft_queue_wait(q, t, 30.0), "fft_queue_wait");
+    q_per = (now_us() - t0) / reps;
+    uint64_t done = 0;
+    ok(fft_queue_info(q, &q_launches, &done), "fft_queue_info");
+    ok(fft_queue_destroy(q), "fft_queue_destroy");
+  }
+
   auto js = [](const char* name, const Result& r, bool comma) {
     printf("\"%s\":{\"host_us\":%.3f,\"device_us\":%.3f,\"round_trip_us\":%.3f}%s", name, r.host_us,
            r.device_us, r.round_trip_us, comma ? "," : "");
@@ -122,7 +155,8 @@ int main(int argc, char** argv) {
   js("fft_execute_noalloc", na, true);
   js("empty_kernel_1x32", e1, true);
   js("empty_kernel_64x256", e64, false);
-  printf("}}\n");
+  printf("},\"fft_queue\":{\"round_trip_us\":%.3f,\"per_job_us\":%.3f,\"worker_launches\":%lld}}\n",
+         q_rt, q_per, (long long)q_launches);
   fft_plan_destroy(plan);
   CK(cudaStreamDestroy(st));
   CK(cudaFree(in));

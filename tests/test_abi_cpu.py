@@ -39,6 +39,12 @@ def test_no_gpu_means_error_not_fallback():
     with pytest.raises(g.GbfftError) as e:
         g.fft_plan_create(1024, 4)
     assert e.value.status == g.FFT_ERR_CUDA
+    # the work queue: shape errors first, then no device
+    for n, st in ((8192, g.FFT_ERR_NOT_IMPLEMENTED), (1000, g.FFT_ERR_UNSUPPORTED_SIZE),
+                  (1024, g.FFT_ERR_CUDA)):
+        with pytest.raises(g.GbfftError) as e:
+            g.Queue(n, 64)
+        assert e.value.status == st
 
 
 @pytest.mark.parametrize("n,batch,status", [
