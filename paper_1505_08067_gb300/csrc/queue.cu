@@ -34,6 +34,7 @@
 #include "kernels.h"
 #include "kernels_impl.cuh"
 #include "planner.h"
+#include "queue_ring.h"
 
 namespace gbfft {
 fft_status_t set_error(fft_status_t st, const char* msg);
@@ -254,16 +255,10 @@ fft_status_t cuda_err(cudaError_t e, const char* what) {
   return set_error(FFT_ERR_CUDA, b);
 }
 
-// Jobs complete in ticket order and a slot's done word only grows, so ticket
-// t is complete once its slot shows t or a later ticket (the slot may already
-// have been reused and completed again).
 void update_completed(fft_queue_t q) {
-  while (q->completed < q->issued) {
-    const uint64_t t = q->completed + 1;
-    QSlot* s = q->ring + (t - 1) % (uint64_t)q->slots;
-    if (done_of(s)->load(std::memory_order_acquire) < t) break;
-    q->completed = t;
-  }
+  q->completed = ring_completed(q->completed, q->issued, q->slots, [q](int slot) {
+    return done_of(q->ring + slot)->load(std::memory_order_acquire);
+  });
 }
 
 // Launches the worker when it is not running and jobs are pending.
@@ -416,10 +411,11 @@ fft_status_t fft_queue_submit(fft_queue_t q, const void* in, void* out, int64_t 
   std::lock_guard<std::mutex> lock(q->mu);
   const uint64_t t = q->issued + 1;
   QSlot* s = q->ring + (t - 1) % (uint64_t)q->slots;
-  if (t > (uint64_t)q->slots) {
+  {
     // the slot's previous job must be done before it is rewritten
     const double limit = now_s() + 1.0;
-    for (uint32_t it = 0; done_of(s)->load(std::memory_order_acquire) < t - q->slots; ++it) {
+    for (uint32_t it = 0; !ring_slot_free(t, q->slots, done_of(s)->load(std::memory_order_acquire));
+         ++it) {
       if ((it & 63) == 0) {
         fft_status_t st = ensure_worker(q);
         if (st != FFT_OK) return st;

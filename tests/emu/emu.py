@@ -13,7 +13,7 @@ CSRC = os.path.join(ROOT, "paper_1505_08067_gb300", "csrc")
 LIB = os.path.join(HERE, "_emu.so")
 SRCS = [os.path.join(HERE, "emu_harness.cpp"), os.path.join(CSRC, "planner.cpp")]
 DEPS = SRCS + [os.path.join(CSRC, f) for f in ("fft_core.h", "fft_stage.h", "fft_split.h", "planner.h", "kernel_shapes.h",
-                                    "tc_stage.h", "umma_stage.h", "tc_stage.h")] + \
+                                    "tc_stage.h", "umma_stage.h", "tc_stage.h", "queue_ring.h")] + \
     [os.path.join(ROOT, "include", "gbfft.h")]
 _lib = None
 
@@ -50,8 +50,19 @@ def load():
                                  ctypes.POINTER(Options), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p,
                                  ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]
+    lib.emu_ring_replay.restype = ctypes.c_int
+    lib.emu_ring_replay.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_char_p, ctypes.c_size_t]
     _lib = lib
     return lib
+
+
+def ring_replay(seed: int, slots: int, jobs: int, exact: bool = False) -> str:
+    """Replay the work queue's ring bookkeeping against a model; '' if every
+    check held, else the first failure."""
+    buf = ctypes.create_string_buffer(256)
+    r = load().emu_ring_replay(seed, slots, jobs, 1 if exact else 0, buf, 256)
+    return "" if r == 0 else buf.value.decode()
 
 
 def run(x: np.ndarray, shape, direction=-1, smem_optin=232448, specialised=True, stats=None,

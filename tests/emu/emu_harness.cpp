@@ -18,6 +18,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,7 @@
 #include "planner.h"
 #include "tc_stage.h"
 #include "umma_stage.h"
+#include "queue_ring.h"
 
 using namespace gbfft;
 
@@ -811,6 +813,73 @@ int64_t emu_conv_run(const int64_t* n, int dims, int64_t batch, const int64_t* l
   }
   return replay(n, dims, batch, -1, 0, opt, smem_optin, specialised, in_f, out_f, msg, msg_len,
                 special_passes, &cs, filters, filter_len);
+}
+
+// The work queue's host bookkeeping (queue_ring.h) against a model of the
+// ring: a worker completing tickets in order at random moments, a host
+// submitting (only into free slots) and scanning for completions at random
+// moments, sometimes after a slot has been reused and completed again.
+// Checks that a scan never reports an incomplete ticket, always reports every
+// complete one, and that a slot is only rewritten after its previous ticket
+// is complete.  exact = 1 scans with an equality test on the done word
+// instead (the form that loses completions once a slot is reused), so a
+// caller can check that the replay catches it.  Returns 0, or 1 with a message.
+int emu_ring_replay(uint64_t seed, int slots, int jobs, int exact, char* msg, size_t msg_len) {
+  std::vector<uint64_t> done(slots, 0);
+  uint64_t issued = 0, worker_next = 1, completed = 0, x = seed * 2654435761u + 1;
+  auto rnd = [&](int m) {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    return (int)(x % (uint64_t)m);
+  };
+  auto done_at = [&](int s) { return done[s]; };
+  auto scan = [&]() {
+    if (!exact) return ring_completed(completed, issued, slots, done_at);
+    uint64_t c = completed;
+    while (c < issued && done[(c) % slots] == c + 1) ++c;
+    return c;
+  };
+  for (long step = 0; worker_next <= (uint64_t)jobs || completed < (uint64_t)jobs; ++step) {
+    if (step > 100L * jobs + 1000) {
+      snprintf(msg, msg_len, "no progress: issued %llu, worker at %llu, host saw %llu",
+               (unsigned long long)issued, (unsigned long long)worker_next - 1,
+               (unsigned long long)completed);
+      return 1;
+    }
+    const int a = rnd(16);
+    if (a < 6 && issued < (uint64_t)jobs) {  // host submits if the slot is free
+      const uint64_t t = issued + 1;
+      const int s = (int)((t - 1) % slots);
+      if (ring_slot_free(t, slots, done[s])) {
+        if (t > (uint64_t)slots && worker_next <= t - slots) {
+          snprintf(msg, msg_len, "slot %d rewritten before ticket %llu completed", s,
+                   (unsigned long long)(t - slots));
+          return 1;
+        }
+        issued = t;
+      }
+    } else if (a < 13) {  // the worker completes the next ticket, if issued
+      if (worker_next <= issued) {
+        done[(worker_next - 1) % slots] = worker_next;
+        ++worker_next;
+      }
+    } else {  // the host looks (rarely: slots get reused in between)
+      const uint64_t c = scan();
+      if (c > worker_next - 1) {
+        snprintf(msg, msg_len, "ticket %llu reported complete, worker at %llu",
+                 (unsigned long long)c, (unsigned long long)worker_next - 1);
+        return 1;
+      }
+      if (c != std::min<uint64_t>(issued, worker_next - 1)) {
+        snprintf(msg, msg_len, "scan stopped at %llu, %llu complete", (unsigned long long)c,
+                 (unsigned long long)std::min<uint64_t>(issued, worker_next - 1));
+        return 1;
+      }
+      completed = c;
+    }
+  }
+  return 0;
 }
 
 }  // extern "C"
