@@ -258,6 +258,10 @@ def _free_device_memory():
 
 
 SECTION_DESC = {
+    "tc6": ("tensor-core classes above 2^14 (six-step plans: transposes and tcgen05 row "
+            "passes) beside the FP32 four-step path: N=2^20 batch 64, N=2^22 batch 16, "
+            "N=2^24 batch 4 (2^26 elements each), forward and inverse; FP16, BF16, split "
+            "BF16x3 and FP16 with complex32 storage"),
     "multipass": ("large multi-pass 1D complex64 FFTs: N=2^20 batch 64, N=2^22 batch 16, "
                   "N=2^24 batch 4 (2^26 elements each), forward and inverse, FP32"),
     "sar": ("2D SAR frame 4096 azimuth x 8192 range complex64 (LFM chirp echoes BT=500, "
@@ -300,7 +304,7 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
     if kind == "tc":
         items = [((4096,), 2 ** (TOTAL_LOG - 12)), ((8192,), 2 ** (TOTAL_LOG - 13)),
                  ((16384,), 2 ** (TOTAL_LOG - 14))]
-    elif kind == "multipass":
+    elif kind in ("multipass", "tc6"):
         items = [((2 ** 20,), 64), ((2 ** 22,), 16), ((2 ** 24,), 4)]
     else:
         items = [((4096, 8192), 1)]
@@ -327,12 +331,13 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
     y = torch.empty_like(x)
     # complex32 copies of the input and an output for the FP16 class with
     # complex32 storage (made before the timed region)
-    x16 = _to_c32(x) if kind == "tc" else None
-    y16 = torch.empty_like(x16) if kind == "tc" else None
+    tc_kinds = ("tc", "tc6")
+    x16 = _to_c32(x) if kind in tc_kinds else None
+    y16 = torch.empty_like(x16) if kind in tc_kinds else None
     plans, order = {}, []
     # (precision, variant): FP32, the tcgen05 classes, and at N = 4096 the
     # warp-level MMA classes beside them
-    precs = [(0, 0), (1, 0), (2, 0), (3, 0), (PREC_C32, 0)] if kind == "tc" else [(0, 0)]
+    precs = [(0, 0), (1, 0), (2, 0), (3, 0), (PREC_C32, 0)] if kind in tc_kinds else [(0, 0)]
     t_plan = time.perf_counter()
     for shape, batch in items:
         extra = [(1, 1), (2, 1), (3, 1)] if kind == "tc" and shape == (4096,) else []
@@ -391,12 +396,16 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         t = statistics.median(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
         passes = len(plans[key].describe()["passes"])
         pname = PREC_NAMES[key[2]] + ("_warp_mma" if key[3] == 1 else "")
-        gbs = 2.0 * esz(key) * passes * e / (t * 1e-3) / 1e9
+        # bytes of the algorithm (one read and one write per pass of an FP32
+        # two-pass plan: 2 passes above 2^14), not of the six-step transposes
+        alg_passes = min(passes, 2)
+        gbs = 2.0 * esz(key) * alg_passes * e / (t * 1e-3) / 1e9
         per[f"{'x'.join(map(str, key[0]))} {'fwd' if key[1] < 0 else 'inv'} {pname}"] = {
             "ms": round(t, 4), "gflops": round(5.0 * e * lg / (t * 1e-3) / 1e9, 1),
             "passes": passes, "gbs": round(gbs, 1), "frac": round(gbs / peaks["hbm_gbs"], 4),
             "tuned": _tuned(plans[key])}
-    tot_bytes = sum(2.0 * esz(k) * len(plans[k].describe()["passes"]) * e for k, e, _ in order)
+    tot_bytes = sum(2.0 * esz(k) * min(len(plans[k].describe()["passes"]), 2) * e
+                    for k, e, _ in order)
     launches = sum(plans[k].launch_count for k, _e, _l in order) * args.steps
     out = {
         "workload": SECTION_DESC[kind], "data": data, "steps": args.steps, "warmup": args.warmup,
@@ -408,6 +417,17 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
         "per_item": per, "clocks": clocks, "gpu_launches": launches,
         "plan_create_s": round(t_plan, 2),
         "l2": "inputs of 256 MiB to 1 GiB per launch, larger than L2; no flush"}
+    if kind == "tc6":
+        out["roofline"]["alg_bytes"] = ("16 B per element per pass of the two-pass algorithm (8 B "
+                                        "for complex32), the six-step plans' five passes counted "
+                                        "as two")
+        out["accuracy_vs_fp32"] = _six_step_accuracy(gbfft, x)
+        out["vs_fp32"] = {
+            "x".join(map(str, shape)): {
+                p: {d: round(per[f"{shape[0]} {d} fp32"]["ms"] / per[f"{shape[0]} {d} {p}"]["ms"], 3)
+                    for d in ("fwd", "inv")}
+                for p in ("tc_fp16", "tc_bf16", "tc_bf16x3", "tc_fp16_c32")}
+            for shape, _b in items}
     if kind == "tc":
         acc = _tc_accuracy(gbfft, x, tone_bins)
         for name, rec in acc.items():
@@ -432,6 +452,38 @@ def section_items(kind: str, args, x_reuse=None) -> dict:
 
 
 PREC_NAMES = ["fp32", "tc_fp16", "tc_bf16", "tc_bf16x3", "tc_fp16_c32"]
+
+
+SIX_STEP_BOUNDS = {"tc_fp16": lambda n: 2e-3, "tc_bf16": lambda n: 7e-3,
+                   "tc_bf16x3": lambda n: 5e-6 * math.log2(n), "tc_fp16_c32": lambda n: 2e-3}
+
+
+def _six_step_accuracy(gbfft, x) -> dict:
+    """Relative L2 error of each tensor-core class's six-step plan against this
+    library's FP32 four-step path (1e-7 level against the FP64 oracle in the
+    parity tests) on the first transform of the input, at 2^20 and 2^24.  The
+    complex32 form reads the input rounded to FP16 pairs, so its error includes
+    that rounding."""
+    import numpy as np
+    import torch
+
+    acc = {}
+    for logn in (20, 24):
+        n = 2 ** logn
+        xs = x[:n]
+        with gbfft.Plan(n, 1, -1) as p:
+            ref = p.execute(xs).cpu().numpy().astype(np.complex128)
+        for prec, name in ((1, "tc_fp16"), (2, "tc_bf16"), (3, "tc_bf16x3"), (PREC_C32, "tc_fp16_c32")):
+            with gbfft.Plan(n, 1, -1, prec) as p:
+                if prec == PREC_C32:
+                    y = _c32_to_numpy(p.execute(_to_c32(xs)))
+                else:
+                    y = p.execute(xs).cpu().numpy().astype(np.complex128)
+                torch.cuda.synchronize()
+            e = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+            bound = SIX_STEP_BOUNDS[name](n)
+            acc[f"{n} {name}"] = {"rel_l2": e, "bound": bound, "within_bound": e <= bound}
+    return acc
 
 
 def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: float = 1e-3):
@@ -468,8 +520,8 @@ def _tc_accuracy(gbfft, x, bins, count: int = 64, n: int = 4096, amplitude: floa
 def section_serve(args, jobs: int, load: float) -> dict:
     """Serving (cfg5): a Poisson stream of FFT jobs, sizes log-uniform over
     N = 2^8..2^22, batch 1..256, forward / inverse 50/50, 80% FP32 and 20%
-    tensor-core class (those take N = 2^8..2^14, the lengths the class
-    covers), admitted under a 64 GB budget.  Offered load: algorithmic bytes
+    tensor-core class (log-uniform over 2^8 .. 2^serve_tc_max_log: single-pass
+    up to 2^14, six-step above), admitted under a 64 GB budget.  Offered load: algorithmic bytes
     per second = `load` x measured HBM bandwidth.  Inputs are slices of one
     seeded device buffer; outputs rotate through a ring that is reused only
     after the job holding it completes.  Reports p50/p99 latency and aggregate
@@ -488,8 +540,8 @@ def section_serve(args, jobs: int, load: float) -> dict:
     batch = rng.integers(1, 257, njobs)
     dirs = np.where(rng.random(njobs) < 0.5, -1, 1)
     prec = np.where(rng.random(njobs) < 0.2, rng.integers(1, 4, njobs), 0)
-    # tensor-core jobs: log-uniform over the lengths the class covers (2^8..2^14)
-    logn = np.where(prec > 0, rng.integers(8, 15, njobs), logn)
+    # tensor-core jobs: log-uniform over 2^8 .. 2^serve_tc_max_log
+    logn = np.where(prec > 0, rng.integers(8, args.serve_tc_max_log + 1, njobs), logn)
     elems = (2 ** logn) * batch
     passes = np.where(logn > 14, 2, 1)
     alg_bytes = 16.0 * passes * elems
@@ -587,8 +639,10 @@ def section_serve(args, jobs: int, load: float) -> dict:
     del xin, yout
     return {
         "workload": "serving: Poisson stream of FFT jobs, N = 2^8..2^22 (tensor-core jobs "
-                    "N = 2^8..2^14), batch 1..256, 50/50 forward/inverse, 80% FP32 / 20% "
-                    "tensor-core class, 64 GB budget",
+                    f"N = 2^8..2^{args.serve_tc_max_log}), batch 1..256, 50/50 forward/inverse, "
+                    "80% FP32 / 20% tensor-core class, 64 GB budget",
+        "alg_bytes": "16 B per element per pass, two passes above 2^14 (the six-step "
+                     "tensor-core plans move more: five passes)",
         "jobs": njobs, "offered_load_frac_of_hbm": load, "offered_jobs_per_s": rate,
         "streams": args.streams, "large_group_log2": args.large_group_log2,
         "admission": "strict arrival order" if args.strict_order else "backfilling",
@@ -912,8 +966,15 @@ def ours(args, rank: int, world: int) -> None:
                     rec = section_items("sar", args)
                 elif name == "tc":
                     rec = section_items("tc", args)
+                elif name == "tc6":
+                    rec = section_items("tc6", args)
                 elif name == "serve":
                     rec = section_serve(args, args.serve_jobs, args.load)
+                elif name == "serve_tc14":
+                    # the same stream with tensor-core jobs up to 2^14 only (single-pass)
+                    a14 = argparse.Namespace(**vars(args))
+                    a14.serve_tc_max_log = 14
+                    rec = section_serve(a14, args.serve_jobs, args.load)
                 elif name == "sar_compress":
                     rec = section_compress(args)
                 else:
@@ -956,9 +1017,9 @@ def ours(args, rank: int, world: int) -> None:
 
 
 SECTION_KEYS = {"small": "cfg1_small_call", "multipass": "cfg3_multipass", "sar": "cfg3_sar_frame",
-                "tc": "cfg4_tensor_core", "serve": "cfg5_serving",
-                "sar_compress": "sar_compression"}
-DEFAULT_SECTIONS = "small,multipass,sar,tc,serve,sar_compress"
+                "tc": "cfg4_tensor_core", "tc6": "cfg4_tensor_core_six_step", "serve": "cfg5_serving",
+                "serve_tc14": "cfg5_serving_tc_single_pass", "sar_compress": "sar_compression"}
+DEFAULT_SECTIONS = "small,multipass,sar,tc,tc6,serve,serve_tc14,sar_compress"
 
 
 def host_numa_record(dev) -> dict:
@@ -1012,7 +1073,7 @@ def main() -> None:
                          "first stream (0: library default, -1: any stream)")
     ap.add_argument("--strict-order", action="store_true",
                     help="serve workload: admit strictly in arrival order (no backfilling)")
-    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "serve", "small",
+    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "tc6", "serve", "small",
                                            "sar_compress"],
                     default="sweep",
                     help="sweep: the headline batched N=2^8..2^14 line with every other "
@@ -1035,6 +1096,8 @@ def main() -> None:
                     help="sweep workload: comma-separated per-configuration sections timed after "
                          "the headline and reported under 'configs' (small, multipass, sar, tc, "
                          "serve, sar_compress), or 'none'")
+    ap.add_argument("--serve-tc-max-log", type=int, default=22,
+                    help="serving: largest log2 N of the tensor-core jobs (14: single-pass only)")
     ap.add_argument("--serve-jobs", type=int, default=4000,
                     help="jobs of the serving section of the sweep workload")
     args = ap.parse_args()

@@ -68,7 +68,10 @@ enum { FFT_FORWARD = -1, FFT_INVERSE = +1 };
  * class but FFT_PREC_TC_FP16_C32; the tensor-core classes compute each
  * radix-16 stage as a dense 16-point DFT matmul on the tensor cores with FP32
  * accumulation (twiddles stay FP32), after a radix-2/4/8 FP32 stage when the
- * length is not a power of 16, for batched 1D lengths 2^4 .. 2^14:
+ * length is not a power of 16, for batched 1D lengths 2^4 .. 2^14 in one pass
+ * and 2^15 .. 2^24 in six steps (transpose, tensor-core rows of N1, transpose
+ * with the twiddle w_N^{n2 k1}, rows of N2, transpose; N = N1 N2, a workspace
+ * of 2 min(batch, c) n elements, c = max(1, 2^28 / n)):
  *   FFT_PREC_TC_FP16    stage inputs and DFT matrix rounded to FP16 (each
  *                       stage's input scaled by 1/16, exactly undone at the end)
  *   FFT_PREC_TC_BF16    rounded to BF16

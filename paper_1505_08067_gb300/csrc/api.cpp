@@ -48,7 +48,7 @@ struct fft_plan_s {
   void* tables = nullptr;  // cf[spec.table_elems], then the status word
   int* status = nullptr;   // set by kernels whose bounded waits give up
   void* work = nullptr;    // cf[spec.work_elems]
-  PassLaunch launches[4];  // whole-batch launches, device pointers filled
+  PassLaunch launches[kMaxPasses];  // whole-batch launches, device pointers filled
   // lazily created resources of fft_execute_host
   cudaStream_t s_h2d = nullptr, s_k = nullptr, s_d2h = nullptr;
   cudaEvent_t ev_start = nullptr, ev_h2d = nullptr, ev_k = nullptr, ev_end = nullptr;
@@ -375,7 +375,8 @@ fft_status_t fft_plan_describe(fft_plan_t plan, char* buf, size_t len) {
   for (int i = 0; i < plan->spec.passes.size(); ++i) {
     const PassSpec& p = plan->spec.passes[i];
     const PassLaunch& l = plan->launches[i];
-    const char* kind = p.kind != PASS_FFT ? "copy"
+    const char* kind = p.kind == PASS_COPY        ? "copy"
+                       : p.kind == PASS_TRANSPOSE ? "transpose"
                        : p.tc_prec        ? (p.variant == 1 ? "tensor_core_warp_mma"
                                                                 : "tensor_core_tcgen05")
                        : l.has_staged     ? "staged"  // for a 16-byte-aligned source

@@ -159,7 +159,7 @@ double time_candidate(const fft_plan_options_t& o, const int64_t* n, int dims, i
   if (s.work_elems && work.alloc((size_t)s.work_elems * 8) != cudaSuccess) return kInf;
   int* status = reinterpret_cast<int*>(static_cast<char*>(tables.p) + (size_t)s.table_elems * 8);
   cudaMemsetAsync(status, 0, 16, st);
-  PassLaunch launches[4];
+  PassLaunch launches[kMaxPasses];
   if (enqueue_tables(s, static_cast<cf*>(tables.p), st) != cudaSuccess) return kInf;
   if (bind_launches(s, caps, static_cast<const cf*>(tables.p), status, launches) != cudaSuccess)
     return kInf;

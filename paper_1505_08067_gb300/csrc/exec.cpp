@@ -10,6 +10,7 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
   for (int i = 0; i < s.passes.size(); ++i) {
     const PassSpec& p = s.passes[i];
     PassLaunch l{};
+    if (p.kind == PASS_TRANSPOSE) l.grid = caps.sm_count;  // SMs: the transpose sizes its grid
     if (p.kind == PASS_FFT) {
       l.d = pass_desc(p, 0, s.batch, s.batch);
       l.d.tw = tables;
@@ -85,36 +86,49 @@ cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st) {
 }
 
 static cudaError_t enqueue_range(const PlanSpec& s, const PassLaunch* launches, const void* in,
-                                 void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st);
+                                 void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st,
+                                 int64_t work2_off);
 
 cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const void* in,
-                           void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st) {
+                           void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st,
+                           int64_t work2_off) {
+  if (work2_off < 0) work2_off = s.work2_off;
   if (nb <= 0) return cudaSuccess;
   if (s.chunk_batch <= 0 || nb <= s.chunk_batch)
-    return enqueue_range(s, launches, in, out, work, b0, nb, st);
+    return enqueue_range(s, launches, in, out, work, b0, nb, st, work2_off);
   // sub-batches in stream order, each reusing the workspace from its start
   const int64_t E = s.dims == 1 ? s.n[0] : s.n[0] * s.n[1];
   const int64_t eb = elem_bytes(s.precision);
   for (int64_t c = 0; c < nb; c += s.chunk_batch) {
     const int64_t n = std::min(s.chunk_batch, nb - c);
     cudaError_t e = enqueue_range(s, launches, static_cast<const char*>(in) + c * E * eb,
-                                  static_cast<char*>(out) + c * E * eb, work, b0 + c, n, st);
+                                  static_cast<char*>(out) + c * E * eb, work, b0 + c, n, st,
+                                  work2_off);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 static cudaError_t enqueue_range(const PlanSpec& s, const PassLaunch* launches, const void* in,
-                                 void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st) {
+                                 void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st,
+                                 int64_t work2_off) {
   if (nb <= 0) return cudaSuccess;
   const int64_t E = s.dims == 1 ? s.n[0] : s.n[0] * s.n[1];
+  // the second workspace buffer of six-step plans
+  void* work2 = work ? static_cast<char*>(work) + work2_off * elem_bytes(s.precision) : nullptr;
+  auto buf = [&](int b) -> void* {
+    return b == BUF_IN ? const_cast<void*>(in) : b == BUF_OUT ? out : b == BUF_WORK2 ? work2 : work;
+  };
   for (int i = 0; i < s.passes.size(); ++i) {
     const PassSpec& p = s.passes[i];
-    const void* src = p.src == BUF_IN ? in : (p.src == BUF_OUT ? (const void*)out : work);
-    void* dst = p.dst == BUF_OUT ? out : work;
+    const void* src = buf(p.src);
+    void* dst = buf(p.dst);
     cudaError_t e;
     if (p.kind == PASS_COPY) {
       e = launch_copy(src, dst, nb * E, 1, 1, st);
+    } else if (p.kind == PASS_TRANSPOSE) {
+      e = launch_transpose(src, dst, nb, p.tr_rows, p.tr_cols, p.tr_logN, p.tr_sign, p.io16,
+                           launches[i].grid, st);
     } else {
       PassLaunch l = launches[i];
       if (b0 != 0 || nb != s.batch) {

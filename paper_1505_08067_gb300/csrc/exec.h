@@ -22,7 +22,11 @@ cudaError_t enqueue_tables(const PlanSpec& s, cf* tables, cudaStream_t st);
 // point at entry b0, `work` holds min(nb, s.chunk_batch) entries (all nb when
 // the plan has no sub-batches) starting with entry b0.  Two-pass plans with
 // chunk_batch > 0 run in sub-batches of chunk_batch entries, in stream order.
+// work2_off: offset (elements) of a six-step plan's second workspace buffer
+// when the workspace was sized for fewer transforms than the plan's (a
+// server job's own workspace); -1 = the plan's.
 cudaError_t enqueue_passes(const PlanSpec& s, const PassLaunch* launches, const void* in,
-                           void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st);
+                           void* out, void* work, int64_t b0, int64_t nb, cudaStream_t st,
+                           int64_t work2_off = -1);
 
 }  // namespace gbfft

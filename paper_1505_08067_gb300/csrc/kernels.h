@@ -88,6 +88,13 @@ inline const void* resolve_tc_pass(int logL, int prec, int variant, int io16 = 0
   return variant == 1 ? resolve_tc(logL, prec) : resolve_umma(logL, prec, &sm);
 }
 
+// Six-step transposes (transpose.cu): per batch entry, rows x cols -> cols x
+// rows, optionally multiplying element (r, c) by exp(sign 2 pi i r c / 2^logN)
+// first (logN > 0); complex64, or complex32 with h16.  rows and cols are
+// multiples of 32.
+cudaError_t launch_transpose(const void* in, void* out, int64_t batch, int64_t rows, int64_t cols,
+                             int logN, int sign, int h16, int sm_count, cudaStream_t st);
+
 // Per-kernel attributes a launch needs (opt-in shared memory); call once after
 // resolving, before the first launch_pass.
 cudaError_t prepare_launch(PassLaunch& p);

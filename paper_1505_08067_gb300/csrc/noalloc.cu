@@ -48,7 +48,7 @@ struct DeviceState {
   int64_t n = 0, batch = 0;
   int direction = 0;
   PlanSpec spec;
-  PassLaunch launches[4];
+  PassLaunch launches[kMaxPasses];
   bool tables_valid = false;  // the array holds the tables of `spec` (segment list below)
   SmallVec<TwSegment, 40> table_layout;
 };

@@ -50,7 +50,7 @@ Sched default_schedule(int logL, int logR) {
 
 static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
   const int L = 1 << p.logL;
-  if (p.kind == PASS_COPY) {
+  if (p.kind == PASS_COPY || p.kind == PASS_TRANSPOSE) {
     p.block = 256;
     p.grid = 0;
     return true;
@@ -232,7 +232,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       return;
     }
     const bool ok = o.variant == 1 ? (l == 16 || l == 256 || l == 4096)
-                                   : (l >= 16 && l <= 16384 && is_pow2(l));
+                                   : (l >= 16 && l <= (int64_t(1) << 24) && is_pow2(l));
     if (precision == FFT_PREC_TC_FP16_C32 && o.variant == 1) {
       fail(FFT_ERR_NOT_IMPLEMENTED, "complex32 storage runs on the tcgen05 kernel (variant 0)");
       return;
@@ -241,7 +241,7 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       fail(FFT_ERR_NOT_IMPLEMENTED,
            o.variant == 1
                ? "the warp-level tensor-core kernel covers batched 1D lengths 16, 256, 4096"
-               : "the tensor-core classes cover batched 1D transforms of length 2^4 .. 2^14");
+               : "the tensor-core classes cover batched 1D transforms of length 2^4 .. 2^24");
       return;
     }
   }
@@ -336,23 +336,68 @@ void make_plan(PlanSpec& s, const int64_t* n, int dims, int64_t batch, int direc
       p.copy_count = batch;
       s.passes.push_back(p);
     } else if (precision != FFT_PREC_FP32) {
-      // radix-16 stages as DFT matmuls, after a radix-2/4/8 FP32 stage when N
-      // is not a power of 16; tiles of max(N, 4096) elements
-      Sched sch;
-      if (logN % 4) sch.push_back(logN % 4);
-      for (int i = 0; i < logN / 4; ++i) sch.push_back(4);
-      const int logT = logN > 12 ? logN : 12;
-      PassSpec p = contiguous_pass(logN, batch, 1, 16, 0, 1 << (logT - logN), caps);
-      p.rlogs = sch;
-      p.G = 1 << (logT - logN);
-      p.tiles_inner = (batch + p.G - 1) / p.G;
-      p.tiles = p.tiles_inner;
-      p.in = Strides{0, (int64_t)p.G * N, N, 1};
-      p.out = p.in;
-      p.tc_prec = precision == FFT_PREC_TC_FP16_C32 ? FFT_PREC_TC_FP16 : precision;
-      p.io16 = precision == FFT_PREC_TC_FP16_C32;
-      p.conj_in = p.conj_out = inv;
-      s.passes.push_back(p);
+      // radix-16 stages as DFT matmuls, after a radix-2/4/8 FP32 stage when L
+      // is not a power of 16; tiles of max(L, 4096) elements; `units`
+      // contiguous transforms of length L per batch entry
+      const int tcp = precision == FFT_PREC_TC_FP16_C32 ? FFT_PREC_TC_FP16 : precision;
+      const int h16 = precision == FFT_PREC_TC_FP16_C32;
+      auto tc_pass = [&](int logL, int64_t units) {
+        Sched sch;
+        if (logL % 4) sch.push_back(logL % 4);
+        for (int i = 0; i < logL / 4; ++i) sch.push_back(4);
+        const int logT = logL > 12 ? logL : 12;
+        PassSpec p = contiguous_pass(logL, batch, units, 16, 0, 1 << (logT - logL), caps);
+        p.rlogs = sch;
+        p.G = 1 << (logT - logL);
+        p.tiles_inner = (batch * units + p.G - 1) / p.G;
+        p.tiles = p.tiles_inner;
+        p.in = Strides{0, (int64_t)p.G << logL, int64_t(1) << logL, 1};
+        p.out = p.in;
+        p.tc_prec = tcp;
+        p.io16 = h16;
+        p.conj_in = p.conj_out = inv;
+        return p;
+      };
+      if (logN <= 14) {
+        s.passes.push_back(tc_pass(logN, 1));
+      } else {
+        // Six-step (Sec. 3.3 split into passes, with explicit transposes):
+        // x viewed as A[n1][n2] (N1 x N2, N = N1 N2, N1 <= N2);
+        //   T1  B = A^T                       (N2 rows of N1)
+        //   F1  C[n2][.] = DFT_N1(B[n2][.])   (tensor-core rows)
+        //   T2  D[k1][n2] = C[n2][k1] w_N^{n2 k1}
+        //   F2  E[k1][.] = DFT_N2(D[k1][.])
+        //   T3  X[k2 N1 + k1] = E[k1][k2]
+        // through two workspace buffers (so in == out is allowed), in
+        // sub-batches like the FP32 two-pass plans.
+        const int l1 = logN / 2, l2 = logN - l1;
+        const int64_t N1 = int64_t(1) << l1, N2 = int64_t(1) << l2;
+        const int64_t chunk = two_pass_chunk(N);
+        const int64_t cb = std::min(batch, chunk);
+        s.chunk_batch = batch > chunk ? chunk : 0;
+        s.work_elems = 2 * cb * N;
+        s.work2_off = cb * N;
+        auto transpose = [&](int64_t rows, int64_t cols, int twiddle_logN, int src, int dst) {
+          PassSpec t;
+          t.kind = PASS_TRANSPOSE;
+          t.tr_rows = rows;
+          t.tr_cols = cols;
+          t.tr_logN = twiddle_logN;
+          t.tr_sign = inv ? 1 : -1;
+          t.io16 = h16;
+          t.src = src;
+          t.dst = dst;
+          return t;
+        };
+        PassSpec f1 = tc_pass(l1, N2), f2 = tc_pass(l2, N1);
+        f1.src = f1.dst = BUF_WORK;
+        f2.src = f2.dst = BUF_WORK2;
+        s.passes.push_back(transpose(N1, N2, 0, BUF_IN, BUF_WORK));
+        s.passes.push_back(f1);
+        s.passes.push_back(transpose(N2, N1, logN, BUF_WORK, BUF_WORK2));
+        s.passes.push_back(f2);
+        s.passes.push_back(transpose(N1, N2, 0, BUF_WORK2, BUF_OUT));
+      }
     } else if (logN <= bmax) {
       int R = choose_R(logN, o.radix);
       PassSpec p = contiguous_pass(logN, batch, 1, R, o.schedule, o.tile, caps);
@@ -563,7 +608,11 @@ std::string describe(const PlanSpec& s) {
   for (size_t i = 0; i < s.passes.size(); ++i) {
     const PassSpec& p = s.passes[i];
     if (i) o << ",";
-    o << "{\"kind\":\"" << (p.kind == PASS_FFT ? "fft" : "copy") << "\"";
+    o << "{\"kind\":\""
+      << (p.kind == PASS_FFT ? "fft" : p.kind == PASS_COPY ? "copy" : "transpose") << "\"";
+    if (p.kind == PASS_TRANSPOSE)
+      o << ",\"rows\":" << p.tr_rows << ",\"cols\":" << p.tr_cols << ",\"twiddle_logN\":"
+        << p.tr_logN << ",\"io16\":" << p.io16;
     if (p.kind == PASS_FFT) {
       o << ",\"L\":" << (1 << p.logL) << ",\"R\":" << p.R << ",\"G\":" << p.G
         << ",\"lmap\":\"" << (p.lmap ? "cols" : "rows") << "\",\"smap\":\""

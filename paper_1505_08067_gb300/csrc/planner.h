@@ -37,8 +37,9 @@ struct SmallVec {
 };
 using Sched = SmallVec<int, 15>;
 
-enum { BUF_IN = 0, BUF_OUT = 1, BUF_WORK = 2 };
-enum { PASS_FFT = 0, PASS_COPY = 1 };
+enum { BUF_IN = 0, BUF_OUT = 1, BUF_WORK = 2, BUF_WORK2 = 3 };
+enum { PASS_FFT = 0, PASS_COPY = 1, PASS_TRANSPOSE = 2 };
+constexpr int kMaxPasses = 6;
 
 struct Caps {
   int sm_count = 152;
@@ -75,6 +76,12 @@ struct PassSpec {
   int64_t units_per_batch = 1;  // contiguous pass: transforms per batch entry
   // PASS_COPY
   int64_t copy_count = 0, copy_in_stride = 1, copy_out_stride = 1;
+  // PASS_TRANSPOSE: per batch entry, the tr_rows x tr_cols row-major matrix at
+  // the source is written as its tr_cols x tr_rows transpose; with tr_logN > 0
+  // element (r, c) is first multiplied by exp(tr_sign * 2 pi i r c / 2^tr_logN)
+  // (the six-step twiddle).
+  int64_t tr_rows = 0, tr_cols = 0;
+  int tr_logN = 0, tr_sign = -1;
   // twiddle-table offsets (complex entries) inside the plan's table allocation
   SmallVec<int32_t, 15> tw_off;  // per stage (stage 0 unused)
   int64_t epi_hi_off = 0, epi_lo_off = 0;
@@ -103,13 +110,15 @@ struct PlanSpec {
   bool generic_only = false;  // never pick compile-time specialisations
   bool conv = false;          // fast-convolution plan (make_plan with a ConvSpec)
   const void* filter[2] = {nullptr, nullptr};  // device filter spectra per dimension
-  SmallVec<PassSpec, 4> passes;
+  SmallVec<PassSpec, kMaxPasses> passes;
   SmallVec<TwSegment, 40> tables;
   int64_t table_elems = 0;
   int64_t work_elems = 0;
   // two-pass 1D plans execute in sub-batches of at most chunk_batch transforms
   // (0: no sub-batching); work_elems holds one sub-batch
   int64_t chunk_batch = 0;
+  // six-step plans: the second workspace buffer starts work2_off elements in
+  int64_t work2_off = 0;
   fft_status_t status = FFT_OK;
   char error[256] = {0};
   char tuning[4096] = {0};  // autotuner report (JSON), empty if not tuned

@@ -71,7 +71,7 @@ struct PlanEntry {
   PlanSpec spec;            // planned for a large batch; per-job descriptors rescale it
   void* tables = nullptr;   // twiddles + status word
   int* status = nullptr;
-  PassLaunch launches[4];
+  PassLaunch launches[kMaxPasses];
   bool groupable = false;   // contiguous single-pass FP32: coalesced launches
   int64_t elems = 0;        // complex elements per batch entry
   int64_t work_per_entry = 0;  // workspace elements per batch entry (two-pass plans)
@@ -289,7 +289,9 @@ bool launch_group(fft_server_t s, Running& r) {
           break;
         }
       }
-      e = enqueue_passes(pe->spec, pe->launches, rec.job.in, rec.job.out, ws, 0, rec.job.batch, st);
+      // a six-step plan's second buffer follows this job's first one
+      e = enqueue_passes(pe->spec, pe->launches, rec.job.in, rec.job.out, ws, 0, rec.job.batch, st,
+                         pe->spec.work2_off > 0 ? ws_entries * pe->elems : -1);
       if (ws) cudaFreeAsync(ws, st);  // after the passes, in stream order
       ++s->launches;
       if (e != cudaSuccess) break;

@@ -1,0 +1,95 @@
+// Batched transpose with an optional twiddle multiply: the transposes of a
+// six-step plan (Sec. 3.3 split into passes; Sec. 3.4 blocked transpose
+// through on-chip memory).  Per batch entry the rows x cols row-major matrix
+// at `in` is written as its cols x rows transpose at `out`; with logN > 0,
+// element (r, c) is first multiplied by exp(sign * 2 pi i r c / 2^logN)
+// (r c < 2^logN: the exponent is exact, the angle 2 r c / 2^logN too).
+// Elements are complex64, or complex32 (FP16 pairs) with H.
+//
+// 32 x 32 tiles through shared memory (one padding column: the column reads
+// of a half warp fall into distinct bank pairs); 256 threads, each moving 4
+// elements of a tile, loads and stores both along rows of 32 consecutive
+// elements.  Persistent grid over all tiles of all batch entries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels_impl.cuh"
+#include "tc_stage.h"
+
+namespace gbfft {
+
+namespace {
+
+template <bool H>
+__device__ __forceinline__ cf tr_load(const void* p, int64_t i) {
+  if (H) {  // an FP16 pair (real in the low half), widened exactly
+    const uint32_t r = __ldcs(static_cast<const unsigned int*>(p) + i);
+    float x, y;
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(x), "=f"(y)
+        : "r"(r));
+    return mk(x, y);
+  }
+  const float2 v = __ldcs(static_cast<const float2*>(p) + i);
+  return mk(v.x, v.y);
+}
+
+template <bool H>
+__device__ __forceinline__ void tr_store(void* p, int64_t i, cf v) {
+  if (H) static_cast<uint32_t*>(p)[i] = pack_rn<TC_FP16>(v.x, v.y);
+  else static_cast<float2*>(p)[i] = make_float2(v.x, v.y);
+}
+
+template <bool H, bool TW>
+__global__ void __launch_bounds__(256)
+transpose_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t batch, int64_t rows,
+                 int64_t cols, int logN, int sign) {
+  __shared__ cf tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t trow = rows / 32, tcol = cols / 32, per = trow * tcol;
+  for (int64_t t = blockIdx.x; t < batch * per; t += gridDim.x) {
+    const int64_t b = t / per, rt = (t - b * per) / tcol, ct = t - b * per - rt * tcol;
+    const int64_t base = b * rows * cols;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = rt * 32 + ty + 8 * i, c = ct * 32 + tx;
+      cf v = tr_load<H>(in, base + r * cols + c);
+      if (TW) {
+        cf w = DevMem::rotor(r * c, logN);  // exp(-2 pi i r c / N)
+        if (sign > 0) w = cconj(w);
+        v = cmul(v, w);
+      }
+      tile[ty + 8 * i][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t c = ct * 32 + ty + 8 * i, r = rt * 32 + tx;
+      tr_store<H>(out, base + c * rows + r, tile[tx][ty + 8 * i]);
+    }
+    __syncthreads();  // the tile is reused
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_transpose(const void* in, void* out, int64_t batch, int64_t rows, int64_t cols,
+                             int logN, int sign, int h16, int sm_count, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  if (rows % 32 || cols % 32 || rows < 32 || cols < 32) return cudaErrorInvalidValue;
+  const int64_t tiles = batch * (rows / 32) * (cols / 32);
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)(sm_count > 0 ? sm_count : 152) * 8);
+#define GB_TR(HH, TT) transpose_kernel<HH, TT><<<grid, 256, 0, st>>>(in, out, batch, rows, cols, logN, sign)
+  if (h16) {
+    if (logN > 0) GB_TR(true, true);
+    else GB_TR(true, false);
+  } else {
+    if (logN > 0) GB_TR(false, true);
+    else GB_TR(false, false);
+  }
+#undef GB_TR
+  return cudaGetLastError();
+}
+
+}  // namespace gbfft

@@ -723,10 +723,34 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
   const cf* in = reinterpret_cast<const cf*>(in_f);
   cf* out = reinterpret_cast<cf*>(out_f);
   for (const PassSpec& p : s.passes) {
-    const cf* src = p.src == BUF_IN ? in : (p.src == BUF_OUT ? out : work.data());
-    cf* dst = p.dst == BUF_OUT ? out : work.data();
+    // the second workspace buffer of six-step plans starts work2_off in
+    auto buf = [&](int b) -> cf* {
+      return b == BUF_IN ? const_cast<cf*>(in) : b == BUF_OUT ? out
+             : b == BUF_WORK2 ? work.data() + s.work2_off : work.data();
+    };
+    const cf* src = buf(p.src);
+    cf* dst = buf(p.dst);
     if (p.kind == PASS_COPY) {
       for (int64_t i = 0; i < E; ++i) dst[i] = src[i];
+      continue;
+    }
+    if (p.kind == PASS_TRANSPOSE) {
+      // written out from the definition: dst[b][c][r] = src[b][r][c], times
+      // exp(sign 2 pi i r c / 2^logN) when a twiddle is asked for
+      const int64_t R = p.tr_rows, C = p.tr_cols;
+      if (R * C * batch != E) err("transpose does not cover the batch", R * C);
+      if (src == dst) err("transpose in place", 0);
+      for (int64_t b = 0; b < batch; ++b)
+        for (int64_t r = 0; r < R; ++r)
+          for (int64_t c = 0; c < C; ++c) {
+            cf v = src[b * R * C + r * C + c];
+            if (p.tr_logN > 0) {
+              cf w = root(r * c, int64_t(1) << p.tr_logN);
+              if (p.tr_sign > 0) w = mk(w.x, -w.y);
+              v = mk(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            }
+            dst[b * R * C + c * R + r] = v;
+          }
       continue;
     }
     PassDesc d = pass_desc(p, 0, batch, batch);
@@ -741,9 +765,9 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
       src = src_copy.data();
     }
     g.in = src;
-    g.in_len = p.src == BUF_WORK ? s.work_elems : E;
+    g.in_len = E;  // every buffer of a replayed plan holds the whole batch
     g.out = dst;
-    g.out_len = p.dst == BUF_WORK ? s.work_elems : E;
+    g.out_len = E;
     std::vector<uint8_t> hits(g.out_len, 0);
     g.out_hits = &hits;
     g.tw = tables.data();

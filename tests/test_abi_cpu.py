@@ -64,9 +64,9 @@ def test_dry_run_rejects_options():
         g.fft_plan_dry_run(1024, 1, schedule=0x333)     # 8*8*8 != 1024
     with pytest.raises(g.GbfftError):
         g.fft_plan_dry_run(1024, 1, precision=9)
-    # tensor-core classes: 2^4 .. 2^14 on the tcgen05 kernel, 16 / 256 / 4096
-    # on the warp-level MMA kernel (variant 1)
-    for n, variant in ((2 ** 15, 0), (8, 0), (1024, 1)):
+    # tensor-core classes: 2^4 .. 2^24 on the tcgen05 kernel (six-step above
+    # 2^14), 16 / 256 / 4096 on the warp-level MMA kernel (variant 1)
+    for n, variant in ((2 ** 25, 0), (8, 0), (1024, 1)):
         with pytest.raises(g.GbfftError) as e:
             g.fft_plan_dry_run(n, 1, precision=g.FFT_PREC_TC_BF16, variant=variant)
         assert e.value.status == g.FFT_ERR_NOT_IMPLEMENTED
@@ -83,13 +83,40 @@ def test_dry_run_rejects_options():
     for logn in range(4, 15):
         (p,) = g.fft_plan_dry_run(2 ** logn, 5, precision=g.FFT_PREC_TC_FP16_C32)["passes"]
         assert p["tc_prec"] == g.FFT_PREC_TC_FP16 and p["io16"] == 1
-    for n, variant in ((2 ** 15, 0), (8, 0), (4096, 1)):
+    for n, variant in ((2 ** 25, 0), (8, 0), (4096, 1)):
         with pytest.raises(g.GbfftError) as e:
             g.fft_plan_dry_run(n, 1, precision=g.FFT_PREC_TC_FP16_C32, variant=variant)
         assert e.value.status == g.FFT_ERR_NOT_IMPLEMENTED
     with pytest.raises(g.GbfftError) as e:
         g.fft_plan_dry_run(1024, 1, precision=g.FFT_PREC_TC_FP16_C32 + 1)
     assert e.value.status == g.FFT_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("logn", range(15, 25))
+@pytest.mark.parametrize("precision", [1, 3, 4])
+def test_tc_six_step_plans(logn, precision):
+    """Tensor-core plans above 2^14: transpose, tensor-core rows of N1, transpose
+    with the twiddle, rows of N2, transpose (N = N1 N2, N1 <= N2), through two
+    workspace buffers, in sub-batches of at most 2^28 elements."""
+    N, batch = 2 ** logn, 3
+    d = g.fft_plan_dry_run(N, batch, precision=precision)
+    kinds = [p["kind"] for p in d["passes"]]
+    assert kinds == ["transpose", "fft", "transpose", "fft", "transpose"]
+    t1, f1, t2, f2, t3 = d["passes"]
+    n1, n2 = 2 ** (logn // 2), 2 ** (logn - logn // 2)
+    assert (t1["rows"], t1["cols"], t1["twiddle_logN"]) == (n1, n2, 0)
+    assert (t2["rows"], t2["cols"], t2["twiddle_logN"]) == (n2, n1, logn)
+    assert (t3["rows"], t3["cols"], t3["twiddle_logN"]) == (n1, n2, 0)
+    assert f1["L"] == n1 and f1["count_inner"] == batch * n2
+    assert f2["L"] == n2 and f2["count_inner"] == batch * n1
+    io16 = 1 if precision == 4 else 0
+    assert all(p["io16"] == io16 for p in d["passes"])
+    # in -> work -> work -> work2 -> work2 -> out
+    assert [(p["src"], p["dst"]) for p in d["passes"]] == [(0, 2), (2, 2), (2, 3), (3, 3), (3, 1)]
+    assert d["workspace_bytes"] == 2 * batch * N * 8
+    big = g.fft_plan_dry_run(N, (2 ** 28 // N) * 2 + 1, precision=precision)
+    assert big["chunk_batch"] == 2 ** 28 // N
+    assert big["workspace_bytes"] == 2 * 2 ** 28 * 8
 
 
 @pytest.mark.parametrize("logn", range(0, 25))

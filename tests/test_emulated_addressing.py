@@ -96,6 +96,9 @@ def test_four_step_twiddle_sources(oracle, epilogue, logn):
 
 # tensor-core class: tolerance per precision (see test_tc_gpu.py for the reading)
 TC_TOL = {1: lambda n: 2e-3, 2: lambda n: 5e-3, 3: lambda n: 5e-6 * np.log2(n)}
+# six-step plans round the data at the stages of both passes (up to six):
+# plain BF16 at about 2e-3 per rounded stage in quadrature needs 7e-3
+SIX_STEP_TOL = {1: lambda n: 2e-3, 2: lambda n: 7e-3, 3: lambda n: 5e-6 * np.log2(n)}
 
 
 @pytest.mark.parametrize("n", [16, 256, 4096])
@@ -128,6 +131,20 @@ def test_tcgen05_class_replay(oracle, logn, precision):
         y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision)
         assert nerr == 0, msg
         assert np.max(oracle.rel_l2(y, oracle.fft(x, d))) <= TC_TOL[precision](n), logn
+
+
+@pytest.mark.parametrize("logn,precision", [(15, 1), (16, 3), (17, 2), (18, 1)])
+def test_tcgen05_six_step_replay(oracle, logn, precision):
+    """Tensor-core plans above 2^14 (transposes, tensor-core rows of N1 and
+    N2, the six-step twiddle in the middle transpose), replayed on the CPU with
+    the UMMA emulated, against the oracle, forward and inverse, batch 2."""
+    n = 2 ** logn
+    x = synth.uniform(90 + logn, 2, n)
+    for d in (-1, 1):
+        y, nerr, msg = emu.run(x, (n,), direction=d, precision=precision)
+        assert nerr == 0, msg
+        err = np.max(oracle.rel_l2(y, oracle.fft(x, d)))
+        assert err <= SIX_STEP_TOL[precision](n), (logn, d, err)
 
 
 # ---------------------------------------------------------------- convolution --

@@ -145,10 +145,23 @@ def test_c32_server_job(gb, oracle):
     assert np.max(err) <= TOL, float(np.max(err))
 
 
+@pytest.mark.parametrize("logn,direction", [(15, -1), (18, 1), (21, -1), (24, 1)])
+def test_c32_six_step(gb, oracle, logn, direction):
+    """complex32 storage above 2^14: the six-step plan's transposes and
+    workspace carry FP16 pairs too."""
+    n = 2 ** logn
+    h, x = _fp16_pairs(synth.uniform(9990 + logn, 2, n))
+    with gb.Plan(n, 2, direction, C32) as p:
+        y = p.execute(_to_device(h))
+        _status(gb, p)
+    err = oracle.rel_l2(_to_numpy(y), oracle.fft(x, direction))
+    assert np.max(err) <= TOL, float(np.max(err))
+
+
 def test_c32_rejects(gb):
     """complex32 storage is the tcgen05 FP16 kernel's: no warp-MMA form, no
     lengths outside 2^4 .. 2^14, and buffers aligned to 4 bytes."""
-    for n, variant in ((2 ** 15, 0), (8, 0), (4096, 1)):
+    for n, variant in ((2 ** 25, 0), (8, 0), (4096, 1)):
         with pytest.raises(gb.GbfftError):
             gb.fft_plan_create(n, 4, -1, C32, variant=variant)
     with pytest.raises(gb.GbfftError):
