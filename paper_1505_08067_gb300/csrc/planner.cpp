@@ -1,5 +1,6 @@
 // Host-side planner (no CUDA calls).  See planner.h.
 #include "planner.h"
+#include "umma_stage.h"
 
 #include <math.h>
 #include <stdio.h>
@@ -80,7 +81,7 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
     const int logT = p.logL > 12 ? p.logL : 12;
     const int rows = 1 << (logT - 4);
     const size_t a = (size_t)rows * 64;
-    p.block = 256;
+    p.block = 32 * umma_warps(p.logL);
     p.pitch = 0;
     p.smem = (p.tc_prec == FFT_PREC_TC_BF16X3 ? 2 : 1) * a + 2 * 2048 + 16 + 1024;
     const int cols = 32 * (rows / 128);

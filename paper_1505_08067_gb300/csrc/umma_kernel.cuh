@@ -4,7 +4,7 @@
 // matrix descriptors, FP32 accumulators in tensor memory), with an optional
 // radix-2/4/8 first stage in FP32 registers.
 //
-// One CTA of 256 threads (8 warps) owns a tile of T = max(L, 4096) elements
+// One CTA of 256 threads (8 warps; 512 at 2^14) owns a tile of T = max(L, 4096) elements
 // at a time, on a persistent grid.  Per tile:
 //   load     every thread reads its share of the tile from global memory
 //            (radix-r0 first stage in registers when L is not a power of
@@ -209,7 +209,7 @@ struct Umma {
                                                   int warp, int lane) {
     const int q = warp & 3;
 #pragma unroll 1
-    for (int rb = warp >> 2; rb < G::RB; rb += 2) {
+    for (int rb = warp >> 2; rb < G::RB; rb += G::NWARP / 4) {
       const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + 32u * rb;
       const int m = rb * 128 + q * 32 + lane;
       typename Body::RowPart rp = Body::template row_part<t>(d, m);
@@ -223,7 +223,7 @@ struct Umma {
 };
 
 template <int LOGL, int PREC, bool H>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(32 * umma_warps(LOGL), umma_warps(LOGL) == 16 ? 2 : 4)
 stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDesc d) {
   using U = Umma<LOGL, PREC, H>;
   using Body = typename U::Body;
@@ -244,7 +244,7 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
 
   if (warp == 0) tmem_alloc(tslot, G::TMEM_COLS);
   // the DFT matrix (and its low part) in the B layout, once per CTA
-  for (int e = tid; e < 1024; e += 256) {
+  for (int e = tid; e < 1024; e += G::THREADS) {
     const int n = e >> 5, k = e & 31;
     const float v = umma_dft_entry(k, n);
     const uint16_t h = U::P == TC_FP16 ? f32_to_f16_bits(v) : f32_to_bf16_bits(v);

@@ -82,6 +82,11 @@ GB_HD constexpr uint32_t umma_load_lanes_code(int logL) {
   return 0;
 }
 
+// Warps of a tcgen05 block for length 2^logL: 8, and 16 at 2^14, whose 256
+// tensor-memory columns per block leave room for two blocks per SM only (16
+// warps there would leave an SM with half the warps of the shorter lengths).
+GB_HD constexpr int umma_warps(int logL) { return logL == 14 ? 16 : 8; }
+
 template <int LOGL>
 struct UmmaGeo {
   static_assert(LOGL >= 4 && LOGL <= 14, "tensor-core lengths are 2^4 .. 2^14");
@@ -101,7 +106,9 @@ struct UmmaGeo {
   static constexpr int B_BYTES = 32 * 64;            // one 32 x 32 B operand
   // loader work items: tile elements, or first-stage butterflies
   static constexpr int ITEMS = R0B ? T / R0 : T;
-  static constexpr int ITEMS_PER_THREAD = ITEMS / 256;
+  static constexpr int NWARP = umma_warps(LOGL);
+  static constexpr int THREADS = 32 * NWARP;
+  static constexpr int ITEMS_PER_THREAD = ITEMS / THREADS;
   // log2 of Ns before tensor-core stage t (the radices of earlier stages multiplied)
   GB_HD static constexpr int ns_log(int t) { return R0B + 4 * t; }
 };
@@ -294,7 +301,7 @@ struct UmmaBody {
   };
   GB_HD static BlockPart block_part_of(int et, int b) {
     BlockPart p{};
-    p.eb = et | umma_load_item<LOGL>(0, b * CH * 8);
+    p.eb = et | umma_load_item<LOGL>(0, b * CH * G::NWARP);
     p.xb = elem_of(p.eb);
     if (G::R0B == 0) p.offb = off_of(p.eb);
     else first_of(p.eb, 0, p.offb, p.ib, p.twb);
@@ -315,17 +322,17 @@ struct UmmaBody {
         cf v[CH];
 GB_UNROLL
         for (int j = 0; j < CH; ++j) {
-          const int ej = umma_load_item<LOGL>(0, j * 8);
+          const int ej = umma_load_item<LOGL>(0, j * G::NWARP);
           v[j] = FULL || tr_of(bp.eb | ej) < valid ? Mem::ldg_sw(gb, ej, swap) : mk(0.f, 0.f);
         }
 GB_UNROLL
         for (int j = 0; j < CH; ++j)
-          put_a<LOAD_SCALE>(a_hi, a_lo, bp.offb ^ off_of(umma_load_item<LOGL>(0, j * 8)), v[j]);
+          put_a<LOAD_SCALE>(a_hi, a_lo, bp.offb ^ off_of(umma_load_item<LOGL>(0, j * G::NWARP)), v[j]);
       } else {
         const cf* tw = d.tw + d.tw_off[1];
 GB_UNROLL
         for (int j = 0; j < CH; ++j) {
-          const int ej = umma_load_item<LOGL>(0, j * 8);
+          const int ej = umma_load_item<LOGL>(0, j * G::NWARP);
           const bool ok = FULL || tr_of(bp.eb | ej) < valid;
           cf y[G::R0];
 GB_UNROLL

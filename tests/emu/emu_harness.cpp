@@ -623,7 +623,7 @@ void run_umma_t(const PassDesc& d, const cf* in, cf* out) {
     const cf* gin = in + first * G::L;
     cf* gout = out + first * G::L;
     ++g_umma.phase;
-    for (int warp = 0; warp < 8; ++warp)
+    for (int warp = 0; warp < G::NWARP; ++warp)
       for (int lane = 0; lane < 32; ++lane) {
         const int et = umma_load_item<LOGL>(lane, warp);
         auto parts = [&](int b) { return Body::block_part_of(et, b); };
@@ -645,9 +645,9 @@ void run_umma_t(const PassDesc& d, const cf* in, cf* out) {
         }
       ++g_umma.phase;
       std::fill(row_reads.begin(), row_reads.end(), 0);
-      for (int warp = 0; warp < 8; ++warp)
+      for (int warp = 0; warp < G::NWARP; ++warp)
         for (int lane = 0; lane < 32; ++lane)
-          for (int rb = warp >> 2; rb < G::RB; rb += 2) {
+          for (int rb = warp >> 2; rb < G::RB; rb += G::NWARP / 4) {
             const int m = rb * 128 + (warp & 3) * 32 + lane;
             ++row_reads[m];
             // as the kernel: one row part, the row read in two halves
