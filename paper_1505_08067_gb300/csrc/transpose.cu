@@ -3,7 +3,9 @@
 // through on-chip memory).  Per batch entry the rows x cols row-major matrix
 // at `in` is written as its cols x rows transpose at `out`; with logN > 0,
 // element (r, c) is first multiplied by exp(sign * 2 pi i r c / 2^logN)
-// (r c < 2^logN: the exponent is exact, the angle 2 r c / 2^logN too).
+// (r c < 2^logN: the exponent is exact, the angle 2 r c / 2^logN too; a
+// thread's rows r, r + 8, r + 16, r + 24 of one column take the powers of
+// exp(sign 2 pi i 8 c / 2^logN), at most three further roundings).
 // Elements are complex64, or complex32 (FP16 pairs) with H.
 //
 // 32 x 32 tiles through shared memory (one padding column: the column reads
@@ -51,14 +53,24 @@ transpose_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t ba
   for (int64_t t = blockIdx.x; t < batch * per; t += gridDim.x) {
     const int64_t b = t / per, rt = (t - b * per) / tcol, ct = t - b * per - rt * tcol;
     const int64_t base = b * rows * cols;
+    // the thread's four elements share column c and step 8 rows: their
+    // twiddles are w^{r c} (w^{8 c})^i, two sincospi and a running product
+    const int64_t c = ct * 32 + tx, r0 = rt * 32 + ty;
+    cf w = mk(1.f, 0.f), step = mk(1.f, 0.f);
+    if (TW) {
+      w = DevMem::rotor(r0 * c, logN);  // exp(-2 pi i r c / N), r c < N
+      step = DevMem::rotor(8 * c, logN);
+      if (sign > 0) {
+        w = cconj(w);
+        step = cconj(step);
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int64_t r = rt * 32 + ty + 8 * i, c = ct * 32 + tx;
-      cf v = tr_load<H>(in, base + r * cols + c);
+      cf v = tr_load<H>(in, base + (r0 + 8 * i) * cols + c);
       if (TW) {
-        cf w = DevMem::rotor(r * c, logN);  // exp(-2 pi i r c / N)
-        if (sign > 0) w = cconj(w);
         v = cmul(v, w);
+        w = cmul(w, step);
       }
       tile[ty + 8 * i][tx] = v;
     }
