@@ -162,8 +162,12 @@ struct UmmaDevMemH : UmmaDevMem {
     return reinterpret_cast<cf*>(reinterpret_cast<uint32_t*>(p) + e);
   }
   __device__ __forceinline__ static cf ldg_sw(const cf* p, int64_t off, bool swap) {
+    return unpack_f16x2(ldg_pair(p, off, swap));
+  }
+  // the packed pair itself, halves swapped when asked
+  __device__ __forceinline__ static uint32_t ldg_pair(const cf* p, int64_t off, bool swap) {
     const uint32_t r = __ldcs(reinterpret_cast<const unsigned int*>(p) + off);
-    return unpack_f16x2(__byte_perm(r, 0u, swap ? 0x1032u : 0x3210u));
+    return __byte_perm(r, 0u, swap ? 0x1032u : 0x3210u);
   }
   __device__ __forceinline__ static void stg_sw(cf* p, int64_t off, cf v, bool swap) {
     reinterpret_cast<uint32_t*>(p)[off] =

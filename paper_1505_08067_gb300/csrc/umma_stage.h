@@ -318,7 +318,19 @@ struct UmmaBody {
     for (int b = 0; b < KB; ++b) {
       const BlockPart bp = parts(b);
       const cf* gb = Mem::at(gin, bp.xb);
-      if (G::R0B == 0) {
+      if constexpr (Mem::kHalfIO && !LOAD_SCALE && P == TC_FP16 && !SPLIT && G::R0B == 0) {
+        // complex32 into an FP16 operand, unscaled: the loaded pair is the
+        // operand's pair (swapped for the inverse), no conversion
+        uint32_t h[CH];
+GB_UNROLL
+        for (int j = 0; j < CH; ++j) {
+          const int ej = umma_load_item<LOGL>(0, j * G::NWARP);
+          h[j] = FULL || tr_of(bp.eb | ej) < valid ? Mem::ldg_pair(gb, ej, swap) : 0u;
+        }
+GB_UNROLL
+        for (int j = 0; j < CH; ++j)
+          Mem::sts32(a_hi + (bp.offb ^ off_of(umma_load_item<LOGL>(0, j * G::NWARP))), h[j]);
+      } else if (G::R0B == 0) {
         cf v[CH];
 GB_UNROLL
         for (int j = 0; j < CH; ++j) {
