@@ -438,7 +438,9 @@ GBFFT_API fft_status_t fft_server_destroy(fft_server_t server);
  * of fft_queue_create: 0 = one per tile of a max_batch job, at most what the
  * GPU holds at once) and a device-wide synchronisation waits for it to go
  * idle.  The queue allocates at creation only; submit and wait allocate
- * nothing.  Calls on one queue are serialised internally.
+ * nothing.  Calls on one queue are thread-safe; a wait polls its job's
+ * completion without holding the queue's lock, so other threads can submit
+ * meanwhile.
  */
 typedef struct fft_queue_s* fft_queue_t;
 

@@ -436,14 +436,21 @@ fft_status_t fft_queue_submit(fft_queue_t q, const void* in, void* out, int64_t 
 
 fft_status_t fft_queue_wait(fft_queue_t q, uint64_t ticket, double timeout_s) {
   if (!queue_ok(q)) return set_error(FFT_ERR_BAD_PLAN, "null or destroyed queue");
-  std::lock_guard<std::mutex> lock(q->mu);
-  if (ticket < 1 || ticket > q->issued) return set_error(FFT_ERR_INVALID_ARG, "unknown ticket");
+  int slots = 0;
+  {
+    std::lock_guard<std::mutex> lock(q->mu);
+    if (ticket < 1 || ticket > q->issued) return set_error(FFT_ERR_INVALID_ARG, "unknown ticket");
+    slots = q->slots;
+  }
+  // the ticket is complete once its slot's done word reaches it (queue_ring.h);
+  // polled without the lock, so other threads can submit meanwhile
+  const std::atomic<uint64_t>* done = done_of(q->ring + (ticket - 1) % (uint64_t)slots);
   const double limit = timeout_s < 0 ? 1e300 : now_s() + timeout_s;
   for (uint32_t it = 0;; ++it) {
-    update_completed(q);
-    if (q->completed >= ticket) return FFT_OK;
+    if (done->load(std::memory_order_acquire) >= ticket) return FFT_OK;
     if ((it & 255) == 255) {
       // a worker that ended just before this job arrived is started again
+      std::lock_guard<std::mutex> lock(q->mu);
       fft_status_t st = ensure_worker(q);
       if (st != FFT_OK) return st;
       if (now_s() > limit) return set_error(FFT_ERR_TIMEOUT, "job not finished before the timeout");

@@ -100,6 +100,47 @@ def test_queue_worker_ends_when_idle_and_restarts(gb, oracle):
     assert np.max(err) <= _tol(n), float(np.max(err))
 
 
+def test_queue_submit_while_another_thread_waits(gb, oracle):
+    """One thread submits 64 jobs while another waits for each in turn."""
+    import threading
+
+    n, B = 512, 32
+    x_np = synth.uniform(9994, B, n)
+    x = torch.from_numpy(x_np).cuda()
+    outs = torch.zeros(64, B, n, dtype=torch.complex64, device="cuda")
+    _ready()
+    errors = []
+    with gb.Queue(n, B, -1, slots=4) as q:
+        tickets = []
+        cv = threading.Condition()
+
+        def waiter():
+            try:
+                for i in range(64):
+                    with cv:
+                        cv.wait_for(lambda: len(tickets) > i, timeout=30)
+                        t = tickets[i]
+                    q.wait(t, 30.0)
+            except Exception as e:  # reported below
+                errors.append(e)
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        for i in range(64):
+            t = q.submit(x, outs[i], B)
+            with cv:
+                tickets.append(t)
+                cv.notify_all()
+        th.join(60)
+        assert not th.is_alive() and not errors, errors
+        assert q.info()["completed"] == 64
+    ref = oracle.fft(x_np, -1)
+    got = outs.cpu().numpy()
+    assert np.max(oracle.rel_l2(got[63], ref)) <= _tol(n)
+    for i in range(64):
+        assert np.array_equal(got[i], got[0]), i
+
+
 def test_queue_rejects(gb):
     x = torch.zeros(64 * 1024 + 1, dtype=torch.complex64, device="cuda")
     _ready()
