@@ -458,13 +458,6 @@ GB_UNROLL
       }
     }
   }
-
-  template <int t, int O0 = 0, int NO = 16>
-  GB_HD static void epilogue_row(const PassDesc& d, cf* gout, int valid, int m,
-                                 const uint32_t (&r)[2 * NO], uint32_t a_hi, uint32_t a_lo) {
-    RowPart rp = row_part<t>(d, m);
-    epilogue_part<t, O0, NO>(d, gout, valid, rp, r, a_hi, a_lo);
-  }
 };
 
 // UMMA shared-memory matrix descriptor (K-major, 64-byte swizzle): start
