@@ -110,6 +110,39 @@ def test_tcgen05_six_step_in_place_and_sub_batches(gb, oracle):
     assert np.max(err) <= SIX_STEP_TOL[3](n), float(np.max(err))
 
 
+def test_tcgen05_six_step_host_graph_and_server(gb, oracle):
+    """A six-step tensor-core plan through fft_execute_host (pinned host
+    buffers, chunked copies), through fft_execute_graph, and as a server job:
+    the same bytes as fft_execute."""
+    n, batch, prec = 2 ** 16, 5, 1
+    x_np = synth.uniform(9860, batch, n)
+    x = torch.from_numpy(x_np).cuda()
+    stream = torch.cuda.current_stream().cuda_stream
+    with gb.Plan(n, batch, 1, prec) as p:
+        ref = p.execute(x)
+        g = p.execute_graph(x)
+        hin = torch.from_numpy(x_np).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        din, dout = torch.empty_like(x), torch.empty_like(x)
+        p.execute_host(hin, hout, din, dout)
+        torch.cuda.synchronize()
+        gb.fft_plan_sync_status(p.handle, stream)
+    assert torch.equal(ref, g)
+    assert torch.equal(ref.cpu(), hout)
+    out = torch.empty_like(x)
+    torch.cuda.synchronize()
+    srv = gb.fft_server_create(memory_budget_bytes=1 << 30, streams=2)
+    try:
+        t = gb.fft_server_submit(srv, n, batch, 1, prec, x.data_ptr(), out.data_ptr())
+        assert gb.fft_server_wait(srv, t, 60.0)["status"] == 0
+    finally:
+        gb.fft_server_destroy(srv)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, out)
+    err = oracle.rel_l2(ref.cpu().numpy(), oracle.fft(x_np, 1))
+    assert np.max(err) <= SIX_STEP_TOL[prec](n), float(np.max(err))
+
+
 def test_tc_rejects_other_lengths(gb):
     for n, variant in ((2 ** 25, 0), (8, 0), (1024, 1)):
         with pytest.raises(gb.GbfftError) as e:
