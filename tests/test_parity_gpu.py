@@ -297,21 +297,29 @@ def test_generic_and_specialised_kernels_agree(gb, oracle, logn):
 def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
     """Contiguous 2^12..2^14 batches run the TMA-staged kernel when the input
     is 16-byte aligned; an input that is only 8-byte aligned takes the
-    register kernel.  Both agree with the oracle."""
+    register kernel.  An output that is only 8-byte aligned does not change
+    the staged kernel's result.  Every combination agrees with the oracle."""
     n = 2 ** logn
     batch = 40
     x_np = synth.uniform(9100 + logn, batch, n)
     buf = torch.zeros(batch * n + 1, dtype=torch.complex64, device="cuda")
-    for shift in (0, 1):                      # 1 complex64 = 8 bytes: breaks 16-byte alignment
+    obuf = torch.zeros(batch * n + 1, dtype=torch.complex64, device="cuda")
+    staged = []
+    # 1 complex64 = 8 bytes: breaks 16-byte alignment
+    for shift, oshift in ((0, 0), (1, 0), (0, 1)):
         xin = buf[shift:shift + batch * n]
         xin.copy_(torch.from_numpy(x_np.reshape(-1)))
-        out = torch.empty(batch * n, dtype=torch.complex64, device="cuda")
+        out = obuf[oshift:oshift + batch * n]
+        out.zero_()
         with gb.Plan(n, batch) as p:
             gb.fft_execute(p.handle, xin.data_ptr(), out.data_ptr(),
                            torch.cuda.current_stream().cuda_stream)
             gb.fft_plan_sync_status(p.handle, torch.cuda.current_stream().cuda_stream)
         y = out.view(batch, n).cpu().numpy()
-        assert np.max(oracle.rel_l2(y, oracle.fft(x_np))) <= _tol(n), shift
+        assert np.max(oracle.rel_l2(y, oracle.fft(x_np))) <= _tol(n), (shift, oshift)
+        if shift == 0:
+            staged.append(y)
+    assert np.array_equal(staged[0], staged[1])
 
 
 @pytest.mark.parametrize("shape,batch,opts", [((4096, 64), 2, {}), ((2 ** 20,), 2, {"split_log2": 10}),
