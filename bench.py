@@ -761,6 +761,76 @@ def section_compress(args) -> dict:
         "l2": "frame and azimuth filters 256 MiB each, larger than L2; no flush"}
 
 
+def section_cufft(args) -> dict:
+    """Context only (not the product path): the same transforms through
+    torch.fft, i.e. cuFFT on this GPU, beside this library, on the same
+    device-resident inputs with the same timing (CUDA events on the launching
+    stream, median of the timed repetitions after warm-up): the sweep sizes
+    2^8..2^14 on 2^27 elements, the two-pass sizes 2^20 / 2^22 / 2^24 on 2^26
+    elements, the 4096 x 8192 frame (2D) and N = 1024 x 64, forward.  Inputs of
+    256 MiB and up exceed L2 (no flush); the small case is L2-resident for
+    both."""
+    import numpy as np
+    import torch
+
+    from paper_1505_08067_gb300 import gbfft
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    items = ([((2 ** e,), 2 ** (TOTAL_LOG - e)) for e in range(8, 15)] +
+             [((2 ** e,), 2 ** (26 - e)) for e in (20, 22, 24)] + [((4096, 8192), 1), ((1024,), 64)])
+    E = max(int(np.prod(sh)) * b for sh, b in items)
+    x = torch.empty(E, dtype=torch.complex64, device=dev)
+    gbfft.fft_fill_uniform(x.data_ptr(), E, 5, 0, stream.cuda_stream)
+    y = torch.empty_like(x)
+    reps, warm = max(args.steps // 2, 10), 3
+
+    def timed(fn):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+    peaks = load_peaks()
+    per = {}
+    sampler = ClockSampler(gpu_id_of(dev))
+    sampler.start()
+    for shape, batch in items:
+        e = int(np.prod(shape)) * batch
+        xi, yi = x[:e], y[:e]
+        if len(shape) == 1:
+            xv = xi.view(batch, shape[0])
+            ref = lambda: torch.fft.fft(xv, dim=-1)  # noqa: E731
+        else:
+            xv = xi.view(batch, *shape)
+            ref = lambda: torch.fft.fft2(xv)  # noqa: E731
+        with gbfft.Plan(shape if len(shape) > 1 else shape[0], batch, -1) as p:
+            ours = timed(lambda: p.execute(xi, yi, stream))
+            passes = len(p.describe()["passes"])
+        cu = timed(ref)
+        lg = int(np.log2(np.prod(shape)))
+        key = f"{'x'.join(map(str, shape))} x {batch}"
+        byts = 16.0 * passes * e
+        per[key] = {"ours_ms": round(ours, 4), "cufft_ms": round(cu, 4),
+                    "speedup_vs_cufft": round(cu / ours, 3),
+                    "ours_gflops": round(5.0 * e * lg / (ours * 1e-3) / 1e9, 1),
+                    "cufft_gflops": round(5.0 * e * lg / (cu * 1e-3) / 1e9, 1),
+                    "ours_frac": round(byts / (ours * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+    clocks = sampler.stop()
+    torch.cuda.empty_cache()  # cuFFT plans and torch.fft outputs
+    return {"workload": "context: torch.fft (cuFFT, torch " + torch.__version__ + ") beside "
+                        "fft_execute on the same inputs, forward, complex64",
+            "data": "iid U[-1,1) from the device generator, seed 5", "reps": reps,
+            "warmup": warm, "per_item": per, "clocks": clocks,
+            "note": "cuFFT is a comparator for context; no part of this library calls it"}
+
+
 def section_small(args) -> dict:
     """Small batch (cfg1): N = 1024, batch 64 (512 KiB), launch-latency bound.
     Per call of fft_execute (one kernel launch), fft_execute_graph (the same
@@ -977,6 +1047,8 @@ def ours(args, rank: int, world: int) -> None:
                     rec = section_serve(a14, args.serve_jobs, args.load)
                 elif name == "sar_compress":
                     rec = section_compress(args)
+                elif name == "cufft":
+                    rec = section_cufft(args)
                 else:
                     rec = {"error": f"unknown section {name}"}
             except Exception as exc:  # recorded in the line, not hidden
@@ -1018,8 +1090,9 @@ def ours(args, rank: int, world: int) -> None:
 
 SECTION_KEYS = {"small": "cfg1_small_call", "multipass": "cfg3_multipass", "sar": "cfg3_sar_frame",
                 "tc": "cfg4_tensor_core", "tc6": "cfg4_tensor_core_six_step", "serve": "cfg5_serving",
-                "serve_tc14": "cfg5_serving_tc_single_pass", "sar_compress": "sar_compression"}
-DEFAULT_SECTIONS = "small,multipass,sar,tc,tc6,serve,serve_tc14,sar_compress"
+                "serve_tc14": "cfg5_serving_tc_single_pass", "sar_compress": "sar_compression",
+                "cufft": "context_cufft"}
+DEFAULT_SECTIONS = "small,multipass,sar,tc,tc6,serve,serve_tc14,sar_compress,cufft"
 
 
 def host_numa_record(dev) -> dict:
@@ -1073,7 +1146,7 @@ def main() -> None:
                          "first stream (0: library default, -1: any stream)")
     ap.add_argument("--strict-order", action="store_true",
                     help="serve workload: admit strictly in arrival order (no backfilling)")
-    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "tc6", "serve", "small",
+    ap.add_argument("--workload", choices=["sweep", "multipass", "sar", "tc", "tc6", "serve", "small", "cufft",
                                            "sar_compress"],
                     default="sweep",
                     help="sweep: the headline batched N=2^8..2^14 line with every other "
@@ -1127,6 +1200,8 @@ def main() -> None:
             rec = section_small(args)
         elif args.workload == "sar_compress":
             rec = section_compress(args)
+        elif args.workload == "cufft":
+            rec = section_cufft(args)
         else:
             rec = section_items(args.workload, args)
         if rank == 0:
