@@ -8,15 +8,15 @@ const void* resolve_umma(int logL, int prec, size_t* smem) {
 #define GB_UMMA(LG)                                                              \
   if (logL == LG) {                                                              \
     if (prec == TC_FP16) {                                                       \
-      *smem = Umma<LG, TC_FP16>::SMEM + 1024;                                    \
+      *smem = Umma<LG, TC_FP16>::SMEM + 1024 + umma_staging_bytes(LG, 8, false); \
       return (const void*)stockham_umma<LG, TC_FP16, false>;                     \
     }                                                                            \
     if (prec == TC_BF16) {                                                       \
-      *smem = Umma<LG, TC_BF16>::SMEM + 1024;                                    \
+      *smem = Umma<LG, TC_BF16>::SMEM + 1024 + umma_staging_bytes(LG, 8, false); \
       return (const void*)stockham_umma<LG, TC_BF16, false>;                     \
     }                                                                            \
     if (prec == TC_BF16X3) {                                                     \
-      *smem = Umma<LG, TC_BF16X3>::SMEM + 1024;                                  \
+      *smem = Umma<LG, TC_BF16X3>::SMEM + 1024 + umma_staging_bytes(LG, 8, true); \
       return (const void*)stockham_umma<LG, TC_BF16X3, false>;                   \
     }                                                                            \
   }

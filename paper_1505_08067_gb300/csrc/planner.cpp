@@ -75,7 +75,7 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
     // tcgen05 kernel: 8 warps; the A operand of a tile (T/16 rows of 64
     // bytes; twice for the split class), the DFT matrix and its low part
     // (2 KB each), an mbarrier and the tensor-memory address, 1 KB of
-    // alignment slack.  Each CTA holds 32 tensor-memory columns per 128
+    // alignment slack, and for tiles of 4096 elements the staging buffer.  Each CTA holds 32 tensor-memory columns per 128
     // rows; the shared-memory request keeps the CTAs an SM can hold within
     // its 512 columns.
     const int logT = p.logL > 12 ? p.logL : 12;
@@ -83,7 +83,8 @@ static bool fill_launch(PassSpec& p, const Caps& caps, const char*& err) {
     const size_t a = (size_t)rows * 64;
     p.block = 32 * umma_warps(p.logL);
     p.pitch = 0;
-    p.smem = (p.tc_prec == FFT_PREC_TC_BF16X3 ? 2 : 1) * a + 2 * 2048 + 16 + 1024;
+    p.smem = (p.tc_prec == FFT_PREC_TC_BF16X3 ? 2 : 1) * a + 2 * 2048 + 16 + 1024 +
+             umma_staging_bytes(p.logL, p.io16 ? 4 : 8, p.tc_prec == FFT_PREC_TC_BF16X3);
     const int cols = 32 * (rows / 128);
     const size_t per_sm = (size_t)caps.smem_optin + 1024;  // the runtime keeps 1 KB per CTA
     const size_t floor_smem = per_sm / (size_t)(512 / cols + 1) + 1 - 1024;

@@ -6,10 +6,15 @@
 //
 // One CTA of 256 threads (8 warps; 512 at 2^14) owns a tile of T = max(L, 4096) elements
 // at a time, on a persistent grid.  Per tile:
-//   load     every thread reads its share of the tile from global memory
-//            (radix-r0 first stage in registers when L is not a power of
-//            16), twiddles, rounds to FP16/BF16 and stores the stage-0 A
-//            operand in shared memory;
+//   load     every thread reads its share of the tile (radix-r0 first stage
+//            in registers when L is not a power of 16), twiddles, rounds to
+//            FP16/BF16 and stores the stage-0 A operand in shared memory.
+//            Tiles of 4096 elements (L <= 2^12; not the split class) from a
+//            16-byte-aligned input are read from a staging buffer in shared
+//            memory, which a
+//            bulk copy (TMA) fills with the CTA's next tile while this one
+//            goes through its stages; the others from global memory, the
+//            next tile prefetched into L2;
 //   stage t  thread 0 issues the UMMAs of the stage (T/2048 row blocks x 2
 //            K halves; x3 for the split-BF16 class) and commits them to an
 //            mbarrier; all threads wait (bounded), each warp reads its rows
@@ -175,11 +180,30 @@ struct UmmaDevMemH : UmmaDevMem {
   }
 };
 
+// The loader's reads from the staging buffer (shared memory, same element
+// offsets as the tile in global memory) instead of global memory.
+template <class Base>
+struct UmmaStagedMem : Base {
+  __device__ __forceinline__ static uint32_t ldg_pair(const cf* p, int64_t off, bool swap) {
+    const uint32_t r = reinterpret_cast<const uint32_t*>(p)[off];
+    return __byte_perm(r, 0u, swap ? 0x1032u : 0x3210u);
+  }
+  __device__ __forceinline__ static cf ldg_sw(const cf* p, int64_t off, bool swap) {
+    if constexpr (Base::kHalfIO) {
+      return unpack_f16x2(ldg_pair(p, off, swap));
+    } else {
+      const float2 v = reinterpret_cast<const float2*>(p)[off];
+      return swap ? mk(v.y, v.x) : mk(v.x, v.y);
+    }
+  }
+};
+
 template <int LOGL, int PREC, bool H = false>
 struct Umma {
   using G = UmmaGeo<LOGL>;
   using Mem = std::conditional_t<H, UmmaDevMemH, UmmaDevMem>;
   using Body = UmmaBody<LOGL, PREC, Mem>;
+  using BodyS = UmmaBody<LOGL, PREC, UmmaStagedMem<Mem>>;  // loader from the staging buffer
   static constexpr int P = Body::P;
   static constexpr bool SPLIT = Body::SPLIT;
   static constexpr int SMEM = (SPLIT ? 2 : 1) * G::A_BYTES + 2 * G::B_BYTES + 16;
@@ -245,6 +269,18 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
   uint64_t* bar = reinterpret_cast<uint64_t*>(gbase + (b_lo + G::B_BYTES - base));
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // staging buffer (umma_staging_bytes): 128-byte aligned after the above
+  constexpr bool kStaged = umma_staging_bytes(LOGL, ESZ, U::SPLIT) > 0;
+  constexpr uint32_t kStageBytes = kStaged ? (uint32_t)G::T * ESZ : 0u;
+  const uint32_t st_rel = ((b_lo + G::B_BYTES - base) + 16u + 127u) & ~127u;
+  const cf* stg = reinterpret_cast<const cf*>(gbase + st_rel);
+  uint64_t* lbar = reinterpret_cast<uint64_t*>(gbase + st_rel + kStageBytes);
+  const bool staged = kStaged && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+  // bytes of tile t's valid transforms (every transform L * ESZ >= 64 bytes)
+  auto tile_bytes = [&](int64_t t) -> uint32_t {
+    const int64_t rem = d.count_inner - t * G::TPT;
+    return (uint32_t)((rem < G::TPT ? rem : G::TPT) * G::L * ESZ);
+  };
 
   if (warp == 0) tmem_alloc(tslot, G::TMEM_COLS);
   // the DFT matrix (and its low part) in the B layout, once per CTA
@@ -257,16 +293,26 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
       *reinterpret_cast<uint16_t*>(gbase + (b_lo - base) + umma_boff(n, k)) =
           f32_to_bf16_bits(v - bf16_bits_to_f32(h));
   }
-  if (tid == 0) mbar_init(bar, 1);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    if (kStaged) mbar_init(lbar, 1);
+  }
   fence_smem_async();
   tc05_fence_before();
   __syncthreads();
   tc05_fence_after();
   const uint32_t tmem = *tslot;
+  // the first tile's copy; `pending`: a copy is in flight that no wait has seen
+  bool pending = staged && blockIdx.x < d.tiles;
+  if (pending && tid == 0)
+    tma_load(const_cast<cf*>(stg), Mem::at(in, (int64_t)blockIdx.x * G::TPT * G::L),
+             tile_bytes(blockIdx.x), lbar);
+  uint32_t lparity = 0;
 
   // the loader's parts of this thread's blocks of items
   const int et = umma_load_item<LOGL>(lane, warp);
   auto parts = [&](int b) { return Body::block_part_of(et, b); };
+  auto parts_s = [&](int b) { return U::BodyS::block_part_of(et, b); };
 
   uint32_t parity = 0;
   bool failed = false;
@@ -278,7 +324,7 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
     cf* gout = Mem::at(out, first * G::L);
     // the tile this CTA takes next, into L2 while this one is computed
     // (whole 16-byte units inside the tile only; none for a ragged tile)
-    if (tid == 0 && tile + gridDim.x < d.tiles) {
+    if (!staged && tid == 0 && tile + gridDim.x < d.tiles) {
       const int64_t nfirst = (tile + gridDim.x) * G::TPT;
       if (nfirst + G::TPT <= d.count_inner) {
         const uintptr_t a = reinterpret_cast<uintptr_t>(Mem::at(in, nfirst * G::L));
@@ -287,11 +333,36 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
         if (e16 > a16) prefetch_l2(reinterpret_cast<const void*>(a16), (uint32_t)(e16 - a16));
       }
     }
-    if (valid == G::TPT) Body::template load_tile<true>(d, gin, valid, a_hi, a_lo, parts);
-    else Body::template load_tile<false>(d, gin, valid, a_hi, a_lo, parts);
+    bool direct = true;
+    if constexpr (kStaged) {
+      if (staged) {
+        const bool ok = mbar_wait(lbar, lparity, kWaitPolls);
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) atomicExch(d.status, 1);
+          failed = true;
+          break;
+        }
+        lparity ^= 1u;
+        pending = false;
+        if (valid == G::TPT) U::BodyS::template load_tile<true>(d, stg, valid, a_hi, a_lo, parts_s);
+        else U::BodyS::template load_tile<false>(d, stg, valid, a_hi, a_lo, parts_s);
+        direct = false;
+      }
+    }
+    if (direct) {
+      if (valid == G::TPT) Body::template load_tile<true>(d, gin, valid, a_hi, a_lo, parts);
+      else Body::template load_tile<false>(d, gin, valid, a_hi, a_lo, parts);
+    }
     fence_smem_async();
     tc05_fence_before();
     __syncthreads();
+    // every thread has read the staging buffer: the next tile's copy
+    if (staged && tile + gridDim.x < d.tiles) {
+      pending = true;
+      if (tid == 0)
+        tma_load(const_cast<cf*>(stg), Mem::at(in, (tile + gridDim.x) * G::TPT * G::L),
+                 tile_bytes(tile + gridDim.x), lbar);
+    }
     auto stage = [&](auto t_) {
       constexpr int t = decltype(t_)::value;
       if (failed) return;
@@ -319,6 +390,8 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
     if constexpr (G::NTC > 1) stage(std::integral_constant<int, 1>());
     if constexpr (G::NTC > 2) stage(std::integral_constant<int, 2>());
   }
+  // a copy still in flight (after a failure) lands before the CTA leaves
+  if (pending && tid == 0) mbar_wait(lbar, lparity, kWaitPolls);
   tc05_fence_before();
   __syncthreads();
   if (warp == 0) {

@@ -87,6 +87,17 @@ GB_HD constexpr uint32_t umma_load_lanes_code(int logL) {
 // warps there would leave an SM with half the warps of the shorter lengths).
 GB_HD constexpr int umma_warps(int logL) { return logL == 14 ? 16 : 8; }
 
+// Shared-memory bytes of the staging buffer of a tcgen05 CTA (elements of
+// eb bytes): tiles of 4096 elements (L <= 2^12) are copied into shared memory
+// by one bulk copy while the previous tile is computed, and the loader reads
+// them from there; 128 bytes of alignment and the copy's mbarrier included.
+// Longer transforms (tiles of L elements, 64 or 128 KB) and the split class
+// (two A operands; with the buffer three CTAs fit an SM instead of four,
+// measured slower) load from global memory.
+GB_HD constexpr int umma_staging_bytes(int logL, int eb, bool split) {
+  return logL <= 12 && !split ? 128 + 4096 * eb + 16 : 0;
+}
+
 template <int LOGL>
 struct UmmaGeo {
   static_assert(LOGL >= 4 && LOGL <= 14, "tensor-core lengths are 2^4 .. 2^14");

@@ -158,6 +158,35 @@ def test_c32_six_step(gb, oracle, logn, direction):
     assert np.max(err) <= TOL, float(np.max(err))
 
 
+@pytest.mark.parametrize("logn", [4, 6, 12, 13])
+def test_c32_unaligned_input(gb, oracle, logn):
+    """A complex32 input that is only 4-byte aligned (an odd element offset)
+    is read from global memory directly instead of through the staging copy
+    (tiles of 4096 elements); both within the class's bound, and the same
+    bytes where the loader does no arithmetic (N a power of 16; 2^13 has no
+    staging copy).  With an FP32 first stage (2^6) the two loaders are
+    separately compiled code whose multiply-adds may be contracted
+    differently."""
+    n = 2 ** logn
+    batch = max(4096 // n, 1) * 40 + 3
+    h, x = _fp16_pairs(synth.uniform(9985 + logn, batch, n))
+    buf = torch.zeros(2 * (batch * n + 1), dtype=torch.float16, device="cuda").view(torch.complex32)
+    outs = []
+    for shift in (0, 1):
+        xin = buf[shift:shift + batch * n]
+        xin.view(torch.float16).copy_(torch.from_numpy(np.ascontiguousarray(h).reshape(-1)).cuda())
+        out = torch.empty(batch * n, dtype=torch.complex32, device="cuda")
+        with gb.Plan(n, batch, -1, C32) as p:
+            st = torch.cuda.current_stream().cuda_stream
+            gb.fft_execute(p.handle, xin.data_ptr(), out.data_ptr(), st)
+            gb.fft_plan_sync_status(p.handle, st)
+        outs.append(out.view(torch.int16))
+        err = oracle.rel_l2(_to_numpy(out.view(batch, n)), oracle.fft(x, -1))
+        assert np.max(err) <= TOL, (shift, float(np.max(err)))
+    if logn % 4 == 0 or logn > 12:
+        assert torch.equal(outs[0], outs[1])
+
+
 def test_c32_rejects(gb):
     """complex32 storage is the tcgen05 FP16 kernel's: no warp-MMA form, no
     lengths outside 2^4 .. 2^14, and buffers aligned to 4 bytes."""
