@@ -198,7 +198,23 @@ struct PassDesc {
   int32_t tmap_in_ok, tmap_out_ok;
   alignas(64) unsigned char tmap_in[128];
   alignas(64) unsigned char tmap_out[128];
+  // Fast convolution over column tiles with per-line filters
+  // (cols_filter_staged): when tmap_h_ok, each tile's filters (G columns of
+  // the filter frame, laid out like the input frame) are copied into shared
+  // memory by tensor-map boxes over h (dims {in.e, L}, box {G, min(L, 256)}).
+  int32_t tmap_h_ok;
+  alignas(64) unsigned char tmap_h[128];
 };
+
+// Column tiles of a fast convolution whose filters can be staged by tile:
+// one filter per column (h_lines = the row length in.e, adjacent columns
+// adjacent: in.g = 1), starting at column 0 (h_first = 0), so that the
+// filters of the tile's columns col0 .. col0 + G - 1 are the same columns of
+// the filter frame.
+GB_HD bool cols_filter_staged(const PassDesc& d) {
+  return d.conv && d.G > 1 && d.h_lines > 1 && d.h_lines == d.in.e && d.in.g == 1 &&
+         d.h_first == 0 && d.in.e % 2 == 0;
+}
 
 // Can the column tiles of `d` (G adjacent columns of L rows) be moved by
 // tensor-map boxes over the buffer with strides `st` (d.in or d.out) viewed

@@ -285,12 +285,17 @@ GB_UNROLL
   // m < R.  Each value is multiplied by h_scale * H[position] and swapped
   // (re <-> im), and round 2's stage 0 (radix 16), whose butterfly q reads
   // positions t + (q + i*NB)*T, runs on the registers: no exchange between
-  // the rounds.  Contiguous lines only; `line` (the tile) selects the filter
-  // (PassDesc::h_lines).
-  GB_HD static void conv_middle(cf (&v)[R], const PassDesc& d, int64_t line, int tid) {
+  // the rounds.  `line`: the tile (contiguous lines) or its first column
+  // (column tiles: line line + g for transform g) selects the filter
+  // (PassDesc::h_lines).  `fst` (column tiles with per-line filters whose
+  // tile cols_filter_staged() allows): the tile's filters staged in shared
+  // memory like the data (position a of column g at a*G + g); else the
+  // filter is read from global memory.
+  GB_HD static void conv_middle(cf (&v)[R], const PassDesc& d, int64_t line, int tid,
+                                const cf* fst = nullptr) {
     constexpr int NB = SH::kNB;
     static_assert(SH::radix(0) == 16, "round 2 starts with a radix-16 stage");
-    static_assert(G == 1, "the staged convolution runs contiguous lines");
+    static_assert(G == 1 || !SH::kFuseLast, "column tiles end with a radix-16 stage");
     int g, t;
     coords(tid, g, t);
     cf y[R];  // y[m]: spectrum at position t + m*T
@@ -317,13 +322,27 @@ GB_UNROLL
 GB_UNROLL
         for (int i = 0; i < 16; ++i) y[q + i * NB] = v[q * 16 + i];
     }
-    const cf* h = d.h;
-    if (d.h_lines > 1) h += ((d.h_first + line) % d.h_lines) * (int64_t)L;
     const float sc = d.h_scale;
+    if (G > 1 && fst) {
 GB_UNROLL
-    for (int m = 0; m < R; ++m) {
-      const cf z = cmul(y[m], Mem::ldtw(h + t + m * T));
-      y[m] = mk(z.y * sc, z.x * sc);
+      for (int m = 0; m < R; ++m) {
+        const cf z = cmul(y[m], Mem::lds(fst, (t + m * T) * G + g));
+        y[m] = mk(z.y * sc, z.x * sc);
+      }
+    } else {
+      // contiguous lines: line u's filter at h + u * L; column tiles: column
+      // u's at h + u * in.g, element a at a * in.e (a shared filter: h + a)
+      const cf* h = d.h;
+      int64_t he = 1;
+      if (d.h_lines > 1) {
+        h += ((d.h_first + line + g) % d.h_lines) * (G == 1 ? (int64_t)L : d.in.g);
+        he = G == 1 ? 1 : d.in.e;
+      }
+GB_UNROLL
+      for (int m = 0; m < R; ++m) {
+        const cf z = cmul(y[m], Mem::ldtw(h + (int64_t)(t + m * T) * he));
+        y[m] = mk(z.y * sc, z.x * sc);
+      }
     }
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {

@@ -67,9 +67,11 @@
 // columns per block, rows copied by 16-byte asynchronous copies while the
 // previous tile is computed, half-size exchanges):
 //   GB_STAGED_COLS(log2 L, schedule, stages, R, G, epilogue, conv)
-// four-step first passes (epilogue 2, 3 or 4) and the 2D column pass.  (The
-// azimuth convolution keeps the 1024-thread register kernel, measured faster.)
+// four-step first passes (epilogue 2, 3 or 4), the 2D column pass and the
+// azimuth convolution of 4096-row frames (conv 1: per-column filters staged
+// by tile, cols_filter_staged).
 #define GB_STAGED_COLS_SHAPES(GB_STAGED_COLS)      \
+  GB_STAGED_COLS(12, 0x444, 3, 32, 4, 0, 1)        \
   GB_STAGED_COLS(10, 0x244, 3, 32, 16, 2, 0)       \
   GB_STAGED_COLS(10, 0x244, 3, 32, 16, 3, 0)       \
   GB_STAGED_COLS(11, 0x344, 3, 32, 8, 2, 0)        \

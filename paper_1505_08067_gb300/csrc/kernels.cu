@@ -81,7 +81,9 @@ bool resolve_staged(const PassDesc& d, int lmap, int smap, bool generic_only, St
   if (generic_only) return false;
   if (lmap == MAP_COLS) {
     s->map_in = s->map_out = true;
-    return !d.conv && resolve_staged_cols_shape(d, lmap, smap, s);
+    // convolutions over column tiles: only with per-column filters staged
+    // by tile (a shared filter keeps the register kernel)
+    return (!d.conv || cols_filter_staged(d)) && resolve_staged_cols_shape(d, lmap, smap, s);
   }
   if (lmap == MAP_ROWS && smap == MAP_COLS) {
     s->map_out = true;
@@ -146,11 +148,32 @@ static bool encode_cols_map(const PassDesc& d, const Strides& st, const void* p,
   return true;
 }
 
+// Tensor map of the filter frame of a convolution over column tiles
+// (cols_filter_staged): dims {in.e, L}, boxes of G columns x min(L, 256) rows.
+static bool encode_filter_map(PassDesc& d) {
+  const int L = 1 << d.logL;
+  if (!cols_filter_staged(d) || ((uintptr_t)d.h & 15)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)d.in.e, (cuuint64_t)L};
+  const cuuint64_t strides[1] = {(cuuint64_t)d.in.e * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)d.G, (cuuint32_t)(L < 256 ? L : 256)};
+  const cuuint32_t elem_strides[2] = {1, 1};
+  CUtensorMap m;
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<cf*>(d.h), dims, strides, box,
+          elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  memcpy(d.tmap_h, &m, sizeof(m));
+  return true;
+}
+
 bool encode_cols_maps(PassDesc& d, bool map_in, bool map_out, const void* in, void* out) {
   const int L = 1 << d.logL;
   d.tmap_in_ok = map_in && encode_cols_map(d, d.in, in, L < 256 ? L : 256, d.tmap_in);
   d.tmap_out_ok =
       map_out && encode_cols_map(d, d.out, out, L / 2 < 256 ? L / 2 : 256, d.tmap_out);
+  d.tmap_h_ok = map_in && d.tmap_in_ok && encode_filter_map(d);
   return d.tmap_in_ok || d.tmap_out_ok;
 }
 

@@ -382,6 +382,27 @@ __device__ __forceinline__ void tma_cols(cf* st, const PassDesc& d, int64_t tile
         : "memory");
 }
 
+// Fast convolution over column tiles (cols_filter_staged, d.tmap_h_ok): the
+// filters of the tile's G columns (all L rows) copied by tensor-map boxes over
+// h into `st`, in the data's interleaved layout; one arrival with the bytes.
+template <class SH>
+__device__ __forceinline__ void tma_filter(cf* st, const PassDesc& d, int64_t col0,
+                                           uint64_t* bar) {
+  constexpr int BR = SH::kL < 256 ? SH::kL : 256;
+  const uint32_t b = smem_u32(bar);
+  const uint64_t map = reinterpret_cast<uint64_t>(&d.tmap_h[0]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+               "r"((uint32_t)(SH::kL * SH::kG * 8))
+               : "memory");
+  for (int j = 0; j < SH::kL / BR; ++j)
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(st + j * BR * SH::kG)),
+        "l"(map), "r"((int32_t)col0), "r"(j * BR), "r"(b)
+        : "memory");
+}
+
 // Column tiles, tensor-map store of rows [0, L/2) of tile `tile` from xs (box
 // layout, SplitBody::store_half_smem) as boxes of min(L/2, 256) rows
 // (d.tmap_out).  Called by one thread after a barrier that follows every
@@ -418,28 +439,19 @@ __device__ __forceinline__ void store_cols_tma(const cf (&v)[SH::kR], const Pass
 }
 
 // HOLD: the exchanged stages' roots in `rt` were loaded before the first tile.
-template <class SH, int S, bool FIRST_EXCHANGE, bool HOLD>
-__device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
-                                               uint64_t* bar, const cf* in, int64_t next,
-                                               int tid,
-                                               typename SplitBody<SH, DevMem>::Roots& rt) {
+// `on_free` runs on every thread once every thread of the block has passed
+// the first barrier (so has read its stage-0 inputs from staging).
+template <class SH, int S, bool HOLD, class OnFree>
+__device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& d, cf* x, int tid,
+                                               typename SplitBody<SH, DevMem>::Roots& rt,
+                                               OnFree on_free) {
   using B = SplitBody<SH, DevMem>;
   auto& r = B::template roots_of<S>(rt);
   if constexpr (SH::kPowTw && !HOLD) B::template roots<S>(r, d, tid);
   if constexpr (SH::kPrefetchFused && S == SH::kExchanges - 1) B::fused_roots(rt.fr, d, tid);
   B::template write_half<S, 0>(v, x, tid);
   __syncthreads();
-  if (FIRST_EXCHANGE && next >= 0) {  // staging is free: every thread has read it
-    if constexpr (SH::kG == 1) {
-      if (tid == 0) tma_load(st, staged_src<SH>(in, d, next), SH::kL * 8, bar);
-    } else if constexpr (SH::kRowsIn) {
-      if (tid == 0) stage_rows<SH>(st, staged_src<SH>(in, d, next), bar);
-    } else if (d.tmap_in_ok) {
-      if (tid == 0) tma_cols<SH>(st, d, next, bar);
-    } else {
-      copy_rows<SH>(st, staged_src<SH>(in, d, next), d.in.e, bar, tid);
-    }
-  }
+  on_free();
   B::template read_half<S, 0>(v, x, tid);
   __syncthreads();
   B::template write_half<S, 1>(v, x, tid);
@@ -449,20 +461,39 @@ __device__ __forceinline__ void split_exchange(cf (&v)[SH::kR], const PassDesc& 
   __syncthreads();
 }
 
-// The exchanges after stages 0 .. kExchanges-1; the first one starts the
-// copy of tile `next` (if >= 0) into the staging buffer; unless HOLD, each
-// loads the twiddle roots of the stage after it into `rt`; the last one loads
-// those of a fused radix-2 last stage (SplitShape::kPrefetchFused).
-template <class SH, bool HOLD>
-__device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, cf* x, cf* st,
-                                            uint64_t* bar, const cf* in, int64_t next, int tid,
-                                            typename SplitBody<SH, DevMem>::Roots& rt) {
+struct NoOp {
+  __device__ void operator()() const {}
+};
+
+// The exchanges after stages 0 .. kExchanges-1; the first one runs
+// `on_free` (the copy of the next tile, or of the filters, into the staging
+// buffer) once staging has been read; unless HOLD, each loads the twiddle
+// roots of the stage after it into `rt`; the last one loads those of a fused
+// radix-2 last stage (SplitShape::kPrefetchFused).
+template <class SH, bool HOLD, class OnFree>
+__device__ __forceinline__ void split_round(cf (&v)[SH::kR], const PassDesc& d, cf* x, int tid,
+                                            typename SplitBody<SH, DevMem>::Roots& rt,
+                                            OnFree on_free) {
   static_assert(SH::kExchanges >= 1, "at least one exchange");
-  split_exchange<SH, 0, true, HOLD>(v, d, x, st, bar, in, next, tid, rt);
-  if constexpr (SH::kExchanges > 1)
-    split_exchange<SH, 1, false, HOLD>(v, d, x, st, bar, in, -1, tid, rt);
-  if constexpr (SH::kExchanges > 2)
-    split_exchange<SH, 2, false, HOLD>(v, d, x, st, bar, in, -1, tid, rt);
+  split_exchange<SH, 0, HOLD>(v, d, x, tid, rt, on_free);
+  if constexpr (SH::kExchanges > 1) split_exchange<SH, 1, HOLD>(v, d, x, tid, rt, NoOp{});
+  if constexpr (SH::kExchanges > 2) split_exchange<SH, 2, HOLD>(v, d, x, tid, rt, NoOp{});
+}
+
+// Start the copy of tile `t` into the staging buffer (one contiguous
+// transform, G rows, or G columns by tensor-map boxes or row copies).
+template <class SH>
+__device__ __forceinline__ void stage_tile(cf* st, const cf* in, const PassDesc& d, int64_t t,
+                                           uint64_t* bar, int tid) {
+  if constexpr (SH::kG == 1) {
+    if (tid == 0) tma_load(st, staged_src<SH>(in, d, t), SH::kL * 8, bar);
+  } else if constexpr (SH::kRowsIn) {
+    if (tid == 0) stage_rows<SH>(st, staged_src<SH>(in, d, t), bar);
+  } else if (d.tmap_in_ok) {
+    if (tid == 0) tma_cols<SH>(st, d, t, bar);
+  } else {
+    copy_rows<SH>(st, staged_src<SH>(in, d, t), d.in.e, bar, tid);
+  }
 }
 
 // One tile per block (a contiguous transform, or G adjacent columns of a
@@ -487,17 +518,7 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
   const bool one_arrival = SH::kG == 1 || SH::kRowsIn || d.tmap_in_ok;
   if (tid == 0) mbar_init(bar, one_arrival ? 1 : SH::kT);
   __syncthreads();
-  if (tile < d.tiles) {  // uniform over the block
-    if constexpr (SH::kG == 1) {
-      if (tid == 0) tma_load(st, in + tile * SH::kL, SH::kL * 8, bar);
-    } else if constexpr (SH::kRowsIn) {
-      if (tid == 0) stage_rows<SH>(st, staged_src<SH>(in, d, tile), bar);
-    } else if (d.tmap_in_ok) {
-      if (tid == 0) tma_cols<SH>(st, d, tile, bar);
-    } else {
-      copy_rows<SH>(st, staged_src<SH>(in, d, tile), d.in.e, bar, tid);
-    }
-  }
+  if (tile < d.tiles) stage_tile<SH>(st, in, d, tile, bar, tid);  // uniform over the block
   // twiddle roots: loaded once here (kHold, kHoldFused) or per tile
   constexpr bool kHold = SH::kHoldRoots && !CONV;
   constexpr bool kHoldFused = SH::kHoldFused && !CONV;
@@ -525,10 +546,6 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
     }
     parity ^= 1u;
     const int64_t next = tile + step < d.tiles ? tile + step : -1;
-    cf v[SH::kR];
-    if (d.conj_in) B::template first<true>(v, st, tid);
-    else B::template first<false>(v, st, tid);
-    split_round<SH, kHold>(v, d, x, st, bar, in, next, tid, rt);
     cf* o;
     int64_t col0;  // G == 1: the line (tile); else the first column of the tile
     if constexpr (SH::kG == 1) {
@@ -539,11 +556,47 @@ stockham_staged(const cf* __restrict__ in, cf* out, const __grid_constant__ Pass
       o = out + outer * d.out.o + inner * d.out.t;
       col0 = inner * SH::kG;
     }
+    // a convolution over column tiles with per-line filters stages the tile's
+    // filters once the data has been read, and the next tile once the
+    // filters have (its copy then overlaps the second round only)
+    const bool fstage = CONV && SH::kG > 1 && d.tmap_h_ok && d.tmap_in_ok;
+    cf v[SH::kR];
+    if (d.conj_in) B::template first<true>(v, st, tid);
+    else B::template first<false>(v, st, tid);
+    split_round<SH, kHold>(v, d, x, tid, rt, [&] {
+      if (fstage) {
+        if (tid == 0) tma_filter<SH>(st, d, col0, bar);
+      } else if (next >= 0) {
+        stage_tile<SH>(st, in, d, next, bar, tid);  // staging has been read
+      }
+    });
     if constexpr (CONV) {
-      B::conv_middle(v, d, col0, tid);
-      split_round<SH, kHold>(v, d, x, st, bar, in, -1, tid, rt);
-      if constexpr (SH::kFuseLast) B::template store_fused<true, kFrReady>(v, d, o, col0, tid, rt.fr);
-      else B::template store<true>(v, d, o, col0, tid);
+      if (fstage) {
+        const bool fok = mbar_wait(bar, parity, kWaitPolls);
+        if (__syncthreads_or(!fok)) {
+          if (tid == 0) {
+            atomicExch(d.status, 1);
+            mbar_wait(bar, parity, kWaitPolls);  // let the copy in flight land before leaving
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+          }
+          return;
+        }
+        parity ^= 1u;
+        B::conv_middle(v, d, col0, tid, st);
+        split_round<SH, kHold>(v, d, x, tid, rt, [&] {
+          if (next >= 0) stage_tile<SH>(st, in, d, next, bar, tid);  // the filters have been read
+        });
+      } else {
+        B::conv_middle(v, d, col0, tid);
+        split_round<SH, kHold>(v, d, x, tid, rt, NoOp{});
+      }
+      if constexpr (SH::kFuseLast) {
+        B::template store_fused<true, kFrReady>(v, d, o, col0, tid, rt.fr);
+      } else if (SH::kG > 1 && d.tmap_out_ok) {
+        if constexpr (SH::kG > 1) store_cols_tma<SH, true>(v, d, x, o, tile, col0, tid);
+      } else {
+        B::template store<true>(v, d, o, col0, tid);
+      }
     } else if constexpr (SH::kFuseLast) {
       if (d.conj_out) B::template store_fused<true, kFrReady>(v, d, o, col0, tid, rt.fr);
       else B::template store_fused<false, kFrReady>(v, d, o, col0, tid, rt.fr);

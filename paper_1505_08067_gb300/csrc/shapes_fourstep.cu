@@ -18,7 +18,7 @@ bool resolve_staged_cols_shape(const PassDesc& d, int lmap, int smap, StagedLaun
 #define GB_STAGED_COLS(LOGL, SCHED, NST, RR, G, EPI, CONV)                         \
   if (staged_cols_matches(d, lmap, smap, LOGL, SCHED, NST, G, EPI, CONV)) {         \
     using SH = SplitShape<LOGL, SCHED, NST, RR, G, EPI>;                           \
-    s->fn = (const void*)staged_fn<SH, (SH::kT <= 256 ? 2 : 1), false>();                                \
+    s->fn = (const void*)staged_fn<SH, (SH::kT <= 256 ? 2 : 1), CONV != 0>();                           \
     s->block = SH::kT;                                                             \
     s->smem = split_smem_bytes<SH>();                                              \
     return true;                                                                   \

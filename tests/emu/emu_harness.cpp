@@ -329,15 +329,35 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
     };
     round();
     cf* o = out + dst;
+    bool conv_swap = false;
     if constexpr (CONV) {
-      for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, col0, t);
-      round();
-      for (int t = 0; t < SH::kT; ++t) {
-        if constexpr (SH::kFuseLast) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true, true>(reg(t), d, o, col0, t, fr); }
-        else B::template store<true>(reg(t), d, o, col0, t);
+      // column tiles with per-column filters: the tile's filters are copied
+      // into the staging buffer by tensor-map boxes over h (element (a, g) at
+      // row a, column col0 + g of the filter frame, inside its {in.e, L}
+      // extent), as the kernel does when its filter map encodes
+      const bool fstage = SH::kG > 1 && cols_filter_staged(d) && use_map;
+      if (fstage) {
+        for (int a = 0; a < SH::kL; ++a)
+          for (int c = 0; c < SH::kG; ++c) {
+            const int64_t col = col0 + c;
+            if (col >= d.in.e || col0 % 2) err("filter box outside the filter frame", col);
+            const int64_t hi = (int64_t)a * d.in.e + col;
+            if (hi < 0 || hi >= g.h_len) { err("filter load out of bounds", hi); continue; }
+            st[a * SH::kG + c] = g.h[hi];
+          }
       }
-      continue;
+      for (int t = 0; t < SH::kT; ++t) B::conv_middle(reg(t), d, col0, t, fstage ? st.data() : nullptr);
+      round();
+      if constexpr (SH::kG == 1 || SH::kFuseLast) {
+        for (int t = 0; t < SH::kT; ++t) {
+          if constexpr (SH::kFuseLast) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true, true>(reg(t), d, o, col0, t, fr); }
+          else B::template store<true>(reg(t), d, o, col0, t);
+        }
+        continue;
+      }
+      conv_swap = true;
     }
+    const bool swap_out = conv_swap || d.conj_out;
     // column tiles the GPU writes half by tensor-map box stores: rows
     // [0, L/2) go to the exchange buffer in the box layout (every slot
     // written once), then box element (a, c) to row y + a, column x + c of the
@@ -350,7 +370,7 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
         tma_tile_coords(d, d.out, tile, ox, oy);
         ++g.epoch;
         for (int t = 0; t < SH::kT; ++t) {
-          if (d.conj_out) B::template store_half_smem<true, 0>(reg(t), d, x.data(), col0, t);
+          if (swap_out) B::template store_half_smem<true, 0>(reg(t), d, x.data(), col0, t);
           else B::template store_half_smem<false, 0>(reg(t), d, x.data(), col0, t);
         }
         for (int a = 0; a < SH::kL / 2; ++a)
@@ -364,7 +384,7 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
             CheckMem::stg(out, row * d.out.e + col, x[slot]);
           }
         for (int t = 0; t < SH::kT; ++t) {
-          if (d.conj_out) B::template store_half<true, 1>(reg(t), d, o, col0, t);
+          if (swap_out) B::template store_half<true, 1>(reg(t), d, o, col0, t);
           else B::template store_half<false, 1>(reg(t), d, o, col0, t);
         }
         continue;
@@ -372,10 +392,10 @@ void run_staged_t(const PassDesc& d, const cf* in, cf* out) {
     }
     for (int t = 0; t < SH::kT; ++t) {
       if constexpr (SH::kFuseLast) {
-        if (d.conj_out) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true, true>(reg(t), d, o, col0, t, fr); }
+        if (swap_out) { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<true, true>(reg(t), d, o, col0, t, fr); }
         else { cf fr[16]; B::fused_roots(fr, d, t); B::template store_fused<false, true>(reg(t), d, o, col0, t, fr); }
       } else {
-        if (d.conj_out) B::template store<true>(reg(t), d, o, col0, t);
+        if (swap_out) B::template store<true>(reg(t), d, o, col0, t);
         else B::template store<false>(reg(t), d, o, col0, t);
       }
     }
@@ -781,6 +801,9 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
       const bool want_staged = p.variant == 0 || p.variant == 2;
       if (specialised && !s.generic_only && want_staged && p.lmap == MAP_ROWS &&
           run_conv_staged(d, src, dst))
+        ++g.staged_passes;
+      else if (specialised && !s.generic_only && want_staged && p.lmap == MAP_COLS &&
+               cols_filter_staged(d) && run_staged_cols(p.lmap, p.smap, d, src, dst))
         ++g.staged_passes;
       else if (specialised && !s.generic_only && run_conv_special(p.R, p.lmap, d, src, dst)) ++g.special_passes;
       else if (p.lmap == MAP_ROWS) run_conv_maps<0>(p.R, d, src, dst);

@@ -100,6 +100,44 @@ def test_conv_prefetch_variant(gb, oracle, shape, batch, per_line):
     _check(gb, oracle, shape, batch, per_line, variant=3)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_conv_azimuth_staged_filters(gb, oracle, variant):
+    """4096-row frames with one filter per column: the staged column kernel
+    copies each tile's filters into shared memory after its data (variant 0;
+    the first pass's kernel kind is reported as staged), the register kernel
+    reads them from global memory (variant 1); both against the oracle, in
+    place and from a replayed graph too."""
+    desc = _check(gb, oracle, (4096, 64), 3, (True, False), variant=variant)
+    kinds = [k["kernel"] for k in desc["kernels"]]
+    assert kinds[1] == ("staged" if variant == 0 else "compile_time"), kinds
+    _check(gb, oracle, (4096, 32), 2, (True, True), variant=variant, in_place=True)
+    _check(gb, oracle, (4096, 16), 1, (True, False), variant=variant, graph=True)
+
+
+def test_conv_azimuth_filter_not_16_byte_aligned(gb, oracle):
+    """A per-column filter frame that starts 8 bytes off a 16-byte boundary
+    cannot be copied by tensor-map boxes: the staged kernel reads it from
+    global memory instead, with the same result."""
+    rows, cols, batch = 4096, 32, 2
+    x = synth.uniform(77, batch, rows * cols).reshape(batch, rows, cols)
+    filters = _filters(oracle, (rows, cols), batch, (True, False), 177)
+    ref = _reference(oracle, x, (rows, cols), filters)
+    xt = torch.from_numpy(x).cuda()
+    ha = torch.from_numpy(np.ascontiguousarray(filters[0][0]).reshape(-1)).cuda()
+    hbuf = torch.zeros(ha.numel() + 1, dtype=torch.complex64, device="cuda")
+    hbuf[1:].copy_(ha)
+    hr = torch.from_numpy(np.ascontiguousarray(filters[1][0])).cuda()
+    outs = []
+    for h in (ha, hbuf[1:]):
+        with gb.ConvPlan((rows, cols), batch, [(h, cols, filters[0][2]), (hr, 1, filters[1][2])]) as p:
+            y = p.execute(xt)
+            torch.cuda.synchronize()
+        outs.append(y)
+        err = oracle.rel_l2(y.cpu().numpy().reshape(batch, -1), ref.reshape(batch, -1))
+        assert np.max(err) <= _tol(rows), float(np.max(err))
+    assert torch.allclose(outs[0], outs[1], rtol=0, atol=1e-5 * float(torch.max(torch.abs(outs[0]))))
+
+
 def test_conv_in_place_and_graph(gb, oracle):
     _check(gb, oracle, (256, 512), 2, (True, False), in_place=True)
     _check(gb, oracle, (1024,), 33, (True, False), graph=True)

@@ -218,11 +218,21 @@ def test_conv_frames(oracle, shape, per_line):
     _check_conv(oracle, shape, 2, per_line)
 
 
-def test_conv_azimuth_shape(oracle):
-    """4096-point columns (4 per tile) run the compile-time register
+@pytest.mark.parametrize("cols", [8, 16])
+def test_conv_azimuth_shape(oracle, cols):
+    """4096-point columns (4 per tile) with one filter per column run the
+    staged column kernel: each tile's filters are copied into the staging
+    buffer by tensor-map boxes once its data has been read.  With one shared
+    filter, or with variant 1, they run the compile-time register
     convolution kernel."""
     st = {}
-    _check_conv(oracle, (4096, 8), 2, (True, False), stats=st, expect_special=1)
+    _check_conv(oracle, (4096, cols), 2, (True, False), stats=st, expect_special=0)
+    assert st["staged_passes"] == 1
+    st = {}
+    _check_conv(oracle, (4096, cols), 2, (False, False), stats=st, expect_special=1)
+    assert st["staged_passes"] == 0
+    st = {}
+    _check_conv(oracle, (4096, cols), 2, (True, False), stats=st, expect_special=1, variant=1)
     assert st["staged_passes"] == 0
 
 
