@@ -287,10 +287,10 @@ GB_UNROLL
   // positions t + (q + i*NB)*T, runs on the registers: no exchange between
   // the rounds.  `line`: the tile (contiguous lines) or its first column
   // (column tiles: line line + g for transform g) selects the filter
-  // (PassDesc::h_lines).  `fst` (column tiles with per-line filters whose
-  // tile cols_filter_staged() allows): the tile's filters staged in shared
-  // memory like the data (position a of column g at a*G + g); else the
-  // filter is read from global memory.
+  // (PassDesc::h_lines).  `fst` (column tiles whose filters are staged,
+  // PassDesc::tmap_h_ok): the tile's filters in shared memory like the data
+  // (position a of column g at a*G + g); else (null) the filter is read from
+  // global memory.
   GB_HD static void conv_middle(cf (&v)[R], const PassDesc& d, int64_t line, int tid,
                                 const cf* fst = nullptr) {
     constexpr int NB = SH::kNB;
@@ -323,7 +323,7 @@ GB_UNROLL
         for (int i = 0; i < 16; ++i) y[q + i * NB] = v[q * 16 + i];
     }
     const float sc = d.h_scale;
-    if (G > 1 && fst) {
+    if (fst) {
 GB_UNROLL
       for (int m = 0; m < R; ++m) {
         const cf z = cmul(y[m], Mem::lds(fst, (t + m * T) * G + g));

@@ -181,15 +181,12 @@ cudaError_t launch_staged(const StagedLaunch& s, const PassDesc& d, const void* 
                           cudaStream_t st) {
   KernelFn k = reinterpret_cast<KernelFn>(const_cast<void*>(s.fn));
   if (!k || s.grid < 1) return cudaErrorInvalidValue;
+  PassDesc dm = d;
   if (s.tmap && (s.map_in || s.map_out)) {
-    PassDesc dm = d;
     const bool mo = s.map_out && cols_store_map(d);
-    if (encode_cols_maps(dm, s.map_in, mo, in, out)) {
-      k<<<s.grid, s.block, s.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), dm);
-      return cudaGetLastError();
-    }
+    encode_cols_maps(dm, s.map_in, mo, in, out);
   }
-  k<<<s.grid, s.block, s.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), d);
+  k<<<s.grid, s.block, s.smem, st>>>(static_cast<const cf*>(in), static_cast<cf*>(out), dm);
   return cudaGetLastError();
 }
 
