@@ -748,7 +748,7 @@ def section_compress(args) -> dict:
         "steps": args.steps, "warmup": args.warmup, "ms_per_frame": ms_full,
         "frames_per_s": 1e3 / ms_full, "gflops": flops / (ms_full * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                     "kernel": "stockham_conv (azimuth pass)", "achieved": round(g_az, 1),
+                     "kernel": "stockham_staged, convolution form (azimuth pass)", "achieved": round(g_az, 1),
                      "frac": round(g_az / peaks["hbm_gbs"], 4), "alg_bytes_per_launch": 24.0 * E},
         "passes": {"range": {"ms": round(ms_rng, 4), "gbs": round(g_rng, 1),
                              "frac": round(g_rng / peaks["hbm_gbs"], 4), "alg_bytes": 16.0 * E},
