@@ -33,9 +33,24 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libgbfft.so")
 
 
+def build_id() -> str:
+    """Hash of the library's sources and header: the autotune results kept in
+    a GBFFT_WISDOM file are keyed by it, so a changed library tunes again."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    with open(os.path.join(ROOT, "include", "gbfft.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def _flags(src: str) -> list[str]:
     f = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
                 "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+    if src == "autotune.cpp":
+        f.append(f'-DGBFFT_BUILD_ID="{build_id()}"')
     if src.endswith(".cu"):
         f += ["-Xptxas", "-warn-spills"]
     else:

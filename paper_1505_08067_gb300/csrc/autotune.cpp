@@ -16,7 +16,8 @@
 //                N = N1 * N2 split and the source of the four-step twiddle.
 //
 // The fastest candidate's options are kept (per device, shape and direction),
-// in memory and, if GBFFT_WISDOM names a file, on disk.
+// in memory and, if GBFFT_WISDOM names a file, on disk.  GBFFT_BUILD_ID (set by
+// the build: a hash of the library's sources) is part of every key.
 #include "autotune.h"
 
 #include <cuda_runtime.h>
@@ -33,6 +34,10 @@
 
 #include "exec.h"
 #include "kernels.h"
+
+#ifndef GBFFT_BUILD_ID
+#define GBFFT_BUILD_ID "unversioned"
+#endif
 
 namespace gbfft {
 
@@ -234,10 +239,14 @@ fft_status_t autotune_options(const int64_t* n, int dims, int64_t batch, int dir
     cudaGetLastError();
     return set_error(FFT_ERR_CUDA, "autotune: cudaGetDeviceProperties failed");
   }
+  // keyed by the library build, the driver, the device and the shape: a
+  // result tuned by another build or driver is not reused
+  int driver = 0;
+  if (cudaDriverGetVersion(&driver) != cudaSuccess) cudaGetLastError();
   char keybuf[256];
-  snprintf(keybuf, sizeof keybuf, "%s/%d %d %lld %lld %lld %d %s", prop.name,
-           prop.multiProcessorCount, dims, (long long)n[0], (long long)(dims > 1 ? n[1] : 1),
-           (long long)batch, direction, opts_key(b).c_str());
+  snprintf(keybuf, sizeof keybuf, "%s/%d/%s/%d %d %lld %lld %lld %d %s", GBFFT_BUILD_ID, driver,
+           prop.name, prop.multiProcessorCount, dims, (long long)n[0],
+           (long long)(dims > 1 ? n[1] : 1), (long long)batch, direction, opts_key(b).c_str());
   const std::string key = keybuf;
   std::lock_guard<std::mutex> lock(g_mu);
   load_wisdom();

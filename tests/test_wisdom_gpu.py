@@ -52,3 +52,8 @@ def test_wisdom_file_written_and_read_back(tmp_path):
         a, b = first[n]["checksum"], second[n]["checksum"]
         assert abs(a[0] - b[0]) <= 1e-5 * abs(a[0]) and abs(a[1] - b[1]) <= 1e-4 * abs(a[0])
     assert path.read_text().splitlines() == lines      # nothing tuned twice
+    # entries keyed by another build of the library are not reused
+    path.write_text("".join("stale-build/" + ln.split("/", 1)[1] + "\n" for ln in lines))
+    third = _child(env)
+    for n in ("1024", str(2 ** 20)):
+        assert "candidates" in third[n]["tuning"], third[n]["tuning"]
