@@ -15,6 +15,7 @@
 #include "exec.h"
 #include "kernels.h"
 #include "planner.h"
+#include "trace.h"
 
 using namespace gbfft;
 
@@ -165,11 +166,13 @@ extern "C" {
 
 fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
                              int direction, int precision) {
+  TraceRange r("fft_plan_create");
   return build_plan(plan, n, dims, batch, direction, precision, nullptr);
 }
 
 fft_status_t fft_plan_create_ex(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
                                 int direction, int precision, const fft_plan_options_t* options) {
+  TraceRange r("fft_plan_create");
   return build_plan(plan, n, dims, batch, direction, precision, options);
 }
 
@@ -179,6 +182,7 @@ static bool aligned_io(const PlanSpec& s, const void* p) {
 }
 
 fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* stream) {
+  TraceRange r("fft_execute");
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
   if (plan->spec.batch == 0) return FFT_OK;
   if (!in || !out) return fail(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
@@ -199,6 +203,7 @@ fft_status_t fft_execute(fft_plan_t plan, const void* in, void* out, void* strea
 
 fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_out, void* dev_in,
                               void* dev_out, void* stream) {
+  TraceRange r("fft_execute_host");
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
   const PlanSpec& s = plan->spec;
   if (s.batch == 0) return FFT_OK;
@@ -263,6 +268,7 @@ fft_status_t fft_execute_host(fft_plan_t plan, const void* host_in, void* host_o
 }
 
 fft_status_t fft_execute_graph(fft_plan_t plan, const void* in, void* out, void* stream) {
+  TraceRange r("fft_execute_graph");
   if (!plan_ok(plan)) return fail(FFT_ERR_BAD_PLAN, "null or destroyed plan");
   if (plan->spec.batch == 0) return FFT_OK;
   if (!in || !out) return fail(FFT_ERR_INVALID_ARG, "in/out must be device pointers");
@@ -436,6 +442,7 @@ static fft_status_t conv_spec(const fft_filter_t* filters, int dims, bool need_p
 
 fft_status_t fft_conv_plan_create(fft_plan_t* plan, const int64_t* n, int dims, int64_t batch,
                                   const fft_filter_t* filters, const fft_plan_options_t* options) {
+  TraceRange r("fft_conv_plan_create");
   if (!plan) return fail(FFT_ERR_INVALID_ARG, "plan output pointer is null");
   *plan = nullptr;
   ConvSpec cs;

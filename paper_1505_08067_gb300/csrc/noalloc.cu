@@ -27,6 +27,7 @@
 
 #include "../../include/gbfft.h"
 #include "exec.h"
+#include "trace.h"
 
 namespace gbfft {
 fft_status_t set_error(fft_status_t st, const char* msg);
@@ -85,6 +86,7 @@ fft_status_t scratch_address(DeviceState& ds) {
 
 extern "C" fft_status_t fft_execute_noalloc(int64_t n, int64_t batch, int direction,
                                             const void* in, void* out, void* stream) {
+  TraceRange trace("fft_execute_noalloc");
   if (n < 1 || (n & (n - 1)) || n > kWorkElems)
     return set_error(FFT_ERR_UNSUPPORTED_SIZE,
                      "fft_execute_noalloc: n must be a power of two between 1 and 2^23");

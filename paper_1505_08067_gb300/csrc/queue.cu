@@ -35,6 +35,7 @@
 #include "kernels_impl.cuh"
 #include "planner.h"
 #include "queue_ring.h"
+#include "trace.h"
 
 namespace gbfft {
 fft_status_t set_error(fft_status_t st, const char* msg);
@@ -401,6 +402,7 @@ fft_status_t fft_queue_create(fft_queue_t* queue, int64_t n, int64_t max_batch, 
 
 fft_status_t fft_queue_submit(fft_queue_t q, const void* in, void* out, int64_t batch,
                               uint64_t* ticket) {
+  TraceRange trace("fft_queue_submit");
   if (!queue_ok(q)) return set_error(FFT_ERR_BAD_PLAN, "null or destroyed queue");
   if (!ticket) return set_error(FFT_ERR_INVALID_ARG, "ticket output pointer is null");
   if (!in || !out) return set_error(FFT_ERR_INVALID_ARG, "in/out must be device pointers");

@@ -35,6 +35,7 @@
 #include "kernels.h"
 #include "planner.h"
 #include "scheduler.h"
+#include "trace.h"
 
 namespace gbfft {
 fft_status_t set_error(fft_status_t st, const char* msg);
@@ -252,6 +253,7 @@ bool launch_group(fft_server_t s, Running& r) {
   r.done = s->free_events.back().second;
   s->free_events.pop_back();
   cudaEventRecord(r.start, st);
+  TraceRange trace("fft_server launch group");
   cudaError_t e = cudaSuccess;
   if (pe->groupable && g.jobs.size() > 1) {
     // one coalesced launch per kMaxGroup jobs
@@ -444,6 +446,7 @@ fft_status_t fft_server_create(fft_server_t* server, const fft_server_options_t*
 }
 
 fft_status_t fft_server_submit(fft_server_t s, const fft_job_t* job, uint64_t* ticket) {
+  TraceRange trace("fft_server_submit");
   if (!server_ok(s)) return set_error(FFT_ERR_BAD_PLAN, "null or destroyed server");
   if (!job || !ticket) return set_error(FFT_ERR_INVALID_ARG, "job and ticket are required");
   // validate the shape with the planner (host only)
