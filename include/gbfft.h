@@ -487,6 +487,18 @@ GBFFT_API fft_status_t fft_fill_uniform(void* out, int64_t count, uint64_t seed,
 /* Message of the last failure on the calling thread ("" if none). */
 GBFFT_API const char* fft_last_error(void);
 
+/* Diagnostic of the device-side bounded waits.  Every wait in the library's
+ * kernels (the staged kernels' and the tensor-core kernel's waits on an
+ * mbarrier, the work queue's polls) gives up after a fixed number of polls,
+ * sets a status word and returns instead of hanging.  This call runs that
+ * wait where it must run out: one block whose threads wait on an mbarrier
+ * that nothing completes, with the library's wait loop limited to `polls`
+ * polls (1 .. 2^22; 2^22 is the limit the kernels use, about 0.5 s), then
+ * reads the status word back.  *gave_up = 1 is the expected result; the call
+ * synchronises the current device and leaves it usable.  FFT_ERR_INVALID_ARG
+ * for polls outside that range or a null gave_up; FFT_ERR_CUDA if no device. */
+GBFFT_API fft_status_t fft_wait_selftest(uint32_t polls, int* gave_up);
+
 /* ------------------------------------------------ schedule model (host) --
  * Sec. 3.2 "FFT performance model": a radix schedule for N = 2^L is a path in
  * the digraph whose nodes are stage indices 0..L and whose edge s -> s+log2(r)

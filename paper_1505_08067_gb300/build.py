@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libgbfft.so")
 MEASURE = os.path.join(HERE, "measure")
 CALL_LATENCY = os.path.join(OUT_DIR, "call_latency")  # C-side per-call timing of the ABI
 SOURCES = ["kernels.cu", "generic_rows.cu", "generic_cols.cu", "generic_transposing.cu",
-           "shapes_contig.cu", "shapes_fourstep.cu", "kernels_tc.cu", "kernels_umma.cu", "kernels_umma_c32.cu", "fill.cu", "conv.cu", "noalloc.cu", "queue.cu", "transpose.cu", "api.cpp",
+           "shapes_contig.cu", "shapes_fourstep.cu", "kernels_tc.cu", "kernels_umma.cu", "kernels_umma_c32.cu", "fill.cu", "conv.cu", "noalloc.cu", "queue.cu", "transpose.cu", "selftest.cu", "api.cpp",
            "exec.cpp", "server.cpp",
            "planner.cpp", "autotune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

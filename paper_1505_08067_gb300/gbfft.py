@@ -99,6 +99,7 @@ _SIGS = {
     "fft_execute_graph": [_vp, _vp, _vp, _vp],
     "fft_execute_noalloc": [_i64, _i64, ctypes.c_int, _vp, _vp, _vp],
     "fft_fill_uniform": [_vp, _i64, ctypes.c_uint64, ctypes.c_uint64, _vp],
+    "fft_wait_selftest": [ctypes.c_uint32, ctypes.POINTER(ctypes.c_int)],
     "fft_plan_destroy": [_vp],
     "fft_plan_workspace_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "fft_plan_launch_count": [_vp, ctypes.POINTER(ctypes.c_int)],
@@ -280,6 +281,14 @@ def fft_fill_uniform(out_ptr: int, count: int, seed: int, first: int = 0, stream
     sequence (synth.uniform_hash computes the same values on the host)."""
     _check(load().fft_fill_uniform(out_ptr, int(count), int(seed) & (2 ** 64 - 1),
                                    int(first), stream))
+
+
+def fft_wait_selftest(polls: int) -> int:
+    """Run the kernels' bounded mbarrier wait on a barrier nothing completes,
+    limited to `polls` polls; 1 if it gave up (the expected result)."""
+    g = ctypes.c_int(0)
+    _check(load().fft_wait_selftest(ctypes.c_uint32(int(polls) & 0xFFFFFFFF), ctypes.byref(g)))
+    return g.value
 
 
 def fft_plan_destroy(plan: int) -> None:

@@ -45,6 +45,12 @@ def test_no_gpu_means_error_not_fallback():
         with pytest.raises(g.GbfftError) as e:
             g.Queue(n, 64)
         assert e.value.status == st
+    # the bounded-wait diagnostic: argument errors first, then no device
+    for polls, st in ((0, g.FFT_ERR_INVALID_ARG), (2 ** 22 + 1, g.FFT_ERR_INVALID_ARG),
+                      (64, g.FFT_ERR_CUDA)):
+        with pytest.raises(g.GbfftError) as e:
+            g.fft_wait_selftest(polls)
+        assert e.value.status == st
 
 
 @pytest.mark.parametrize("n,batch,status", [
