@@ -413,19 +413,23 @@ GB_UNROLL
     int g, t;
     coords(tid, g, t);
     const int col = (int)col0 + g;
-    // factored four-step twiddle: w_N^{col (jb + i Ns)} = w_N^{col jb} (w_N^{col Ns})^i
-    cf pw[RR];
+    // factored four-step twiddle: with jb = t + q T,
+    //   w_N^{col (jb + i Ns)} = w_N^{col t} (w_N^{col T})^q (w_N^{col Ns})^i:
+    // three sincospi per call (the first two and the step of the third), the
+    // rest by products (a butterfly's base after at most NB - 1 of them)
+    cf pw[RR], base = mk(1.f, 0.f), qstep = mk(1.f, 0.f);
     if constexpr (SH::kEpi == 4) {
       pw[0] = mk(1.f, 0.f);
       pw[1] = Mem::rotor(col * (int64_t)Ns, d.epi_logN);  // col*Ns < N
 GB_UNROLL
       for (int i = 2; i < RR; ++i) pw[i] = cmul(pw[i / 2], pw[i - i / 2]);
+      base = Mem::rotor(col * (int64_t)t, d.epi_logN);  // col*t < N
+      if (NB > 1) qstep = Mem::rotor(col * (int64_t)T, d.epi_logN);  // col*T < N
     }
 GB_UNROLL
     for (int q = 0; q < NB; ++q) {
       const int jb = q * T + t;
-      cf base = mk(1.f, 0.f);
-      if constexpr (SH::kEpi == 4) base = Mem::rotor(col * (int64_t)jb, d.epi_logN);
+      if (SH::kEpi == 4 && q > 0) base = cmul(base, qstep);
 GB_UNROLL
       for (int i = I0; i < I1; ++i) {
         cf x = v[q * RR + i];
