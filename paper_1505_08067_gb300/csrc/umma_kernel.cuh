@@ -13,8 +13,8 @@
 //            16-byte-aligned input are read from a staging buffer in shared
 //            memory, which a
 //            bulk copy (TMA) fills with the CTA's next tile while this one
-//            goes through its stages; the others from global memory, the
-//            next tile prefetched into L2;
+//            goes through its stages; the others from global memory (the
+//            next tile prefetched into L2 where that measured faster);
 //   stage t  thread 0 issues the UMMAs of the stage (T/2048 row blocks x 2
 //            K halves; x3 for the split-BF16 class) and commits them to an
 //            mbarrier; all threads wait (bounded), each warp reads its rows
@@ -323,8 +323,14 @@ stockham_umma(const cf* __restrict__ in, cf* out, const __grid_constant__ PassDe
     const cf* gin = Mem::at(in, first * G::L);
     cf* gout = Mem::at(out, first * G::L);
     // the tile this CTA takes next, into L2 while this one is computed
-    // (whole 16-byte units inside the tile only; none for a ragged tile)
-    if (!staged && tid == 0 && tile + gridDim.x < d.tiles) {
+    // (whole 16-byte units inside the tile only; none for a ragged tile).
+    // Measured per form: it pays for complex32 storage, for tiles of 4096
+    // elements and for the split class at 2^13; for complex64 FP16 / BF16 at
+    // 2^13 and 2^14 and the split class at 2^14 it costs 5-18% (at 2^14 with
+    // it, DRAM reads were 17% above the tile bytes: prefetched lines read
+    // again).
+    constexpr bool kPrefetchL2 = H || LOGL < 13 || (U::SPLIT && LOGL == 13);
+    if (kPrefetchL2 && !staged && tid == 0 && tile + gridDim.x < d.tiles) {
       const int64_t nfirst = (tile + gridDim.x) * G::TPT;
       if (nfirst + G::TPT <= d.count_inner) {
         const uintptr_t a = reinterpret_cast<uintptr_t>(Mem::at(in, nfirst * G::L));
