@@ -11,10 +11,10 @@
 //            FP16/BF16 and stores the stage-0 A operand in shared memory.
 //            Tiles of 4096 elements (L <= 2^12; not the split class) from a
 //            16-byte-aligned input are read from a staging buffer in shared
-//            memory, which a
-//            bulk copy (TMA) fills with the CTA's next tile while this one
-//            goes through its stages; the others from global memory (the
-//            next tile prefetched into L2 where that measured faster);
+//            memory, which a bulk copy (TMA) fills with the CTA's next tile
+//            while this one goes through its stages; the others from global
+//            memory (the next tile prefetched into L2 where that measured
+//            faster);
 //   stage t  thread 0 issues the UMMAs of the stage (T/2048 row blocks x 2
 //            K halves; x3 for the split-BF16 class) and commits them to an
 //            mbarrier; all threads wait (bounded), each warp reads its rows
@@ -27,7 +27,8 @@
 // stage overwrites the accumulators.
 //
 // Every wait is bounded: a give-up sets the pass's status word, waits (again
-// bounded) for the UMMAs in flight, frees the tensor memory and returns.
+// bounded) for the UMMAs and the staging copy in flight, frees the tensor
+// memory and returns.
 //
 // Input and output are complex64, or complex32 (FP16 re, im; 4 bytes per
 // element) when the kernel's H parameter is set: the loader widens each FP16
