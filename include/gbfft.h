@@ -132,7 +132,9 @@ GBFFT_API fft_status_t fft_plan_create(fft_plan_t* plan, const int64_t* n, int d
  *                 where a compile-time specialisation of the shape exists.
  *   variant       kernel variant: 0 library choice, 1 register kernel (one
  *                 tile per block), 2 TMA-staged kernel (batched contiguous
- *                 N = 2^12..2^14: the next transform is copied into shared
+ *                 N = 2^12..2^14, where the library's own choice is the
+ *                 staged kernel for 2^13 and 2^14 and the register kernel
+ *                 for 2^12: the next transform is copied into shared
  *                 memory while the current one is computed), 3 register
  *                 kernel on a persistent grid that prefetches its next tile
  *                 into L2 (every pass with a compile-time shape: contiguous

@@ -55,7 +55,14 @@ cudaError_t bind_launches(const PlanSpec& s, const Caps& caps, const cf* tables,
         launches[i] = l;
         continue;
       }
-      const bool want_staged = p.variant == 0 || p.variant == 2 || p.variant == 4;
+      // the library's choice for contiguous FP32 transforms of 2^12 is the
+      // register kernel (0.320 against 0.335 ms per 2^27 elements for the
+      // staged one, the choice the autotuner makes in every measured run);
+      // variant 2 still asks for the staged kernel
+      const bool reg4096 = p.variant == 0 && !p.conv && !p.tc_prec && p.logL == 12 &&
+                           p.lmap == MAP_ROWS && p.smap == MAP_ROWS;
+      const bool want_staged =
+          (p.variant == 0 && !reg4096) || p.variant == 2 || p.variant == 4;
       l.has_staged = want_staged && resolve_staged(l.d, l.lmap, l.smap, s.generic_only, &l.staged);
       l.staged.tmap = p.variant != 4;
       if (l.has_staged) {

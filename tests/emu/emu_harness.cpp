@@ -813,7 +813,9 @@ int64_t replay(const int64_t* n, int dims, int64_t batch, int direction, int pre
                            : run_umma(p.logL, p.tc_prec, d, src, dst)))
         err("no replay for this tensor-core pass", p.logL);
     }
-    else if (specialised && !s.generic_only && (p.variant == 0 || p.variant == 2) &&
+    else if (specialised && !s.generic_only &&
+             ((p.variant == 0 && !(p.logL == 12 && p.lmap == MAP_ROWS && p.smap == MAP_ROWS)) ||
+              p.variant == 2) &&  // contiguous 2^12: the library's choice is the register kernel
              (p.lmap == MAP_COLS ? run_staged_cols(p.lmap, p.smap, d, src, dst)
               : p.smap == MAP_COLS ? run_staged_trans(p.lmap, p.smap, d, src, dst)
                                    : run_staged(d, src, dst)))

@@ -41,10 +41,22 @@ def test_compile_time_shapes(oracle, logn, direction, specialised):
     x = synth.uniform(9, batch, n)
     y, nerr, msg = emu.run(x, (n,), direction=direction, specialised=specialised, stats=st)
     assert nerr == 0, msg
-    expect_staged = specialised and logn >= 12      # staged kernel for 2^12 .. 2^14
+    expect_staged = specialised and logn >= 13      # staged kernel for 2^13, 2^14 (2^12: register)
     assert st["staged_passes"] == (1 if expect_staged else 0)
     assert st["special_passes"] == (1 if specialised and not expect_staged else 0)
     assert np.max(oracle.rel_l2(y, oracle.fft(x, direction))) <= 1e-6 * logn
+
+
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_staged_4096_on_request(oracle, direction):
+    """Variant 2 runs contiguous 4096-point transforms on the staged kernel
+    (the library's own choice there is the register kernel)."""
+    st = {}
+    x = synth.uniform(10, 7, 4096)
+    y, nerr, msg = emu.run(x, (4096,), direction=direction, stats=st, variant=2)
+    assert nerr == 0, msg
+    assert st["staged_passes"] == 1
+    assert np.max(oracle.rel_l2(y, oracle.fft(x, direction))) <= 1e-6 * 12
 
 
 @pytest.mark.parametrize("logn,batch", [(15, 2), (16, 1), (17, 1), (18, 1)])

@@ -311,7 +311,7 @@ def test_staged_kernel_and_unaligned_fallback(gb, oracle, logn):
         xin.copy_(torch.from_numpy(x_np.reshape(-1)))
         out = obuf[oshift:oshift + batch * n]
         out.zero_()
-        with gb.Plan(n, batch) as p:
+        with gb.Plan(n, batch, variant=2) as p:  # the staged kernel at 2^12 too
             gb.fft_execute(p.handle, xin.data_ptr(), out.data_ptr(),
                            torch.cuda.current_stream().cuda_stream)
             gb.fft_plan_sync_status(p.handle, torch.cuda.current_stream().cuda_stream)
@@ -451,14 +451,14 @@ def test_graph_execution_matches(gb, oracle, shape, batch):
 
 @pytest.mark.parametrize("shape,batch,kernels", [
     ((256,), 2 ** 19, ["compile_time"]), ((2048,), 2 ** 16, ["compile_time"]),
-    ((4096,), 2 ** 15, ["staged"]), ((8192,), 2 ** 14, ["staged"]), ((16384,), 2 ** 13, ["staged"]),
+    ((4096,), 2 ** 15, ["compile_time"]), ((8192,), 2 ** 14, ["staged"]), ((16384,), 2 ** 13, ["staged"]),
     ((2 ** 20,), 4, ["staged", "staged"]), ((2 ** 22,), 1, ["staged", "staged"]),
     ((4096, 8192), 1, ["staged", "staged"]), ((512,), 2 ** 18, ["compile_time"]),
     ((512,), 3, ["generic"])])
 def test_kernel_selection(gb, shape, batch, kernels):
-    """The benchmarked shapes bind the intended kernels; a small batch whose
-    tile has no compiled shape (4 transforms of 512 points) runs the generic
-    kernel."""
+    """The benchmarked shapes bind the intended kernels (2^12 the register
+    kernel, 2^13 and 2^14 the staged one); a small batch whose tile has no
+    compiled shape (4 transforms of 512 points) runs the generic kernel."""
     with gb.Plan(shape if len(shape) > 1 else shape[0], batch) as p:
         got = [k["kernel"] for k in p.describe()["kernels"]]
     assert got == kernels, got
