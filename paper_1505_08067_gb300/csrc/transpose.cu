@@ -9,9 +9,10 @@
 // Elements are complex64, or complex32 (FP16 pairs) with H.
 //
 // 32 x 32 tiles through shared memory (one padding column: the column reads
-// of a half warp fall into distinct bank pairs); 256 threads, each moving 4
-// elements of a tile, loads and stores both along rows of 32 consecutive
-// elements.  Persistent grid over all tiles of all batch entries.
+// of a half warp fall into distinct bank pairs); 256 threads moving 4
+// elements each (complex64) or 128 threads moving 8 (complex32), loads and
+// stores both along rows of 32 consecutive elements.  Persistent grid over
+// all tiles of all batch entries.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,42 +44,50 @@ __device__ __forceinline__ void tr_store(void* p, int64_t i, cf v) {
   else static_cast<float2*>(p)[i] = make_float2(v.x, v.y);
 }
 
+// THREADS = 32 x WY: each thread moves 32 / WY elements of a tile, rows
+// r0 + WY i of one column (complex64: WY = 8, four elements; complex32:
+// WY = 4, eight elements, so that a warp keeps as many bytes in flight as
+// with complex64 -- four 4-byte loads per thread held the complex32
+// transpose to about 60% of the HBM bandwidth).
 template <bool H, bool TW>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(H ? 128 : 256)
 transpose_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t batch, int64_t rows,
                  int64_t cols, int logN, int sign) {
+  constexpr int WY = H ? 4 : 8, PER = 32 / WY;
   __shared__ cf tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x WY
   const int64_t trow = rows / 32, tcol = cols / 32, per = trow * tcol;
   for (int64_t t = blockIdx.x; t < batch * per; t += gridDim.x) {
     const int64_t b = t / per, rt = (t - b * per) / tcol, ct = t - b * per - rt * tcol;
     const int64_t base = b * rows * cols;
-    // the thread's four elements share column c and step 8 rows: their
-    // twiddles are w^{r c} (w^{8 c})^i, two sincospi and a running product
+    // the thread's elements share column c and step WY rows: their
+    // twiddles are w^{r c} (w^{WY c})^i, two sincospi and a running product
     const int64_t c = ct * 32 + tx, r0 = rt * 32 + ty;
     cf w = mk(1.f, 0.f), step = mk(1.f, 0.f);
     if (TW) {
       w = DevMem::rotor(r0 * c, logN);  // exp(-2 pi i r c / N), r c < N
-      step = DevMem::rotor(8 * c, logN);
+      step = DevMem::rotor(WY * c, logN);
       if (sign > 0) {
         w = cconj(w);
         step = cconj(step);
       }
     }
+    cf v[PER];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      cf v = tr_load<H>(in, base + (r0 + 8 * i) * cols + c);
+    for (int i = 0; i < PER; ++i) v[i] = tr_load<H>(in, base + (r0 + WY * i) * cols + c);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
       if (TW) {
-        v = cmul(v, w);
+        v[i] = cmul(v[i], w);
         w = cmul(w, step);
       }
-      tile[ty + 8 * i][tx] = v;
+      tile[ty + WY * i][tx] = v[i];
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t c = ct * 32 + ty + 8 * i, r = rt * 32 + tx;
-      tr_store<H>(out, base + c * rows + r, tile[tx][ty + 8 * i]);
+    for (int i = 0; i < PER; ++i) {
+      const int64_t c = ct * 32 + ty + WY * i, r = rt * 32 + tx;
+      tr_store<H>(out, base + c * rows + r, tile[tx][ty + WY * i]);
     }
     __syncthreads();  // the tile is reused
   }
@@ -91,8 +100,13 @@ cudaError_t launch_transpose(const void* in, void* out, int64_t batch, int64_t r
   if (batch <= 0) return cudaSuccess;
   if (rows % 32 || cols % 32 || rows < 32 || cols < 32) return cudaErrorInvalidValue;
   const int64_t tiles = batch * (rows / 32) * (cols / 32);
-  const int grid = (int)std::min<int64_t>(tiles, (int64_t)(sm_count > 0 ? sm_count : 152) * 8);
-#define GB_TR(HH, TT) transpose_kernel<HH, TT><<<grid, 256, 0, st>>>(in, out, batch, rows, cols, logN, sign)
+  // eight 256-thread blocks (complex64) or sixteen 128-thread blocks
+  // (complex32) per SM
+  const int per_sm = h16 ? 16 : 8;
+  const int grid =
+      (int)std::min<int64_t>(tiles, (int64_t)(sm_count > 0 ? sm_count : 152) * per_sm);
+#define GB_TR(HH, TT) \
+  transpose_kernel<HH, TT><<<grid, HH ? 128 : 256, 0, st>>>(in, out, batch, rows, cols, logN, sign)
   if (h16) {
     if (logN > 0) GB_TR(true, true);
     else GB_TR(true, false);
