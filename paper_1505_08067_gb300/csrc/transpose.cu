@@ -10,9 +10,10 @@
 //
 // 32 x 32 tiles through shared memory (one padding column: the column reads
 // of a half warp fall into distinct bank pairs); 256 threads moving 4
-// elements each (complex64) or 128 threads moving 8 (complex32), loads and
-// stores both along rows of 32 consecutive elements.  Persistent grid over
-// all tiles of all batch entries.
+// elements each (plain complex64) or 128 threads moving 8 (complex32, and
+// the twiddle transpose), loads and stores both along rows of 32
+// consecutive elements.  Persistent grid over all tiles of all batch
+// entries.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,15 +46,16 @@ __device__ __forceinline__ void tr_store(void* p, int64_t i, cf v) {
 }
 
 // THREADS = 32 x WY: each thread moves 32 / WY elements of a tile, rows
-// r0 + WY i of one column (complex64: WY = 8, four elements; complex32:
-// WY = 4, eight elements, so that a warp keeps as many bytes in flight as
-// with complex64 -- four 4-byte loads per thread held the complex32
-// transpose to about 60% of the HBM bandwidth).
+// r0 + WY i of one column.  Plain complex64: WY = 8, four elements.
+// complex32: WY = 4, eight elements, so that a warp keeps as many bytes in
+// flight as with complex64 (four 4-byte loads per thread held the complex32
+// transpose to about 60% of the HBM bandwidth).  With the twiddle: WY = 4
+// as well, which spreads each thread's two sincospi over eight elements.
 template <bool H, bool TW>
-__global__ void __launch_bounds__(H ? 128 : 256)
+__global__ void __launch_bounds__(H || TW ? 128 : 256)
 transpose_kernel(const void* __restrict__ in, void* __restrict__ out, int64_t batch, int64_t rows,
                  int64_t cols, int logN, int sign) {
-  constexpr int WY = H ? 4 : 8, PER = 32 / WY;
+  constexpr int WY = H || TW ? 4 : 8, PER = 32 / WY;
   __shared__ cf tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x WY
   const int64_t trow = rows / 32, tcol = cols / 32, per = trow * tcol;
@@ -100,13 +102,13 @@ cudaError_t launch_transpose(const void* in, void* out, int64_t batch, int64_t r
   if (batch <= 0) return cudaSuccess;
   if (rows % 32 || cols % 32 || rows < 32 || cols < 32) return cudaErrorInvalidValue;
   const int64_t tiles = batch * (rows / 32) * (cols / 32);
-  // eight 256-thread blocks (complex64) or sixteen 128-thread blocks
-  // (complex32) per SM
-  const int per_sm = h16 ? 16 : 8;
+  // eight 256-thread blocks (plain complex64) or sixteen 128-thread blocks
+  // per SM
+  const int per_sm = h16 || logN > 0 ? 16 : 8;
   const int grid =
       (int)std::min<int64_t>(tiles, (int64_t)(sm_count > 0 ? sm_count : 152) * per_sm);
 #define GB_TR(HH, TT) \
-  transpose_kernel<HH, TT><<<grid, HH ? 128 : 256, 0, st>>>(in, out, batch, rows, cols, logN, sign)
+  transpose_kernel<HH, TT><<<grid, HH || TT ? 128 : 256, 0, st>>>(in, out, batch, rows, cols, logN, sign)
   if (h16) {
     if (logN > 0) GB_TR(true, true);
     else GB_TR(true, false);
